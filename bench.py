@@ -1,0 +1,393 @@
+"""Benchmark of the batched HeSP simulator (sim task-events/s, bit-exact).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hesp|reference]
+
+One step = the hot path over one batch: 65,536 candidate partition vectors of
+the 8 x 8-tile Cholesky (b = 2048, split levels uniform in {0, 1, 2}) drawn on
+the device from SplitMix64, then simulated on both platforms of that workload
+(12 CPU + 1 GPU-type processor with transfers, and 4 big + 4 LITTLE cores in
+shared memory).  The metric counts one task-event per task scheduled and
+completed in one candidate's simulation.
+
+N > 1 (torchrun): weak scaling -- rank r simulates its own 65,536 candidates
+(indices r * 65,536 ...); no collective touches the data path, only a barrier
+and a max over ranks of the timed region.
+
+--impl reference times the CPU oracle (the plain C implementation the GPU
+results are checked against) on the host cores, on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1602_05510_b300 import workloads as W  # noqa: E402
+
+WORKLOAD = W.WORKLOADS["cfg1"]
+N_TILES, B, N_LEVELS, N_CAND = WORKLOAD.n_tiles, WORKLOAD.b, WORKLOAD.n_levels, WORKLOAD.n_cand
+MAX_LEVEL = N_LEVELS - 1
+PLATS = ("cfg1a", "cfg1b")
+METRIC = "sim task-events/s (bit-exact)"
+UNIT = "task-events/s"
+CONFIG = {"workload": "random search, N=16384 Cholesky, b=2048 (8x8 tiles, 120 base tasks), split levels "
+                      "uniform {0,1,2}, 65,536 candidates per launch, simulated on 12 CPU + 1 GPU-type "
+                      "(transfers, write-back caching) and on 4 big + 4 LITTLE cores (shared memory)",
+          "n_tiles": N_TILES, "b": B, "levels": N_LEVELS, "candidates_per_step": N_CAND,
+          "platforms": ["cpu12_gpu1", "big4_little4"], "seed": WORKLOAD.seed}
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+# --------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- GPU arm
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1602_05510_b300 import build, hesp
+
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    nb = W.base_count(N_TILES)
+    C = N_CAND
+    first0 = rank * C
+
+    plats = [hesp.Platform(W.PLATFORMS[k]) for k in PLATS]
+    ws = [hesp.alloc_workspace(p, N_TILES, MAX_LEVEL, C) for p in plats]
+    levels = torch.empty(C * nb, dtype=torch.int8, device=dev)
+    cands = torch.empty(C * 16, dtype=torch.uint8, device=dev)
+    ms = [torch.empty(C, dtype=torch.int64, device=dev) for _ in plats]
+    stt = [torch.empty(C, dtype=torch.int32, device=dev) for _ in plats]
+    nts = [torch.empty(C, dtype=torch.int64, device=dev) for _ in plats]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+
+    def step(first, ev=None):
+        hesp.generate_candidates(hesp.GEN_UNIFORM, WORKLOAD.seed, first, C, N_TILES, B, N_LEVELS, levels, cands)
+        for i, p in enumerate(plats):
+            if ev is not None:
+                ev[i][0].record(stream)
+            hesp.simulate_batch(p, cands, levels, C, N_TILES, MAX_LEVEL, ws[i], makespan=ms[i], status=stt[i],
+                                ntasks=nts[i])
+            if ev is not None:
+                ev[i][1].record(stream)
+
+    for w in range(args.warmup):
+        step(first0 + w * world * C)
+    torch.cuda.synchronize()
+    for i in range(len(plats)):
+        bad = int((stt[i] != 0).sum().item())
+        if bad:
+            raise RuntimeError("%d candidates failed on %s" % (bad, PLATS[i]))
+
+    K = args.steps
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    kern_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in plats]
+               for _ in range(K)]
+    task_events = 0
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for k in range(K):
+        flush.fill_(k & 0xFF)  # evict L2 between timed steps (outside the step's events)
+        step_ev[k][0].record(stream)
+        step(first0 + (args.warmup + k) * world * C, kern_ev[k])
+        step_ev[k][1].record(stream)
+        for i in range(len(plats)):
+            task_events += nts[i].sum()  # device-side accumulation, read after the loop
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    task_events = int(task_events.item()) if K else 0
+    for i in range(len(plats)):
+        if int((stt[i] != 0).sum().item()):
+            raise RuntimeError("candidates failed on %s" % PLATS[i])
+    t_steps = sum(step_ev[k][0].elapsed_time(step_ev[k][1]) for k in range(K)) / 1e3
+    t_kern = [sum(kern_ev[k][i][0].elapsed_time(kern_ev[k][i][1]) for k in range(K)) / 1e3 for i in range(len(plats))]
+    t_max = t_steps
+    tot_events = task_events
+    if world > 1:
+        tt = torch.tensor([t_steps], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        ev = torch.tensor([task_events], dtype=torch.int64, device=dev)
+        dist.all_reduce(ev, op=dist.ReduceOp.SUM)
+        tot_events = int(ev.item())
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        lv_host = [torch.from_numpy(W.uniform_levels(WORKLOAD.seed, first0 + (1000 + s) * C, C, nb, N_LEVELS)
+                                    .reshape(-1)).pin_memory() for s in range(min(args.e2e_steps, 2))]
+        cand_host = hesp.cands_tensor(N_TILES, B, np.arange(C, dtype=np.int64) * nb, device="cpu").pin_memory()
+        out_host = [torch.empty(C, dtype=torch.int64).pin_memory() for _ in plats]
+        e2e_ev = []
+        e2e_tasks = 0
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for s in range(args.e2e_steps):
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(s & 0xFF)
+            a.record(stream)
+            levels.copy_(lv_host[s % len(lv_host)], non_blocking=True)
+            cands.copy_(cand_host, non_blocking=True)
+            for i, p in enumerate(plats):
+                hesp.simulate_batch(p, cands, levels, C, N_TILES, MAX_LEVEL, ws[i], makespan=ms[i], status=stt[i],
+                                    ntasks=nts[i])
+                out_host[i].copy_(ms[i], non_blocking=True)
+            b_.record(stream)
+            e2e_ev.append((a, b_))
+            for i in range(len(plats)):
+                e2e_tasks += nts[i].sum()
+        torch.cuda.synchronize()
+        t_e2e = sum(a.elapsed_time(b_) for a, b_ in e2e_ev) / 1e3
+        e2e_tasks = int(e2e_tasks.item())
+        if world > 1:
+            tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+            ev = torch.tensor([e2e_tasks], dtype=torch.int64, device=dev)
+            dist.all_reduce(ev, op=dist.ReduceOp.SUM)
+            e2e_tasks = int(ev.item())
+        e2e = {"value": e2e_tasks / t_e2e, "unit": UNIT, "h2d_bytes_per_step": C * nb + C * 16,
+               "d2h_bytes_per_step": 8 * C * len(plats), "steps": args.e2e_steps,
+               "path": "pinned host partition vectors -> hesp_simulate_batch x2 -> host makespans"}
+
+    if rank == 0:
+        peaks = measured_peaks()
+        line = {
+            "metric": METRIC, "value": tot_events / t_max if t_max > 0 else None, "unit": UNIT,
+            "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / max(K, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded SplitMix64 partition vectors generated on the device)",
+            "config": dict(CONFIG, parallelism="candidates sharded across ranks (dp%d)" % world,
+                           l2="256 MB buffer written between timed steps; per-step working set ~GBs > L2"),
+            "candidates_per_s": 2 * C * world * K / t_max if t_max > 0 else None,
+            "task_events": tot_events,
+            "wall_s": wall,
+            "gpu_launches": 3 * K,
+            "clocks": clk,
+            "e2e": e2e,
+        }
+        line["roofline"] = roofline(plats, t_kern, K, tot_events // world, clk, peaks)
+        if args.cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def roofline(plats, t_kern, K, task_events_rank, clk, peaks):
+    """Dominant kernel: the simulation kernel on the CPU+GPU platform.  It is
+    bound by integer/control issue, not by HBM or tensor cores; `achieved`
+    counts the algorithmic int64 operations of the simulation per task-event
+    (EFT evaluation 4 P, data-ready times M A_j, coherence commit A_j) and the
+    peak is the SM integer issue rate at the maximum SM clock (148 SMs x 128
+    lanes, one int64 operation = 2 lane-operations)."""
+    alg = alg_ops_per_event(W.workload_levels("cfg1", 0, 4096), len(W.PLATFORMS["cfg1a"].procs),
+                            W.PLATFORMS["cfg1a"].n_mem)
+    t = t_kern[0] / max(K, 1)
+    sm_max = (peaks or {}).get("sm_max_mhz", 2032.0)
+    peak = 148 * 128 * sm_max * 1e6 / 2 / 1e12  # T int64-op/s
+    ev_a = task_events_rank / 2  # both platforms run the same candidates
+    achieved = alg * ev_a / t / 1e12 if t > 0 and alg else None
+    return {"bound": "alu", "kernel": "sim_kernel<M=2> (cpu12_gpu1)", "achieved": achieved, "peak": peak,
+            "unit": "T int64-op/s", "frac": achieved / peak if achieved else None,
+            "peak_source": "derived: 148 SMs x 128 INT32 lanes x %.0f MHz / 2 (of MEASURED_PEAKS sm_max_mhz)" % sm_max,
+            "kernel_ms": 1e3 * t, "traffic": None,
+            "alg_ops_per_task_event": alg}
+
+
+def alg_ops_per_event(levels, P, M):
+    """Algorithmic int64 operations per task-event of one launch: 4 P for the
+    EFT evaluation (two max, one add, one compare per processor) plus
+    (M + 1) per atom of the task's data (data-ready time per memory, then the
+    coherence commit), with atoms of side b >> (candidate's deepest level)."""
+    from paper_1602_05510_b300 import hesp
+    kids = {0: (2, 1, 1, 0), 1: (0, 4, 0, 2), 2: (0, 0, 4, 2), 3: (0, 0, 0, 8)}
+    nreg = np.array([1, 2, 2, 3])
+    tab = np.zeros((4, 5, 4), np.int64)
+    for op in range(4):
+        tab[op, 0, op] = 1
+    for l in range(1, 5):
+        for op in range(4):
+            tab[op, l] = sum(kids[op][c] * tab[c, l - 1] for c in range(4))
+    ops = hesp.Dag(N_TILES, B, MAX_LEVEL).base_tasks()[0]
+    lv = np.asarray(levels, np.int64)
+    Lc = lv.max(axis=1, keepdims=True)
+    tasks = tab[ops[None, :], lv].sum(-1)                  # [C, n_base]
+    regs = (tab[ops[None, :], lv] * nreg).sum(-1)
+    atoms = regs * (4 ** (Lc - lv))
+    return 4 * P + (M + 1) * atoms.sum() / tasks.sum()
+
+
+def cpu_baseline(sample):
+    import oracle as O
+
+    cores = os.cpu_count() or 1
+    lv = W.workload_levels("cfg1", 0, sample)
+    t0 = time.perf_counter()
+    ev = 0
+    for k in PLATS:
+        pl = O.make_platform(W.PLATFORMS[k])
+        ms, st, tasks = O.simulate_many(pl, N_TILES, B, lv, threads=cores)
+        ev += int(tasks.sum())
+    dt = time.perf_counter() - t0
+    return {"value": ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d candidates of the same workload x 2 platforms (%d task-events), one candidate per "
+                      "thread-chunk over %d host threads, %.1f s" % (sample, ev, cores, dt)}
+
+
+# ---------------------------------------------------------- reference arm
+
+
+def run_reference(args):
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return
+    import oracle as O
+
+    O.build()
+    cores = os.cpu_count() or 1
+    per_step = args.ref_sample
+    pls = [O.make_platform(W.PLATFORMS[k]) for k in PLATS]
+
+    def one(k):
+        lv = W.workload_levels("cfg1", (k * 7919) % (N_CAND - per_step), per_step)
+        ev = 0
+        for pl in pls:
+            _, st, tasks = O.simulate_many(pl, N_TILES, B, lv, threads=cores)
+            ev += int(tasks.sum())
+        return ev
+
+    for w in range(args.warmup):
+        one(w)
+    t0 = time.perf_counter()
+    ev = 0
+    for k in range(args.steps):
+        ev += one(args.warmup + k)
+    dt = time.perf_counter() - t0
+    v = ev / dt
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "impl": "reference",
+            "config": dict(CONFIG, parallelism="host threads"),
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": v, "unit": UNIT,
+                             "sample": "%d candidates per step x 2 platforms on %d host threads" % (per_step, cores)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hesp", choices=["hesp", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-sample", type=int, default=16384)
+    ap.add_argument("--ref-sample", type=int, default=256)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

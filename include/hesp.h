@@ -1,0 +1,212 @@
+/*
+ * hesp.h -- C ABI of libhesp.so, a single-GPU (NVIDIA B300, sm_103a) engine
+ * for the data-parallel hot path of HeSP (Rey, Igual, Prieto-Matias, "HeSP: a
+ * simulation framework for solving the task scheduling-partitioning problem
+ * on heterogeneous architectures", arXiv 1602.05510): batched evaluation of
+ * candidate partitions of the tiled Cholesky task DAG.
+ *
+ * Conventions
+ *   - Every call returns an int status: HESP_OK (0) or a negative HESP_ERR_*.
+ *     hesp_status_string() names it.
+ *   - "_dev" pointers are device memory owned by the caller; "_host" pointers
+ *     are host memory owned by the caller.  Opaque handles are created and
+ *     destroyed by the library.
+ *   - Calls that take `void* stream` (a cudaStream_t; NULL = legacy default
+ *     stream) are asynchronous on that stream; their per-candidate results
+ *     (status words) are valid once the stream has reached them.  Argument
+ *     errors are reported synchronously by the return value.
+ *   - Simulated time is int64 nanoseconds.  No floating point is used in the
+ *     simulation; results are exactly those of the rules described below.
+ *   - Handles are not thread-safe; distinct handles may be used concurrently.
+ *   - There is no CPU fallback: without a usable CUDA device the calls that
+ *     launch work return HESP_ERR_CUDA.
+ */
+#ifndef HESP_H
+#define HESP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define HESP_OK 0
+#define HESP_ERR_ARG (-1)         /* invalid argument (host) or candidate (device) */
+#define HESP_ERR_CAPACITY (-2)    /* a candidate exceeds the workspace capacities */
+#define HESP_ERR_CUDA (-3)        /* CUDA runtime error or no device */
+#define HESP_ERR_TIMEOUT (-4)     /* a candidate's event loop exceeded its iteration cap */
+#define HESP_ERR_STATE (-5)       /* internal consistency check failed */
+#define HESP_ERR_UNSUPPORTED (-6) /* outside the supported limits below */
+
+const char *hesp_status_string(int status);
+
+/* ----------------------------------------------------------------- limits */
+#define HESP_MAX_MEMS 4   /* memory spaces (0 = host) */
+#define HESP_MAX_TYPES 4  /* processor types */
+#define HESP_MAX_PROCS 64 /* processors */
+#define HESP_MAX_LEVEL 4  /* split levels per base task: 0..4 */
+#define HESP_MAX_TILES 64 /* tiles per matrix side */
+#define HESP_MAX_LOG2_BLOCK 20 /* block sizes are powers of two up to 2^20 */
+
+/* Operations of the blocked Cholesky factorization (Sec. 1.1, Fig. 1). */
+#define HESP_OP_CHOL 0
+#define HESP_OP_TRSM 1
+#define HESP_OP_SYRK 2
+#define HESP_OP_GEMM 3
+
+/* -------------------------------------------------------------- platform
+ * Sec. 2: a platform is a set of memory spaces connected by a network and a
+ * set of processors, each tied to one memory space; Sec. 2.1 "Performance and
+ * data transfer models": task and transfer times come from models given a
+ * priori.
+ *
+ * Processor type model: a task of operation op on a bs x bs block takes
+ *     ceil(flops / rate) ns,  flops = {1, 3, 3, 6}[op] * bs^3 / 3,
+ *     rate = peak_gflops * eff_pct[op] / 100 * bs^2 / (bs^2 + h^2) GFLOP/s,
+ * unless overridden by hesp_platform_set_exec_table (measured models).
+ * Transfer model (every pair of memories, no contention): a message of E
+ * elements takes xfer_latency_ns + ceil(bytes_per_elem * E / bw_bytes_per_ns).
+ * Memory 0 is host memory; accelerator memories act as write-back software
+ * caches of it (Sec. 2.1).  Memories have unlimited capacity. */
+typedef struct {
+    int64_t peak_gflops;
+    int64_t h;
+    int32_t eff_pct[4]; /* indexed by HESP_OP_* */
+} hesp_ptype;
+
+typedef struct {
+    int32_t memory; /* 0 .. n_mem-1 */
+    int32_t type;   /* 0 .. n_types-1 */
+} hesp_proc;
+
+typedef struct {
+    int32_t n_mem;          /* 1 .. HESP_MAX_MEMS */
+    int32_t n_types;        /* 1 .. HESP_MAX_TYPES */
+    const hesp_ptype *types;
+    int32_t n_procs;        /* 1 .. HESP_MAX_PROCS; processor id = index */
+    const hesp_proc *procs;
+    int64_t xfer_latency_ns;
+    int64_t bytes_per_elem;
+    int64_t bw_bytes_per_ns; /* >= 1 when n_mem > 1 */
+} hesp_platform_desc;
+
+typedef struct hesp_platform hesp_platform;
+
+/* Copies `desc` (host memory) into a new handle.  ERR_ARG on invalid fields,
+ * ERR_UNSUPPORTED beyond the limits. */
+int hesp_platform_create(const hesp_platform_desc *desc, hesp_platform **out);
+/* Override the time of (op, type, block) with `ns` (a measured model,
+ * Sec. 2.1 / Sec. 3).  `block` must be a power of two <= 2^20, ns >= 1. */
+int hesp_platform_set_exec_table(hesp_platform *p, int32_t op, int32_t type, int64_t block, int64_t ns);
+/* Host queries of the models, as used by the simulator. */
+int hesp_platform_exec_ns(const hesp_platform *p, int32_t op, int32_t type, int64_t block, int64_t *ns_out);
+int hesp_platform_xfer_ns(const hesp_platform *p, int64_t elems, int64_t *ns_out);
+void hesp_platform_destroy(hesp_platform *p);
+
+/* ------------------------------------------------------------------- DAG
+ * Sec. 1.1 Fig. 1: the base tasks of an n x n tiled Cholesky (upper storage,
+ * A[k][j], j >= k) in the loop order
+ *     for k: chol(k); for j>k: trsm(k,j); for i>k: { for j>i: gemm(k,i,j); syrk(k,i) }
+ * Sec. 2.1 "Recursive task partitioners": a base task with split level l is
+ * replaced in place by the tasks of its 2x2 blocked algorithm, recursively l
+ * times (chol -> 4, trsm -> 6, syrk -> 6, gemm -> 8 tasks per level); task
+ * ids follow the depth-first order of this expansion. */
+typedef struct hesp_dag hesp_dag;
+
+int hesp_dag_build(int32_t n_tiles, int32_t b, int32_t max_level, hesp_dag **out);
+int64_t hesp_dag_n_base(const hesp_dag *d);
+/* Base task list (host arrays of hesp_dag_n_base entries): op and tile
+ * indices (k, i, j) with chol(k): i = j = k; trsm(k, j): i = k; syrk(k, i): j = i. */
+int hesp_dag_base_tasks(const hesp_dag *d, int32_t *op_host, int32_t *k_host, int32_t *i_host, int32_t *j_host);
+/* Tasks of one partition vector (levels_host: n_base int8 in 0..max_level),
+ * and the flop total times 3 (must equal (n b)^3 for every partition). */
+int hesp_dag_count_tasks(const hesp_dag *d, const int8_t *levels_host, int64_t *n_tasks_out,
+                         int64_t *flops3_out);
+void hesp_dag_destroy(hesp_dag *d);
+
+/* ---------------------------------------------------- batched simulation
+ * One candidate = (n_tiles, b, levels[level_offset .. + n_base)).  b must be
+ * a power of two with b >> max(levels) >= 1. */
+typedef struct {
+    int32_t n_tiles;
+    int32_t b;
+    int64_t level_offset;
+} hesp_cand;
+
+/* Bytes of device workspace needed to simulate candidates with at most
+ * `max_tiles` tiles and split levels <= `max_level` on platform `p`, using up
+ * to `n_cand` concurrent candidates (the library caps it at the number of
+ * resident warps of the current device).  The workspace is caller-owned
+ * device memory, 256-byte aligned, reused across calls on one stream. */
+int hesp_sim_workspace_size(const hesp_platform *p, int32_t max_tiles, int32_t max_level, int64_t n_cand,
+                            size_t *bytes_out);
+
+/* Simulate n_cand candidates (HeSP Sec. 2.1: FCFS task order at release time,
+ * EFT-P processor selection, write-back caching with prefetching transfers).
+ * For each candidate: expand its DAG, derive RaW/WaW/WaR dependences from the
+ * overlap of the tasks' data blocks, then run the event loop:
+ *   t = 0; released = tasks without predecessors; repeat: schedule every
+ *   released task in ascending id at time t; t = earliest finish in flight;
+ *   complete every task finishing at t; released = tasks whose predecessors
+ *   all completed.
+ * Scheduling task j at time t: for each memory m, DRT(j, m) = latest of the
+ * times its data is usable in m -- a copy valid in m is usable from the time
+ * it was written or arrived; data valid nowhere usable in m is fetched from
+ * the lowest-numbered memory holding a copy usable at t, one message per
+ * source memory issued at t.  EFT(p) = max(t, avail(p), DRT(j, mem(p))) +
+ * exec(op, type(p), block); the processor with the smallest EFT wins, ties to
+ * the lowest id.  Fetched data becomes valid in the chosen memory from its
+ * arrival; the written block then becomes valid only there, from the finish
+ * time.  The makespan is the largest finish time.
+ *
+ * Inputs (device): cands_dev[n_cand], levels_dev (int8, addressed through
+ * level_offset).  max_tiles / max_level bound every candidate and must match
+ * the workspace sizing.
+ * Outputs (device): makespan_dev[n_cand] (-1 on error), status_dev[n_cand]
+ * (HESP_OK or HESP_ERR_ARG / _CAPACITY / _TIMEOUT / _STATE for that
+ * candidate), ntasks_dev[n_cand] (nullable: task count of each candidate).
+ * Optional schedule (all four non-NULL or all NULL): task j of candidate c is
+ * written at index sched_offsets_dev[c] + j of proc_dev (int16 processor id),
+ * start_dev and finish_dev (int64 ns); the caller sizes them with
+ * hesp_dag_count_tasks.
+ * workspace: from hesp_sim_workspace_size for the same platform, max_tiles,
+ * max_level; any size >= the size for n_cand = 1 works (fewer candidates then
+ * run concurrently). */
+int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands_dev, const int8_t *levels_dev,
+                        int64_t n_cand, int32_t max_tiles, int32_t max_level, int64_t *makespan_dev,
+                        int32_t *status_dev, int64_t *ntasks_dev, const int64_t *sched_offsets_dev,
+                        int16_t *proc_dev, int64_t *start_dev, int64_t *finish_dev, void *workspace_dev,
+                        size_t workspace_bytes, void *stream);
+
+/* --------------------------------------------------- candidate generation
+ * Partition vectors drawn on the device from SplitMix64 (Steele, Lea, Flood,
+ * OOPSLA 2014) used as a counter-based generator: output k of candidate c is
+ * mix(seed + ((c << 32) + k + 1) * 0x9E3779B97F4A7C15) and a draw in [0, m)
+ * is ((u >> 32) * m) >> 32.  Candidates first .. first+n_cand-1 are written to
+ * index 0 .. n_cand-1 (the search of Sec. 2.1 "Iterative solver" proposes
+ * partitions; these are its random proposals). */
+#define HESP_GEN_EXHAUSTIVE 0 /* level[c][t] = bit t of c (levels 0/1) */
+#define HESP_GEN_UNIFORM 1    /* level[c][t] = draw(n_levels) at k = t */
+
+/* Fixed (n_tiles, b): levels_dev[n_cand * n_base], cands_dev[n_cand]
+ * (level_offset = c * n_base).  cands_dev may be NULL. */
+int hesp_generate_candidates(int32_t kind, uint64_t seed, int64_t first, int64_t n_cand, int32_t n_tiles,
+                             int32_t b, int32_t n_levels, hesp_cand *cands_dev, int8_t *levels_dev,
+                             void *stream);
+
+/* Ragged batch: n = 4 + draw(29) at k = 0, b = {512, 1024, 2048}[draw(3)] at
+ * k = 1, level of base task t from r = draw(10) at k = 2 + t mapped 0-4 -> 0,
+ * 5-7 -> 1, 8-9 -> 2.  Writes cands_dev[n_cand] with prefix-summed
+ * level_offset and the levels (capacity levels_cap bytes; ERR_CAPACITY
+ * reported through *levels_used_dev = -1 when too small).  levels_used_dev
+ * (device int64) receives the total. */
+int hesp_generate_uneven(uint64_t seed, int64_t first, int64_t n_cand, hesp_cand *cands_dev, int8_t *levels_dev,
+                         int64_t levels_cap, int64_t *levels_used_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HESP_H */

@@ -654,6 +654,8 @@ int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *c
     int32_t *pending = (int32_t *)malloc(sizeof(int32_t) * (size_t)(T + 1));
     int64_t *finish = (int64_t *)malloc(sizeof(int64_t) * (size_t)(T + 1));
     int8_t *state = (int8_t *)calloc((size_t)T + 1, 1); /* 0 waiting, 1 in flight, 2 done */
+    int32_t *inflight = (int32_t *)malloc(sizeof(int32_t) * (size_t)(T + 1)); /* tasks in flight */
+    int32_t n_inflight = 0;
     int32_t *released = (int32_t *)malloc(sizeof(int32_t) * (size_t)(T + 1));
     uint8_t *valid = (uint8_t *)calloc((size_t)(natoms * M), 1);
     int64_t *vfrom = (int64_t *)calloc((size_t)(natoms * M), sizeof(int64_t));
@@ -670,7 +672,7 @@ int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *c
     or_stats s;
     memset(&s, 0, sizeof s);
     if (!succ_off || !succ || !fill || !pending || !finish || !state || !released || !valid || !vfrom || !ax ||
-        !axw || !src) {
+        !axw || !src || !inflight) {
         rc = OR_ERR_CAPACITY;
         goto out;
     }
@@ -783,6 +785,7 @@ int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *c
             avail[best] = best_eft;
             finish[j] = best_eft;
             state[j] = 1;
+            inflight[n_inflight++] = j;
             if (proc_out) proc_out[j] = (int16_t)best;
             if (start_out) start_out[j] = best_eft - best_exec;
             if (finish_out) finish_out[j] = best_eft;
@@ -793,19 +796,23 @@ int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *c
         nrel = 0;
         /* next completion time */
         int64_t tn = -1;
-        for (int32_t j = 0; j < T; j++)
-            if (state[j] == 1 && (tn < 0 || finish[j] < tn)) tn = finish[j];
+        for (int32_t q = 0; q < n_inflight; q++)
+            if (tn < 0 || finish[inflight[q]] < tn) tn = finish[inflight[q]];
         if (tn < 0) break;
         t = tn;
         s.n_events++;
-        for (int32_t j = 0; j < T; j++) {
-            if (state[j] == 1 && finish[j] == t) {
+        for (int32_t q = 0; q < n_inflight;) {
+            int32_t j = inflight[q];
+            if (finish[j] == t) {
                 state[j] = 2;
                 n_done++;
                 for (int64_t e = succ_off[j]; e < succ_off[j + 1]; e++) {
                     int32_t sj = succ[e];
                     if (--pending[sj] == 0) released[nrel++] = sj;
                 }
+                inflight[q] = inflight[--n_inflight];
+            } else {
+                q++;
             }
         }
     }
@@ -822,6 +829,7 @@ out:
     free(pending);
     free(finish);
     free(state);
+    free(inflight);
     free(released);
     free(valid);
     free(vfrom);

@@ -1,0 +1,131 @@
+// On-device candidate generation: partition vectors from SplitMix64 used as a
+// counter-based generator (Steele, Lea, Flood, OOPSLA 2014): output k of
+// candidate c is mix(seed + ((c << 32) + k + 1) * 0x9E3779B97F4A7C15), and a
+// draw in [0, m) is Lemire's multiply-shift ((u >> 32) * m) >> 32.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hesp_internal.h"
+
+namespace hesp {
+namespace {
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t sm64_at(uint64_t seed, uint64_t c, uint64_t k) {
+    return sm64_mix(seed + ((c << 32) + k + 1) * kGamma);
+}
+
+__device__ __forceinline__ uint32_t draw(uint64_t u, uint32_t m) { return (uint32_t)(((u >> 32) * m) >> 32); }
+
+// One block row of threads per candidate tile of the level array.
+__global__ void gen_fixed_kernel(int kind, uint64_t seed, int64_t first, int64_t n_cand, int nb, int n_levels,
+                                 int n_tiles, int b, hesp_cand *cands, int8_t *levels) {
+    const int64_t c = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    if (c >= n_cand) return;
+    const uint64_t cg = (uint64_t)(first + c);
+    int8_t *row = levels + c * nb;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        int lv;
+        if (kind == HESP_GEN_EXHAUSTIVE) lv = t < 63 ? (int)((cg >> t) & 1u) : 0;
+        else lv = (int)draw(sm64_at(seed, cg, (uint64_t)t), (uint32_t)n_levels);
+        row[t] = (int8_t)lv;
+    }
+    if (threadIdx.x == 0 && cands) {
+        hesp_cand cd;
+        cd.n_tiles = n_tiles;
+        cd.b = b;
+        cd.level_offset = c * nb;
+        cands[c] = cd;
+    }
+}
+
+__global__ void uneven_shape_kernel(uint64_t seed, int64_t first, int64_t n_cand, hesp_cand *cands) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cand) return;
+    const uint64_t cg = (uint64_t)(first + c);
+    const int n = 4 + (int)draw(sm64_at(seed, cg, 0), 29);
+    const int bsel = (int)draw(sm64_at(seed, cg, 1), 3);
+    hesp_cand cd;
+    cd.n_tiles = n;
+    cd.b = 512 << bsel;
+    cd.level_offset = (int64_t)n * (n + 1) * (n + 2) / 6;  // count; prefix-summed next
+    cands[c] = cd;
+}
+
+// Exclusive prefix sum of the per-candidate base counts (one block).
+__global__ void uneven_scan_kernel(int64_t n_cand, hesp_cand *cands, int64_t levels_cap, int64_t *levels_used) {
+    __shared__ int64_t part[1024];
+    const int tid = threadIdx.x;
+    const int64_t chunk = (n_cand + blockDim.x - 1) / blockDim.x;
+    const int64_t lo = tid * chunk, hi = min(n_cand, lo + chunk);
+    int64_t s = 0;
+    for (int64_t c = lo; c < hi; ++c) s += cands[c].level_offset;
+    part[tid] = s;
+    __syncthreads();
+    if (tid == 0) {
+        int64_t run = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) {
+            const int64_t v = part[i];
+            part[i] = run;
+            run += v;
+        }
+        *levels_used = run <= levels_cap ? run : -1;
+    }
+    __syncthreads();
+    int64_t run = part[tid];
+    for (int64_t c = lo; c < hi; ++c) {
+        const int64_t v = cands[c].level_offset;
+        cands[c].level_offset = run;
+        run += v;
+    }
+}
+
+__global__ void uneven_fill_kernel(uint64_t seed, int64_t first, int64_t n_cand, const hesp_cand *cands,
+                                   int8_t *levels, const int64_t *levels_used) {
+    if (*levels_used < 0) return;
+    const int64_t c = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    if (c >= n_cand) return;
+    const uint64_t cg = (uint64_t)(first + c);
+    const hesp_cand cd = cands[c];
+    const int nb = cd.n_tiles * (cd.n_tiles + 1) * (cd.n_tiles + 2) / 6;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        const uint32_t r = draw(sm64_at(seed, cg, (uint64_t)t + 2), 10);
+        levels[cd.level_offset + t] = (int8_t)(r < 5 ? 0 : (r < 8 ? 1 : 2));
+    }
+}
+
+dim3 cand_grid(int64_t n_cand) {
+    const int64_t gx = n_cand < 65535 ? n_cand : 65535;
+    return dim3((unsigned)gx, (unsigned)((n_cand + gx - 1) / gx));
+}
+
+}  // namespace
+
+int launch_generate(int32_t kind, uint64_t seed, int64_t first, int64_t n_cand, int32_t n_tiles, int32_t b,
+                    int32_t n_levels, hesp_cand *cands, int8_t *levels, cudaStream_t stream) {
+    if (n_cand == 0) return HESP_OK;
+    const int nb = n_tiles * (n_tiles + 1) * (n_tiles + 2) / 6;
+    gen_fixed_kernel<<<cand_grid(n_cand), 128, 0, stream>>>(kind, seed, first, n_cand, nb, n_levels, n_tiles, b,
+                                                             cands, levels);
+    return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
+}
+
+int launch_generate_uneven(uint64_t seed, int64_t first, int64_t n_cand, hesp_cand *cands, int8_t *levels,
+                           int64_t levels_cap, int64_t *levels_used, cudaStream_t stream) {
+    if (n_cand == 0) return cudaMemsetAsync(levels_used, 0, sizeof(int64_t), stream) == cudaSuccess
+                                ? HESP_OK
+                                : HESP_ERR_CUDA;
+    uneven_shape_kernel<<<(unsigned)((n_cand + 255) / 256), 256, 0, stream>>>(seed, first, n_cand, cands);
+    uneven_scan_kernel<<<1, 1024, 0, stream>>>(n_cand, cands, levels_cap, levels_used);
+    uneven_fill_kernel<<<cand_grid(n_cand), 128, 0, stream>>>(seed, first, n_cand, cands, levels, levels_used);
+    return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
+}
+
+}  // namespace hesp

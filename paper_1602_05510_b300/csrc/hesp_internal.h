@@ -1,0 +1,75 @@
+// Internal declarations shared by the CUDA sources of libhesp.so.
+#pragma once
+
+#include <stdint.h>
+
+#include "hesp.h"
+
+#define HESP_LB (HESP_MAX_LOG2_BLOCK + 1)  // exec table entries per (op, type): block 2^0 .. 2^20
+
+struct hesp_platform {
+    int32_t n_mem, n_types, n_procs;
+    int64_t xfer_latency_ns, bytes_per_elem, bw_bytes_per_ns;
+    hesp_ptype types[HESP_MAX_TYPES];
+    hesp_proc procs[HESP_MAX_PROCS];
+    // exec[op][type][log2 block] in ns; -1 where the model does not fit in
+    // 56 bits (the simulator then flags the candidate with HESP_ERR_ARG).
+    int64_t exec[4][HESP_MAX_TYPES][HESP_LB];
+};
+
+struct hesp_dag {
+    int32_t n_tiles, b, max_level;
+    int64_t n_base;
+    int32_t *op, *k, *i, *j;  // host arrays of n_base
+};
+
+namespace hesp {
+
+// Platform image passed by value to the simulation kernel (constant bank),
+// copied to shared memory at kernel start.
+struct DevPlatform {
+    int32_t n_mem, n_types, n_procs, pad;
+    int64_t exec[4 * HESP_MAX_TYPES * HESP_LB];
+    int8_t proc_mem[HESP_MAX_PROCS];
+    int8_t proc_type[HESP_MAX_PROCS];
+    int64_t lat, bpe, bw;
+};
+
+// Per-warp arena of the simulator (one arena per concurrently simulated
+// candidate).  Capacities hold any candidate with n <= max_tiles and
+// levels <= max_level; offsets are bytes from the arena start.
+struct Arena {
+    int64_t slot_bytes;
+    int64_t Tcap;  // tasks
+    int64_t Ecap;  // dependence edges
+    int64_t Acap;  // atoms
+    int64_t Kcap;  // transfer-table entries (atoms per task + 1)
+    int64_t off_desc, off_pending, off_finish, off_next, off_succoff, off_succ, off_epred, off_esucc, off_lw,
+        off_valid, off_vfrom, off_bitmap, off_xt;
+};
+
+// Header at the start of the workspace.
+struct WsHeader {
+    unsigned long long work_counter;
+    unsigned long long pad[31];
+};
+constexpr int64_t kWsHeaderBytes = 256;
+
+// Closed forms used to size arenas (host side).
+int64_t tasks_uniform(int64_t n, int level);  // tasks when every base task is split `level` times
+int64_t regions_uniform(int64_t n, int level); // sum over those tasks of their region count
+Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem);
+
+int sim_slots_for(const hesp_platform *p, int64_t *resident_warps);  // device resident warp count
+int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, int64_t n_slots,
+               const hesp_cand *cands, const int8_t *levels, int64_t n_cand, int32_t max_tiles, int32_t max_level,
+               int64_t *makespan, int32_t *status, int64_t *ntasks, const int64_t *sched_off, int16_t *sproc,
+               int64_t *sstart, int64_t *sfinish, char *ws, cudaStream_t stream);
+int sim_kernel_occupancy(int n_mem, int n_procs, int *blocks_per_sm, int *threads_per_block);
+
+int launch_generate(int32_t kind, uint64_t seed, int64_t first, int64_t n_cand, int32_t n_tiles, int32_t b,
+                    int32_t n_levels, hesp_cand *cands, int8_t *levels, cudaStream_t stream);
+int launch_generate_uneven(uint64_t seed, int64_t first, int64_t n_cand, hesp_cand *cands, int8_t *levels,
+                           int64_t levels_cap, int64_t *levels_used, cudaStream_t stream);
+
+}  // namespace hesp

@@ -1,0 +1,232 @@
+"""Thin ctypes binding of libhesp.so (C ABI in include/hesp.h).
+
+Argument marshalling only: every step of the simulation and of the surrogate
+runs in the library's CUDA kernels.  PyTorch supplies device memory and the
+current stream.  There is no CPU fallback: if the library is missing or no
+CUDA device is usable, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhesp.so")
+
+HESP_OK = 0
+STATUS_NAMES = {0: "HESP_OK", -1: "HESP_ERR_ARG", -2: "HESP_ERR_CAPACITY", -3: "HESP_ERR_CUDA",
+                -4: "HESP_ERR_TIMEOUT", -5: "HESP_ERR_STATE", -6: "HESP_ERR_UNSUPPORTED"}
+GEN_EXHAUSTIVE, GEN_UNIFORM = 0, 1
+MAX_LEVEL, MAX_TILES, MAX_PROCS, MAX_MEMS, MAX_TYPES = 4, 64, 64, 4, 4
+
+# Every symbol include/hesp.h declares (checked by the CPU tests).
+EXPORTS = (
+    "hesp_status_string", "hesp_platform_create", "hesp_platform_set_exec_table", "hesp_platform_exec_ns",
+    "hesp_platform_xfer_ns", "hesp_platform_destroy", "hesp_dag_build", "hesp_dag_n_base",
+    "hesp_dag_base_tasks", "hesp_dag_count_tasks", "hesp_dag_destroy", "hesp_sim_workspace_size",
+    "hesp_simulate_batch", "hesp_generate_candidates", "hesp_generate_uneven",
+)
+
+CAND_DTYPE = np.dtype([("n_tiles", "<i4"), ("b", "<i4"), ("level_offset", "<i8")])
+
+
+class HespError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s failed: %s (%d)" % (what, STATUS_NAMES.get(code, "?"), code))
+        self.code = code
+
+
+class _PType(ctypes.Structure):
+    _fields_ = [("peak_gflops", ctypes.c_int64), ("h", ctypes.c_int64), ("eff_pct", ctypes.c_int32 * 4)]
+
+
+class _Proc(ctypes.Structure):
+    _fields_ = [("memory", ctypes.c_int32), ("type", ctypes.c_int32)]
+
+
+class _PlatDesc(ctypes.Structure):
+    _fields_ = [("n_mem", ctypes.c_int32), ("n_types", ctypes.c_int32), ("types", ctypes.POINTER(_PType)),
+                ("n_procs", ctypes.c_int32), ("procs", ctypes.POINTER(_Proc)),
+                ("xfer_latency_ns", ctypes.c_int64), ("bytes_per_elem", ctypes.c_int64),
+                ("bw_bytes_per_ns", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libhesp.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhesp.so not built: run `python -m paper_1602_05510_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        i32, i64, u64, vp, sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_size_t
+        L.hesp_status_string.restype = ctypes.c_char_p
+        L.hesp_status_string.argtypes = [ctypes.c_int]
+        L.hesp_platform_create.argtypes = [ctypes.POINTER(_PlatDesc), ctypes.POINTER(vp)]
+        L.hesp_platform_set_exec_table.argtypes = [vp, i32, i32, i64, i64]
+        L.hesp_platform_exec_ns.argtypes = [vp, i32, i32, i64, ctypes.POINTER(i64)]
+        L.hesp_platform_xfer_ns.argtypes = [vp, i64, ctypes.POINTER(i64)]
+        L.hesp_platform_destroy.argtypes = [vp]
+        L.hesp_platform_destroy.restype = None
+        L.hesp_dag_build.argtypes = [i32, i32, i32, ctypes.POINTER(vp)]
+        L.hesp_dag_n_base.argtypes = [vp]
+        L.hesp_dag_n_base.restype = i64
+        L.hesp_dag_base_tasks.argtypes = [vp, vp, vp, vp, vp]
+        L.hesp_dag_count_tasks.argtypes = [vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.hesp_dag_destroy.argtypes = [vp]
+        L.hesp_dag_destroy.restype = None
+        L.hesp_sim_workspace_size.argtypes = [vp, i32, i32, i64, ctypes.POINTER(sz)]
+        L.hesp_simulate_batch.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.hesp_generate_candidates.argtypes = [i32, u64, i64, i64, i32, i32, i32, vp, vp, vp]
+        L.hesp_generate_uneven.argtypes = [u64, i64, i64, vp, vp, i64, vp, vp]
+        _lib = L
+    return _lib
+
+
+def check(rc, what):
+    if rc != HESP_OK:
+        raise HespError(rc, what)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Platform:
+    """A simulated platform (hesp_platform handle) built from a
+    ``workloads.PlatformSpec``."""
+
+    def __init__(self, spec):
+        self.spec = spec
+        L = lib()
+        types = (_PType * len(spec.types))()
+        for i, t in enumerate(spec.types):
+            types[i].peak_gflops, types[i].h = t.peak_gflops, t.h
+            for o in range(4):
+                types[i].eff_pct[o] = t.eff_pct[o]
+        procs = (_Proc * len(spec.procs))()
+        for i, (m, ty) in enumerate(spec.procs):
+            procs[i].memory, procs[i].type = m, ty
+        d = _PlatDesc(spec.n_mem, len(spec.types), types, len(spec.procs), procs, spec.xfer_latency_ns,
+                      spec.bytes_per_elem, spec.bw_bytes_per_ns)
+        h = ctypes.c_void_p()
+        check(L.hesp_platform_create(ctypes.byref(d), ctypes.byref(h)), "hesp_platform_create")
+        self.h = h
+        for (op, ty, bs, ns) in getattr(spec, "exec_overrides", ()):
+            check(L.hesp_platform_set_exec_table(h, op, ty, bs, ns), "hesp_platform_set_exec_table")
+
+    @property
+    def n_mem(self):
+        return self.spec.n_mem
+
+    def exec_ns(self, op, ptype, block):
+        v = ctypes.c_int64()
+        check(lib().hesp_platform_exec_ns(self.h, op, ptype, block, ctypes.byref(v)), "hesp_platform_exec_ns")
+        return v.value
+
+    def xfer_ns(self, elems):
+        v = ctypes.c_int64()
+        check(lib().hesp_platform_xfer_ns(self.h, elems, ctypes.byref(v)), "hesp_platform_xfer_ns")
+        return v.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hesp_platform_destroy(self.h)
+            self.h = None
+
+
+class Dag:
+    """Base task list of an n x n tiled Cholesky (hesp_dag handle)."""
+
+    def __init__(self, n_tiles, b, max_level):
+        h = ctypes.c_void_p()
+        check(lib().hesp_dag_build(n_tiles, b, max_level, ctypes.byref(h)), "hesp_dag_build")
+        self.h = h
+        self.n_tiles, self.b, self.max_level = n_tiles, b, max_level
+        self.n_base = int(lib().hesp_dag_n_base(h))
+
+    def base_tasks(self):
+        out = [np.zeros(self.n_base, np.int32) for _ in range(4)]
+        check(lib().hesp_dag_base_tasks(self.h, *[o.ctypes.data for o in out]), "hesp_dag_base_tasks")
+        return out
+
+    def count_tasks(self, levels):
+        lv = np.ascontiguousarray(levels, np.int8)
+        t = ctypes.c_int64()
+        f = ctypes.c_int64()
+        check(lib().hesp_dag_count_tasks(self.h, lv.ctypes.data, ctypes.byref(t), ctypes.byref(f)),
+              "hesp_dag_count_tasks")
+        return t.value, f.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hesp_dag_destroy(self.h)
+            self.h = None
+
+
+def cands_tensor(n_tiles, b, offsets, device="cuda"):
+    """hesp_cand[] as a byte tensor on the device."""
+    import torch
+    offsets = np.asarray(offsets, np.int64)
+    a = np.zeros(len(offsets), CAND_DTYPE)
+    a["n_tiles"] = n_tiles
+    a["b"] = b
+    a["level_offset"] = offsets
+    return torch.from_numpy(a.view(np.uint8).copy()).to(device)
+
+
+def workspace_bytes(platform: Platform, max_tiles, max_level, n_cand):
+    v = ctypes.c_size_t()
+    check(lib().hesp_sim_workspace_size(platform.h, max_tiles, max_level, n_cand, ctypes.byref(v)),
+          "hesp_sim_workspace_size")
+    return v.value
+
+
+def alloc_workspace(platform: Platform, max_tiles, max_level, n_cand):
+    import torch
+    return torch.empty(workspace_bytes(platform, max_tiles, max_level, n_cand), dtype=torch.uint8, device="cuda")
+
+
+def simulate_batch(platform: Platform, cands, levels, n_cand, max_tiles, max_level, workspace,
+                   makespan=None, status=None, ntasks=None, schedule=None, stream=None):
+    """Launch hesp_simulate_batch on the current stream.  `cands` is a byte
+    tensor of hesp_cand, `levels` an int8 device tensor.  `schedule` is None
+    or (offsets int64, proc int16, start int64, finish int64) device tensors.
+    Returns (makespan, status, ntasks) device tensors."""
+    import torch
+    dev = levels.device
+    if makespan is None:
+        makespan = torch.empty(n_cand, dtype=torch.int64, device=dev)
+    if status is None:
+        status = torch.empty(n_cand, dtype=torch.int32, device=dev)
+    so = sp = ss = sf = None
+    if schedule is not None:
+        so, sp, ss, sf = schedule
+    check(lib().hesp_simulate_batch(platform.h, _ptr(cands), _ptr(levels), n_cand, max_tiles, max_level,
+                                    _ptr(makespan), _ptr(status), _ptr(ntasks), _ptr(so), _ptr(sp), _ptr(ss),
+                                    _ptr(sf), _ptr(workspace), workspace.numel(), _stream(stream)),
+          "hesp_simulate_batch")
+    return makespan, status, ntasks
+
+
+def generate_candidates(kind, seed, first, n_cand, n_tiles, b, n_levels, levels, cands=None, stream=None):
+    check(lib().hesp_generate_candidates(kind, seed, first, n_cand, n_tiles, b, n_levels, _ptr(cands),
+                                         _ptr(levels), _stream(stream)), "hesp_generate_candidates")
+
+
+def generate_uneven(seed, first, n_cand, cands, levels, levels_used, stream=None):
+    check(lib().hesp_generate_uneven(seed, first, n_cand, _ptr(cands), _ptr(levels), levels.numel(),
+                                     _ptr(levels_used), _stream(stream)), "hesp_generate_uneven")

@@ -1,0 +1,230 @@
+"""GPU parity of the batched simulator (hesp_simulate_batch through the C ABI)
+against the CPU oracle: makespans, per-task processors, start and finish times
+must be bit-identical (int64 ns, fixed tie-breaking), on every workload shape,
+at oracle-sized samples and at the full 65,536-candidate launch the benchmark
+times, plus edge cases and per-candidate error statuses."""
+import dataclasses
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1602_05510_b300 import hesp  # noqa: E402
+from paper_1602_05510_b300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1602_05510_b300 import build
+    build.build()
+
+
+def gpu_sim(spec, n, b, levels, max_level=None, schedule=False, max_tiles=None, ws_cands=None):
+    """Run one batch of candidates of the same (n, b) on the GPU."""
+    levels = np.ascontiguousarray(levels, np.int8)
+    C, nb = levels.shape
+    max_level = int(levels.max()) if max_level is None else max_level
+    max_tiles = n if max_tiles is None else max_tiles
+    plat = hesp.Platform(spec)
+    lv = torch.from_numpy(levels.reshape(-1).copy()).cuda()
+    cands = hesp.cands_tensor(n, b, np.arange(C, dtype=np.int64) * nb)
+    ws = hesp.alloc_workspace(plat, max_tiles, max_level, C if ws_cands is None else ws_cands)
+    ntasks = torch.empty(C, dtype=torch.int64, device="cuda")
+    sched = None
+    offs = None
+    if schedule:
+        dag = hesp.Dag(n, b, max(max_level, 0))
+        cnt = np.array([dag.count_tasks(levels[c])[0] for c in range(C)], np.int64)
+        offs = np.zeros(C + 1, np.int64)
+        offs[1:] = np.cumsum(cnt)
+        tot = int(offs[-1])
+        sched = (torch.from_numpy(offs[:-1].copy()).cuda(), torch.empty(tot, dtype=torch.int16, device="cuda"),
+                 torch.empty(tot, dtype=torch.int64, device="cuda"), torch.empty(tot, dtype=torch.int64, device="cuda"))
+    ms, st, nt = hesp.simulate_batch(plat, cands, lv, C, max_tiles, max_level, ws, ntasks=ntasks, schedule=sched)
+    torch.cuda.synchronize()
+    out = dict(makespan=ms.cpu().numpy(), status=st.cpu().numpy(), ntasks=nt.cpu().numpy())
+    if schedule:
+        out.update(offs=offs, proc=sched[1].cpu().numpy(), start=sched[2].cpu().numpy(),
+                   finish=sched[3].cpu().numpy())
+    return out
+
+
+def check_parity(spec, n, b, levels, g, idx=None, schedule=True):
+    pl = O.make_platform(spec)
+    idx = range(levels.shape[0]) if idx is None else idx
+    for c in idx:
+        r = O.simulate(pl, n, b, levels[c], schedule=schedule)
+        assert r["status"] == 0
+        assert g["status"][c] == 0, (c, g["status"][c])
+        assert g["makespan"][c] == r["makespan"], c
+        assert g["ntasks"][c] == r["n_tasks"], c
+        if schedule and "proc" in g:
+            a, e = g["offs"][c], g["offs"][c + 1]
+            assert np.array_equal(g["proc"][a:e], r["proc"]), c
+            assert np.array_equal(g["start"][a:e], r["start"]), c
+            assert np.array_equal(g["finish"][a:e], r["finish"]), c
+
+
+def test_worked_examples_on_gpu():
+    for key in ("n2_b1024_all_level0_cpu4_gpu1", "n1_b1024_chol_level1_cpu4_gpu1"):
+        e = GOLD[key]
+        g = gpu_sim(W.PLATFORMS[e["platform"]], e["n"], e["b"], np.array([e["levels"]]), schedule=True)
+        assert g["makespan"][0] == e["makespan"]
+        assert g["proc"].tolist() == e["proc"] and g["finish"].tolist() == e["finish"]
+    for key, ncpu in (("n2_b1024_cpu1_gpu1_overrides", 1), ("n3_b1024_cpu2_gpu1_overrides", 2)):
+        e = GOLD[key]
+        spec = dataclasses.replace(W.cpu_gpu_platform(ncpu, 1), exec_overrides=tuple(tuple(x) for x in e["overrides"]))
+        g = gpu_sim(spec, e["n"], e["b"], np.array([e["levels"]]), schedule=True)
+        assert g["makespan"][0] == e["makespan"]
+        assert g["proc"].tolist() == e["proc"]
+        assert g["start"].tolist() == e["start"] and g["finish"].tolist() == e["finish"]
+
+
+def test_cfg0_exhaustive_all_1024():
+    lv = W.workload_levels("cfg0")
+    g = gpu_sim(W.PLATFORMS["cfg0"], 3, 1024, lv, max_level=1, schedule=True)
+    check_parity(W.PLATFORMS["cfg0"], 3, 1024, lv, g)
+
+
+@pytest.mark.parametrize("key", ["cfg1a", "cfg1b"])
+def test_cfg1_sample_with_schedules(key):
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(65536, 192, replace=False))
+    lv = np.concatenate([W.workload_levels("cfg1", int(i), 1) for i in idx])
+    g = gpu_sim(W.PLATFORMS[key], 8, 2048, lv, max_level=2, schedule=True)
+    check_parity(W.PLATFORMS[key], 8, 2048, lv, g)
+
+
+@pytest.mark.parametrize("key", ["cfg1a", "cfg1b"])
+def test_cfg1_full_launch_sampled(key):
+    """The whole 65,536-candidate batch in one launch (the benchmark's launch
+    configuration); sampled candidates checked against the oracle, the rest
+    by properties that hold at any size."""
+    lv = W.workload_levels("cfg1")
+    g = gpu_sim(W.PLATFORMS[key], 8, 2048, lv, max_level=2)
+    assert (g["status"] == 0).all()
+    dag = hesp.Dag(8, 2048, 2)
+    rng = np.random.default_rng(5)
+    for c in rng.choice(65536, 200, replace=False):
+        assert g["ntasks"][c] == dag.count_tasks(lv[c])[0]
+    assert (g["makespan"] > 0).all()
+    idx = np.sort(rng.choice(65536, 48, replace=False))
+    check_parity(W.PLATFORMS[key], 8, 2048, lv, g, idx=idx, schedule=False)
+
+
+def test_device_generation_matches_host():
+    n = 8
+    nb = W.base_count(n)
+    lv = torch.empty(4096 * nb, dtype=torch.int8, device="cuda")
+    cands = torch.empty(4096 * 16, dtype=torch.uint8, device="cuda")
+    hesp.generate_candidates(hesp.GEN_UNIFORM, 1, 1000, 4096, n, 2048, 3, lv, cands)
+    torch.cuda.synchronize()
+    assert np.array_equal(lv.cpu().numpy().reshape(4096, nb), W.uniform_levels(1, 1000, 4096, nb, 3))
+    c = cands.cpu().numpy().view(hesp.CAND_DTYPE)
+    assert (c["n_tiles"] == n).all() and (c["b"] == 2048).all()
+    assert np.array_equal(c["level_offset"], np.arange(4096) * nb)
+    lv0 = torch.empty(1024 * 10, dtype=torch.int8, device="cuda")
+    hesp.generate_candidates(hesp.GEN_EXHAUSTIVE, 0, 0, 1024, 3, 1024, 2, lv0)
+    torch.cuda.synchronize()
+    assert np.array_equal(lv0.cpu().numpy().reshape(1024, 10), W.exhaustive_levels(10))
+    lv4 = torch.empty(64 * 5984, dtype=torch.int8, device="cuda")
+    hesp.generate_candidates(hesp.GEN_UNIFORM, 4, 0, 64, 32, 2048, 4, lv4)
+    torch.cuda.synchronize()
+    assert np.array_equal(lv4.cpu().numpy().reshape(64, 5984), W.uniform_levels(4, 0, 64, 5984, 4))
+
+
+def test_uneven_generation_and_parity():
+    C = 256
+    n, b, off, lvh = W.uneven_candidates(2, 0, C)
+    cands = torch.empty(C * 16, dtype=torch.uint8, device="cuda")
+    lv = torch.empty(int(off[-1]) + 100, dtype=torch.int8, device="cuda")
+    used = torch.zeros(1, dtype=torch.int64, device="cuda")
+    hesp.generate_uneven(2, 0, C, cands, lv, used)
+    torch.cuda.synchronize()
+    assert int(used.item()) == int(off[-1])
+    cd = cands.cpu().numpy().view(hesp.CAND_DTYPE)
+    assert np.array_equal(cd["n_tiles"], n) and np.array_equal(cd["b"], b)
+    assert np.array_equal(cd["level_offset"], off[:-1])
+    assert np.array_equal(lv.cpu().numpy()[:off[-1]], lvh)
+    # simulate the ragged batch and check a budget of small and large ones
+    spec = W.PLATFORMS["cfg2"]
+    plat = hesp.Platform(spec)
+    ws = hesp.alloc_workspace(plat, 32, 2, C)
+    ntasks = torch.empty(C, dtype=torch.int64, device="cuda")
+    ms, st, nt = hesp.simulate_batch(plat, cands, lv, C, 32, 2, ws, ntasks=ntasks)
+    torch.cuda.synchronize()
+    ms, st, nt = ms.cpu().numpy(), st.cpu().numpy(), nt.cpu().numpy()
+    assert (st == 0).all()
+    pl = O.make_platform(spec)
+    order = np.argsort(nt)
+    pick = list(order[:24]) + list(order[-3:]) + list(order[C // 2:C // 2 + 6])
+    for c in pick:
+        r = O.simulate(pl, int(n[c]), int(b[c]), lvh[off[c]:off[c + 1]], schedule=False)
+        assert r["makespan"] == ms[c] and r["n_tasks"] == nt[c], c
+
+
+@pytest.mark.parametrize("level", [0, 1, 2, 3, 4])
+def test_single_tile_every_level(level):
+    lv = np.array([[level]], np.int8)
+    for key in ("cfg0", "cfg2", "cfg1b"):
+        g = gpu_sim(W.PLATFORMS[key], 1, 2048, lv, schedule=True)
+        check_parity(W.PLATFORMS[key], 1, 2048, lv, g)
+
+
+def test_more_than_32_processors_and_four_levels():
+    rng = np.random.default_rng(3)
+    lv = rng.integers(0, 4, (24, W.base_count(5))).astype(np.int8)
+    g = gpu_sim(W.PLATFORMS["cfg4"], 5, 2048, lv, max_level=3, schedule=True)
+    check_parity(W.PLATFORMS["cfg4"], 5, 2048, lv, g)
+    spec = W.cpu_gpu_platform(60, 3)   # 63 processors, 4 memories
+    g = gpu_sim(spec, 4, 1024, lv[:, :W.base_count(4)], max_level=3, schedule=True)
+    check_parity(spec, 4, 1024, lv[:, :W.base_count(4)], g)
+
+
+def test_single_processor_and_identical_processors():
+    rng = np.random.default_rng(8)
+    lv = rng.integers(0, 3, (16, W.base_count(4))).astype(np.int8)
+    for spec in (W.single_cpu_platform(), W.PlatformSpec("id3", 1, (W.CPU_TYPE,), ((0, 0),) * 3)):
+        g = gpu_sim(spec, 4, 512, lv, max_level=2, schedule=True)
+        check_parity(spec, 4, 512, lv, g)
+
+
+def test_workspace_smaller_than_batch():
+    """Fewer arenas than candidates: warps pull candidates until done."""
+    lv = W.workload_levels("cfg1", 0, 300)
+    g = gpu_sim(W.PLATFORMS["cfg1a"], 8, 2048, lv, max_level=2, ws_cands=7)
+    check_parity(W.PLATFORMS["cfg1a"], 8, 2048, lv, g, idx=range(0, 300, 37), schedule=False)
+
+
+def test_bad_candidates_get_status_not_fault():
+    spec = W.PLATFORMS["cfg0"]
+    plat = hesp.Platform(spec)
+    nb = 10
+    lvh = np.zeros((4, nb), np.int8)
+    lvh[1, 3] = 3      # above max_level = 2
+    lvh[2, 0] = -1     # negative
+    lv = torch.from_numpy(lvh.reshape(-1).copy()).cuda()
+    a = np.zeros(6, hesp.CAND_DTYPE)
+    a["n_tiles"] = [3, 3, 3, 3, 4, 3]
+    a["b"] = [1024, 1024, 1024, 1000, 1024, 1]
+    a["level_offset"] = [0, nb, 2 * nb, 3 * nb, 0, 0]
+    lvh[0, 0] = 0
+    cands = torch.from_numpy(a.view(np.uint8).copy()).cuda()
+    ws = hesp.alloc_workspace(plat, 3, 2, 6)
+    ms, st, _ = hesp.simulate_batch(plat, cands, lv, 6, 3, 2, ws)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy().tolist()
+    # b = 1 with every level 0 is a valid (tiny) problem
+    assert st == [0, -1, -1, -1, -1, 0]
+    with pytest.raises(hesp.HespError):
+        hesp.simulate_batch(plat, cands, lv, 6, 3, 2, ws[:100])
