@@ -14,10 +14,9 @@ partitioners, dependences, performance / transfer models, FCFS + EFT-P with
 write-back caching).  This module compiles it with gcc and wraps it with
 ctypes and numpy.  ``mlp_ref`` holds the FP64 reference of the surrogate MLP.
 
-Parity status per function is listed in the module docstrings and in
-the design doc: every simulator function here is pinned by the tests in
-``tests/test_oracle_*.py`` (closed forms, hand-derived worked examples,
-brute force, invariants).
+Every simulator function here is pinned by the tests in
+``tests/test_oracle_*.py`` (closed forms, numerical execution of the DAG,
+hand-derived worked examples, brute force, invariants).
 """
 from __future__ import annotations
 

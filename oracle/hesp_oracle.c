@@ -6,9 +6,10 @@
  * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link or call
  * this file: only the tests, the smoke check and the CPU-baseline leg of the
  * benchmark use it.  It shares no source, header, table or helper with the
- * CUDA library; it is written from the paper's text and the readings listed
- * in the design doc, in the order the paper describes the method, without blocking
- * or fusion, so that it can be checked against the paper by eye.
+ * CUDA library; it is written from the paper's text (and, where the paper is
+ * silent, from the readings stated next to each rule below), in the order the
+ * paper describes the method, without blocking or fusion, so that it can be
+ * checked against the paper by eye.
  *
  * What it computes, by section of the paper:
  *   - Sec. 1.1, Fig. 1: the blocked Cholesky loop that creates the base tasks
