@@ -180,6 +180,32 @@ int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands_dev, cons
                         int16_t *proc_dev, int64_t *start_dev, int64_t *finish_dev, void *workspace_dev,
                         size_t workspace_bytes, void *stream);
 
+/* Allocation-free variant of hesp_simulate_batch.  The paper has no
+ * counterpart: it exists for callers that cannot allocate device memory when
+ * they simulate (a memory manager that owns the whole device budget, a plugin
+ * host that hands over only input and output buffers, a loop that may not
+ * call cudaMalloc).  Instead of a caller workspace it uses one fixed array of
+ * HESP_NOALLOC_SCRATCH_BYTES in the library's device memory, held by every
+ * GPU that loads the library until the process exits.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   - Arguments and results are those of hesp_simulate_batch (no workspace).
+ *   - HESP_ERR_CAPACITY (synchronously) if one candidate arena for
+ *     (max_tiles, max_level, platform memories) does not fit the array, e.g.
+ *     max_tiles 8 / max_level 2 fits (about 180 concurrent candidates), while
+ *     max_tiles 32 / max_level 3 does not.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; each
+ *     call resets what must start at zero.  Calls whose executions overlap on
+ *     the GPU (different streams, or different host threads) race on it: run
+ *     them one after another. */
+#define HESP_NOALLOC_SCRATCH_BYTES (64u << 20)
+int hesp_simulate_batch_noalloc(const hesp_platform *p, const hesp_cand *cands_dev, const int8_t *levels_dev,
+                                int64_t n_cand, int32_t max_tiles, int32_t max_level, int64_t *makespan_dev,
+                                int32_t *status_dev, int64_t *ntasks_dev, const int64_t *sched_offsets_dev,
+                                int16_t *proc_dev, int64_t *start_dev, int64_t *finish_dev, void *stream);
+
 /* --------------------------------------------------- candidate generation
  * Partition vectors drawn on the device from SplitMix64 (Steele, Lea, Flood,
  * OOPSLA 2014) used as a counter-based generator: output k of candidate c is

@@ -28,8 +28,9 @@ EXPORTS = (
     "hesp_status_string", "hesp_platform_create", "hesp_platform_set_exec_table", "hesp_platform_exec_ns",
     "hesp_platform_xfer_ns", "hesp_platform_destroy", "hesp_dag_build", "hesp_dag_n_base",
     "hesp_dag_base_tasks", "hesp_dag_count_tasks", "hesp_dag_destroy", "hesp_sim_workspace_size",
-    "hesp_simulate_batch", "hesp_generate_candidates", "hesp_generate_uneven",
+    "hesp_simulate_batch", "hesp_simulate_batch_noalloc", "hesp_generate_candidates", "hesp_generate_uneven",
 )
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 CAND_DTYPE = np.dtype([("n_tiles", "<i4"), ("b", "<i4"), ("level_offset", "<i8")])
 
@@ -83,6 +84,7 @@ def lib():
         L.hesp_dag_destroy.restype = None
         L.hesp_sim_workspace_size.argtypes = [vp, i32, i32, i64, ctypes.POINTER(sz)]
         L.hesp_simulate_batch.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.hesp_simulate_batch_noalloc.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.hesp_generate_candidates.argtypes = [i32, u64, i64, i64, i32, i32, i32, vp, vp, vp]
         L.hesp_generate_uneven.argtypes = [u64, i64, i64, vp, vp, i64, vp, vp]
         _lib = L
@@ -219,6 +221,28 @@ def simulate_batch(platform: Platform, cands, levels, n_cand, max_tiles, max_lev
                                     _ptr(makespan), _ptr(status), _ptr(ntasks), _ptr(so), _ptr(sp), _ptr(ss),
                                     _ptr(sf), _ptr(workspace), workspace.numel(), _stream(stream)),
           "hesp_simulate_batch")
+    return makespan, status, ntasks
+
+
+def simulate_batch_noalloc(platform: Platform, cands, levels, n_cand, max_tiles, max_level, makespan=None,
+                           status=None, ntasks=None, schedule=None, stream=None):
+    """hesp_simulate_batch_noalloc: same results as simulate_batch, with the
+    library's fixed device scratch array instead of a workspace (for callers
+    that cannot allocate device memory).  Calls that overlap on the GPU race
+    on that array."""
+    import torch
+    dev = levels.device
+    if makespan is None:
+        makespan = torch.empty(n_cand, dtype=torch.int64, device=dev)
+    if status is None:
+        status = torch.empty(n_cand, dtype=torch.int32, device=dev)
+    so = sp = ss = sf = None
+    if schedule is not None:
+        so, sp, ss, sf = schedule
+    check(lib().hesp_simulate_batch_noalloc(platform.h, _ptr(cands), _ptr(levels), n_cand, max_tiles, max_level,
+                                            _ptr(makespan), _ptr(status), _ptr(ntasks), _ptr(so), _ptr(sp),
+                                            _ptr(ss), _ptr(sf), _stream(stream)),
+          "hesp_simulate_batch_noalloc")
     return makespan, status, ntasks
 
 
