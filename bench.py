@@ -137,7 +137,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     nb = W.base_count(N_TILES)
-    C = N_CAND
+    C = args.candidates
     first0 = rank * C
 
     plats = [hesp.Platform(W.PLATFORMS[k]) for k in PLATS]
@@ -252,7 +252,8 @@ def run_gpu(args):
             "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / max(K, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic (seeded SplitMix64 partition vectors generated on the device)",
-            "config": dict(CONFIG, parallelism="candidates sharded across ranks (dp%d)" % world,
+            "config": dict(CONFIG, candidates_per_step=C,
+                           parallelism="candidates sharded across ranks (dp%d)" % world,
                            l2="256 MB buffer written between timed steps; per-step working set ~GBs > L2"),
             "candidates_per_s": 2 * C * world * K / t_max if t_max > 0 else None,
             "task_events": tot_events,
@@ -382,6 +383,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-sample", type=int, default=16384)
     ap.add_argument("--ref-sample", type=int, default=256)
+    ap.add_argument("--candidates", type=int, default=N_CAND,
+                    help="candidates per step (default: the workload's 65,536; smaller only for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

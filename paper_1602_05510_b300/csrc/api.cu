@@ -33,17 +33,17 @@ Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem) {
     a.Acap = ((int64_t)max_tiles * (max_tiles + 1) / 2) << (2 * max_level);
     a.Kcap = (3LL << (2 * max_level)) + 1;
     int64_t o = 0;
+    const int64_t mp = n_mem <= 1 ? 0 : (n_mem == 2 ? 2 : 4);  // int64 words of coherence state per atom
     a.off_desc = o; o = align256(o + 8 * a.Tcap);
     a.off_pending = o; o = align256(o + 2 * a.Tcap);
-    a.off_finish = o; o = align256(o + 8 * a.Tcap);
+    a.off_link = o; o = align256(o + 32 * a.Tcap);
     a.off_next = o; o = align256(o + 4 * a.Tcap);
     a.off_succoff = o; o = align256(o + 4 * (a.Tcap + 1));
     a.off_succ = o; o = align256(o + 4 * a.Ecap);
     a.off_epred = o; o = align256(o + 4 * a.Ecap);
     a.off_esucc = o; o = align256(o + 4 * a.Ecap);
     a.off_lw = o; o = align256(o + 4 * a.Acap);
-    a.off_valid = o; o = align256(o + a.Acap);
-    a.off_vfrom = o; o = align256(o + 8 * a.Acap * (n_mem > 1 ? n_mem : 0));
+    a.off_vfrom = o; o = align256(o + 8 * a.Acap * mp);
     a.off_bitmap = o; o = align256(o + 4 * ((a.Tcap + 31) / 32));
     a.off_xt = o; o = align256(o + 8 * a.Kcap);
     a.slot_bytes = o;
@@ -70,13 +70,13 @@ static DevPlatform dev_platform(const hesp_platform *p) {
 }
 
 // Resident warps of the simulation kernel on the current device.
-int sim_slots_for(const hesp_platform *p, int64_t *resident_warps) {
+int sim_slots_for(const hesp_platform *p, const Arena &ar, int64_t *resident_warps) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return HESP_ERR_CUDA;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HESP_ERR_CUDA;
     int blocks = 0, threads = 0;
-    int rc = sim_kernel_occupancy(p->n_mem, p->n_procs, &blocks, &threads);
+    int rc = sim_kernel_occupancy(p->n_mem, p->n_procs, ar.Tcap, &blocks, &threads);
     if (rc) return rc;
     if (blocks < 1) blocks = 1;
     *resident_warps = (int64_t)sms * blocks * (threads / 32);
@@ -289,7 +289,7 @@ int hesp_sim_workspace_size(const hesp_platform *p, int32_t max_tiles, int32_t m
         return HESP_ERR_UNSUPPORTED;
     const Arena ar = make_arena(max_tiles, max_level, p->n_mem);
     int64_t resident = 0;
-    const int rc = sim_slots_for(p, &resident);
+    const int rc = sim_slots_for(p, ar, &resident);
     if (rc) return rc;
     int64_t slots = n_cand < resident ? n_cand : resident;
     if (slots < 1) slots = 1;
@@ -313,7 +313,7 @@ int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands, const in
     const Arena ar = make_arena(max_tiles, max_level, p->n_mem);
     if ((int64_t)ws_bytes < kWsHeaderBytes + ar.slot_bytes) return HESP_ERR_ARG;
     int64_t resident = 0;
-    int rc = sim_slots_for(p, &resident);
+    int rc = sim_slots_for(p, ar, &resident);
     if (rc) return rc;
     int64_t slots = ((int64_t)ws_bytes - kWsHeaderBytes) / ar.slot_bytes;
     if (slots > resident) slots = resident;

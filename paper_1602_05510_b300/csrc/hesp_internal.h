@@ -44,8 +44,8 @@ struct Arena {
     int64_t Ecap;  // dependence edges
     int64_t Acap;  // atoms
     int64_t Kcap;  // transfer-table entries (atoms per task + 1)
-    int64_t off_desc, off_pending, off_finish, off_next, off_succoff, off_succ, off_epred, off_esucc, off_lw,
-        off_valid, off_vfrom, off_bitmap, off_xt;
+    int64_t off_desc, off_pending, off_link, off_next, off_succoff, off_succ, off_epred, off_esucc, off_lw,
+        off_vfrom, off_bitmap, off_xt;
 };
 
 // Header at the start of the workspace.
@@ -60,12 +60,13 @@ int64_t tasks_uniform(int64_t n, int level);  // tasks when every base task is s
 int64_t regions_uniform(int64_t n, int level); // sum over those tasks of their region count
 Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem);
 
-int sim_slots_for(const hesp_platform *p, int64_t *resident_warps);  // device resident warp count
+int sim_slots_for(const hesp_platform *p, const Arena &ar, int64_t *resident_warps);  // device resident warps
 int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, int64_t n_slots,
                const hesp_cand *cands, const int8_t *levels, int64_t n_cand, int32_t max_tiles, int32_t max_level,
                int64_t *makespan, int32_t *status, int64_t *ntasks, const int64_t *sched_off, int16_t *sproc,
                int64_t *sstart, int64_t *sfinish, char *ws, cudaStream_t stream);
-int sim_kernel_occupancy(int n_mem, int n_procs, int *blocks_per_sm, int *threads_per_block);
+int sim_kernel_occupancy(int n_mem, int n_procs, int64_t Tcap, int *blocks_per_sm, int *threads_per_block);
+int sim_bitmap_smem_words(int64_t Tcap);
 
 int launch_generate(int32_t kind, uint64_t seed, int64_t first, int64_t n_cand, int32_t n_tiles, int32_t b,
                     int32_t n_levels, hesp_cand *cands, int8_t *levels, cudaStream_t stream);

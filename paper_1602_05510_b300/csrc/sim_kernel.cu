@@ -199,20 +199,16 @@ __device__ __forceinline__ uint64_t warp_min_u64(uint64_t k) {
     return ((uint64_t)hmin << 32) | lmin;
 }
 
-struct SimPtrs {
-    uint64_t *desc;
-    uint16_t *pending;
-    int64_t *finish;
-    int32_t *mark;  // aliases finish during dependence derivation
-    int32_t *next;  // successor counts, then cursors, then per-processor FIFO links
-    int32_t *succoff;
-    int32_t *succ;
-    int32_t *epred, *esucc;
-    int32_t *lw;
-    uint8_t *valid;
-    int64_t *vfrom;
-    uint32_t *bitmap;
-    int64_t *xt;
+// Per-processor FIFO of tasks in flight, threaded through the tasks.  For a
+// task in flight: its successor in the FIFO and that successor's finish time,
+// and the range of its own successor list, all read together when it
+// completes.
+struct __align__(16) Link {
+    int32_t next;
+    int32_t e0, e1;  // successor list succ[e0 .. e1)
+    int32_t pad;
+    int64_t nfin;
+    int64_t pad2;
 };
 
 struct KArgs {
@@ -229,88 +225,130 @@ struct KArgs {
     char *ws;
     Arena ar;
     int64_t n_slots;
+    int32_t bm_smem_words;  // > 0: the released-task bitmap lives in shared memory
 };
 
+template <typename T>
+__device__ __forceinline__ T *at(char *base, int64_t off) {
+    return reinterpret_cast<T *>(base + off);
+}
+
+// Coherence state of one atom: for each memory the time from which its copy
+// is usable there, or -1 if the memory holds no valid copy.  Stored as MP
+// int64 per atom (MP = 2 for two memories, 4 for three or four).
 template <int M>
-struct AtomAcc {
-    unsigned amax[M];   // latest (valid copy usable time - t) per memory, clamped to 0
-    int cnt[M][M];      // atoms missing in m fetched from s
+struct AtomState {
+    static constexpr int MP = M <= 2 ? 2 : 4;
+    int64_t v[MP];
+    __device__ __forceinline__ void load(const int64_t *p) {
+        const longlong2 a = *reinterpret_cast<const longlong2 *>(p);
+        v[0] = a.x;
+        v[1] = a.y;
+        if (MP == 4) {
+            const longlong2 b = *reinterpret_cast<const longlong2 *>(p + 2);
+            v[2] = b.x;
+            v[3] = b.y;
+        }
+    }
+    // lowest memory holding a copy usable at t, or -1
+    __device__ __forceinline__ int source(int64_t t) const {
+        int src = -1;
+#pragma unroll
+        for (int s = M - 1; s >= 0; --s)
+            if (v[s] >= 0 && v[s] <= t) src = s;
+        return src;
+    }
 };
 
-// Schedule task j at time t (EFT-P with data-ready times per memory).
-// Returns false on an internal consistency failure.
+// Packed per-(destination m, source s != m) atom counts: counter q =
+// m * (M - 1) + (s < m ? s : s - 1), 16 bits each, two per word.
+template <int M>
+struct Counts {
+    static constexpr int NQ = M * (M - 1);
+    static constexpr int NW = (NQ + 1) / 2;
+    unsigned w[NW > 0 ? NW : 1];
+    __device__ __forceinline__ static int q_of(int m, int s) { return m * (M - 1) + (s < m ? s : s - 1); }
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int k = 0; k < (NW > 0 ? NW : 1); ++k) w[k] = 0;
+    }
+    __device__ __forceinline__ void add(int m, int src) {
+#pragma unroll
+        for (int s = 0; s < M; ++s) {
+            if (s == m) continue;
+            const int q = q_of(m, s);
+            if (s == src) w[q >> 1] += 1u << (16 * (q & 1));
+        }
+    }
+    __device__ __forceinline__ unsigned get(int m, int s) const {
+        const int q = q_of(m, s);
+        return (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+    }
+};
+
+// Schedule task j at time t: data-ready time per memory, EFT over the
+// processors (ties to the lowest id), commit of the coherence state, append
+// to the chosen processor's FIFO.  Clears `ok` on an internal inconsistency.
 template <int M, int NS>
-__device__ __forceinline__ bool schedule_task(int j, int64_t t, const SimPtrs &P, int Lc, int lb_b, int lane,
-                                               const int64_t *s_exec, const int8_t *s_pmem, const int8_t *s_ptype,
-                                               int n_types, int pm[NS], int pt[NS], bool pv[NS], int64_t avail[NS],
-                                               int head[NS], int tail[NS], int64_t hfin[NS], int64_t &mk,
-                                               int16_t *sproc, int64_t *sstart, int64_t *sfinish) {
-    const uint64_t d = P.desc[j];
+__device__ __forceinline__ void schedule_task(int j, int64_t t, char *base, const KArgs &a, int Lc, int lb_b,
+                                              int lane, const int64_t *s_exec, const int8_t *s_pmem,
+                                              const int8_t *s_ptype, const int pm[NS], const int pt[NS],
+                                              const bool pv[NS], int64_t avail[NS], int head[NS], int tail[NS],
+                                              int64_t hfin[NS], int64_t &mk, bool &ok, int64_t sched_base) {
+    const uint64_t d = at<uint64_t>(base, a.ar.off_desc)[j];
+    const int32_t *const succoff = at<int32_t>(base, a.ar.off_succoff);
+    const int se0 = succoff[j], se1 = succoff[j + 1];  // kept with the task while it is in flight
     const int op = (int)(d & 3);
     const int lvl = (int)((d >> 2) & 7);
     const int nr = nreg_of(op);
     const int sh = 2 * (Lc - lvl);
-    const int na = 1 << sh;
     const int tot = nr << sh;
     const int lb = lb_b - lvl;
-    bool ok = true;
+    constexpr int MP = AtomState<M>::MP;
+    int64_t *vfrom = at<int64_t>(base, a.ar.off_vfrom);
+    const int64_t *xt = at<int64_t>(base, a.ar.off_xt);
 
     int64_t drt_off[M];
-    int64_t arr_off[M][M];
+    Counts<M> cnt;
+    cnt.clear();
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-        drt_off[m] = 0;
-#pragma unroll
-        for (int s = 0; s < M; ++s) arr_off[m][s] = 0;
-    }
+    for (int m = 0; m < M; ++m) drt_off[m] = 0;
     if (M > 1) {
-        AtomAcc<M> acc;
+        unsigned amax[M];
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            acc.amax[m] = 0;
-#pragma unroll
-            for (int s = 0; s < M; ++s) acc.cnt[m][s] = 0;
-        }
+        for (int m = 0; m < M; ++m) amax[m] = 0;
         for (int i0 = 0; i0 < tot; i0 += 32) {
-            int i = i0 + lane;
+            const int i = i0 + lane;
             if (i < tot) {
-                uint32_t x = desc_atom(d, i >> sh) + (uint32_t)(i & (na - 1));
-                unsigned v = P.valid[x];
-                int64_t vf[M];
-#pragma unroll
-                for (int m = 0; m < M; ++m) vf[m] = ((v >> m) & 1u) ? P.vfrom[(int64_t)x * M + m] : kInf;
-                int src = -1;
-#pragma unroll
-                for (int s = M - 1; s >= 0; --s)
-                    if (vf[s] <= t) src = s;
+                const uint32_t x = desc_atom(d, i >> sh) + (uint32_t)(i & ((1 << sh) - 1));
+                AtomState<M> st;
+                st.load(vfrom + (int64_t)x * MP);
+                const int src = st.source(t);
 #pragma unroll
                 for (int m = 0; m < M; ++m) {
-                    if ((v >> m) & 1u) {
-                        int64_t dd = vf[m] - t;
+                    if (st.v[m] >= 0) {
+                        const int64_t dd = st.v[m] - t;
                         if (dd > 0) {
-                            if (dd > 0x7FFFFFFFLL) ok = false;
-                            acc.amax[m] = max(acc.amax[m], (unsigned)min(dd, (int64_t)0x7FFFFFFF));
+                            ok &= dd <= 0x7FFFFFFFLL;
+                            amax[m] = max(amax[m], (unsigned)min(dd, (int64_t)0x7FFFFFFF));
                         }
                     } else {
-                        if (src < 0) ok = false;
-#pragma unroll
-                        for (int s = 0; s < M; ++s)
-                            if (s == src) acc.cnt[m][s] += 1;
+                        ok &= src >= 0;
+                        cnt.add(m, src);
                     }
                 }
             }
         }
 #pragma unroll
+        for (int k = 0; k < Counts<M>::NW; ++k) cnt.w[k] = __reduce_add_sync(FULL, cnt.w[k]);
+#pragma unroll
         for (int m = 0; m < M; ++m) {
-            int64_t off = (int64_t)__reduce_max_sync(FULL, acc.amax[m]);
+            int64_t off = (int64_t)__reduce_max_sync(FULL, amax[m]);
 #pragma unroll
             for (int s = 0; s < M; ++s) {
                 if (s == m) continue;
-                int c = (int)__reduce_add_sync(FULL, (unsigned)acc.cnt[m][s]);
-                if (c > 0) {
-                    arr_off[m][s] = P.xt[c];
-                    off = max(off, arr_off[m][s]);
-                }
+                const unsigned c = cnt.get(m, s);
+                if (c > 0) off = max(off, xt[c]);
             }
             drt_off[m] = off;
         }
@@ -320,7 +358,7 @@ __device__ __forceinline__ bool schedule_task(int j, int64_t t, const SimPtrs &P
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         if (pv[s]) {
-            int64_t ex = s_exec[(op * HESP_MAX_TYPES + pt[s]) * HESP_LB + lb];
+            const int64_t ex = s_exec[(op * HESP_MAX_TYPES + pt[s]) * HESP_LB + lb];
             int64_t ready = max(t, avail[s]);
             if (M > 1) {
                 int64_t off = 0;
@@ -329,48 +367,58 @@ __device__ __forceinline__ bool schedule_task(int j, int64_t t, const SimPtrs &P
                     if (pm[s] == m) off = drt_off[m];
                 ready = max(ready, t + off);
             }
-            int64_t e = ready + ex;
-            uint64_t k = ((uint64_t)e << 6) | (uint64_t)(lane + 32 * s);
-            if (ex < 0 || e >= (1ll << 57)) ok = false;
-            key = min(key, k);
+            const int64_t e = ready + ex;
+            ok &= ex >= 0 && e < (1ll << 57);
+            key = min(key, ((uint64_t)e << 6) | (uint64_t)(lane + 32 * s));
         }
     }
     key = warp_min_u64(key);
     const int pbest = (int)(key & 63);
     const int64_t eft = (int64_t)(key >> 6);
     const int ms = s_pmem[pbest];
-    const int64_t exb = s_exec[(op * HESP_MAX_TYPES + s_ptype[pbest]) * HESP_LB + lb];
 
     if (M > 1) {
         for (int i0 = 0; i0 < tot; i0 += 32) {
-            int i = i0 + lane;
+            const int i = i0 + lane;
             if (i < tot) {
-                int r = i >> sh;
-                uint32_t x = desc_atom(d, r) + (uint32_t)(i & (na - 1));
+                const int r = i >> sh;
+                const uint32_t x = desc_atom(d, r) + (uint32_t)(i & ((1 << sh) - 1));
+                int64_t *px = vfrom + (int64_t)x * MP;
                 if (r == nr - 1) {
-                    P.valid[x] = (uint8_t)(1u << ms);
-                    P.vfrom[(int64_t)x * M + ms] = eft;
+                    // written block: valid only in the chosen memory, from the finish time
+                    longlong2 w0, w1;
+                    w0.x = ms == 0 ? eft : -1;
+                    w0.y = ms == 1 ? eft : -1;
+                    *reinterpret_cast<longlong2 *>(px) = w0;
+                    if (MP == 4) {
+                        w1.x = ms == 2 ? eft : -1;
+                        w1.y = ms == 3 ? eft : -1;
+                        *reinterpret_cast<longlong2 *>(px + 2) = w1;
+                    }
                 } else {
-                    unsigned v = P.valid[x];
-                    if (!((v >> ms) & 1u)) {
-                        int src = -1;
+                    AtomState<M> st;
+                    st.load(px);
+                    int64_t vm = -1;
 #pragma unroll
-                        for (int s = M - 1; s >= 0; --s)
-                            if (((v >> s) & 1u) && P.vfrom[(int64_t)x * M + s] <= t) src = s;
-                        int64_t ao = 0;
+                    for (int m = 0; m < M; ++m)
+                        if (m == ms) vm = st.v[m];
+                    if (vm < 0) {
+                        // fetched: valid in the chosen memory from its message's arrival
+                        const int src = st.source(t);
+                        unsigned c = 0;
 #pragma unroll
                         for (int m = 0; m < M; ++m)
 #pragma unroll
                             for (int s = 0; s < M; ++s)
-                                if (m == ms && s == src) ao = arr_off[m][s];
-                        P.valid[x] = (uint8_t)(v | (1u << ms));
-                        P.vfrom[(int64_t)x * M + ms] = t + ao;
+                                if (m != s && m == ms && s == src) c = cnt.get(m, s);
+                        px[ms] = t + xt[c];
                     }
                 }
             }
         }
     }
     if (lane == (pbest & 31)) {
+        Link *link = at<Link>(base, a.ar.off_link);
         const int s = pbest >> 5;
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
@@ -380,31 +428,34 @@ __device__ __forceinline__ bool schedule_task(int j, int64_t t, const SimPtrs &P
                     head[q] = j;
                     hfin[q] = eft;
                 } else {
-                    P.next[tail[q]] = j;
+                    link[tail[q]].next = j;
+                    link[tail[q]].nfin = eft;
                 }
+                int4 lj;
+                lj.x = -1;
+                lj.y = se0;
+                lj.z = se1;
+                lj.w = 0;
+                *reinterpret_cast<int4 *>(&link[j]) = lj;
                 tail[q] = j;
             }
         }
     }
-    if (lane == 0) {
-        P.finish[j] = eft;
-        P.next[j] = -1;
-        if (sproc) {
-            sproc[j] = (int16_t)pbest;
-            sstart[j] = eft - exb;
-            sfinish[j] = eft;
-        }
+    if (lane == 0 && sched_base >= 0) {
+        a.sproc[sched_base + j] = (int16_t)pbest;
+        a.sstart[sched_base + j] = eft - s_exec[(op * HESP_MAX_TYPES + s_ptype[pbest]) * HESP_LB + lb];
+        a.sfinish[sched_base + j] = eft;
     }
     mk = max(mk, eft);
     __syncwarp();
-    return __all_sync(FULL, ok);
 }
 
 template <int M, int NS>
-__global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsigned long long *work_counter) {
+__global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, unsigned long long *work_counter) {
     __shared__ int64_t s_exec[4 * HESP_MAX_TYPES * HESP_LB];
     __shared__ int8_t s_pmem[HESP_MAX_PROCS];
     __shared__ int8_t s_ptype[HESP_MAX_PROCS];
+    extern __shared__ uint32_t s_bitmap[];
     for (int i = threadIdx.x; i < 4 * HESP_MAX_TYPES * HESP_LB; i += blockDim.x) s_exec[i] = pl.exec[i];
     for (int i = threadIdx.x; i < HESP_MAX_PROCS; i += blockDim.x) {
         s_pmem[i] = pl.proc_mem[i];
@@ -415,32 +466,19 @@ __global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsig
     const int lane = threadIdx.x & 31;
     const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (slot >= a.n_slots) return;  // whole warp
-    char *base = a.ws + slot * a.ar.slot_bytes;
-    SimPtrs P;
-    P.desc = (uint64_t *)(base + a.ar.off_desc);
-    P.pending = (uint16_t *)(base + a.ar.off_pending);
-    P.finish = (int64_t *)(base + a.ar.off_finish);
-    P.mark = (int32_t *)(base + a.ar.off_finish);
-    P.next = (int32_t *)(base + a.ar.off_next);
-    P.succoff = (int32_t *)(base + a.ar.off_succoff);
-    P.succ = (int32_t *)(base + a.ar.off_succ);
-    P.epred = (int32_t *)(base + a.ar.off_epred);
-    P.esucc = (int32_t *)(base + a.ar.off_esucc);
-    P.lw = (int32_t *)(base + a.ar.off_lw);
-    P.valid = (uint8_t *)(base + a.ar.off_valid);
-    P.vfrom = (int64_t *)(base + a.ar.off_vfrom);
-    P.bitmap = (uint32_t *)(base + a.ar.off_bitmap);
-    P.xt = (int64_t *)(base + a.ar.off_xt);
+    char *const base = a.ws + slot * a.ar.slot_bytes;
+    uint32_t *const bm = a.bm_smem_words > 0 ? s_bitmap + (threadIdx.x >> 5) * a.bm_smem_words
+                                             : at<uint32_t>(base, a.ar.off_bitmap);
+    constexpr int MP = AtomState<M>::MP;
 
-    const int nprocs = pl.n_procs;
     int pm[NS], pt[NS];
     bool pv[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        int p = lane + 32 * s;
-        pv[s] = p < nprocs;
-        pm[s] = pv[s] ? pl.proc_mem[p] : 0;
-        pt[s] = pv[s] ? pl.proc_type[p] : 0;
+        const int p = lane + 32 * s;
+        pv[s] = p < pl.n_procs;
+        pm[s] = pv[s] ? s_pmem[p] : 0;
+        pt[s] = pv[s] ? s_ptype[p] : 0;
     }
 
     for (;;) {
@@ -463,7 +501,7 @@ __global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsig
         int lmax = 0;
         bool badl = false;
         for (int64_t t0 = lane; t0 < nb; t0 += 32) {
-            int l = a.levels[loff + t0];
+            const int l = a.levels[loff + t0];
             lmax = max(lmax, l);
             badl |= (l < 0 || l > a.max_level);
         }
@@ -479,19 +517,20 @@ __global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsig
         if (status == HESP_OK) {
             bool bad = false;
             for (int e = lane; e < 4 * HESP_MAX_TYPES * (Lc + 1); e += 32) {
-                int op = e / (HESP_MAX_TYPES * (Lc + 1));
-                int rem = e % (HESP_MAX_TYPES * (Lc + 1));
-                int ty = rem / (Lc + 1), l = rem % (Lc + 1);
+                const int op = e / (HESP_MAX_TYPES * (Lc + 1));
+                const int rem = e % (HESP_MAX_TYPES * (Lc + 1));
+                const int ty = rem / (Lc + 1), l = rem % (Lc + 1);
                 if (ty < pl.n_types && s_exec[(op * HESP_MAX_TYPES + ty) * HESP_LB + lb_b - l] < 0) bad = true;
             }
             if (__any_sync(FULL, bad)) status = HESP_ERR_ARG;
         }
 
         // ---- 1. count and expand tasks
+        uint64_t *const desc = at<uint64_t>(base, a.ar.off_desc);
         if (status == HESP_OK) {
             int64_t tcount = 0;
             for (int64_t t0 = 0; t0 < nb; t0 += 32) {
-                int64_t t = t0 + lane;
+                const int64_t t = t0 + lane;
                 int cnt = 0;
                 if (t < nb) {
                     int op, K, I, J;
@@ -501,12 +540,13 @@ __global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsig
                 tcount += __reduce_add_sync(FULL, (unsigned)cnt);
             }
             T = tcount;
-            if (T > a.ar.Tcap || T >= INT_MAX / 2) status = HESP_ERR_CAPACITY;
+            if (T > a.ar.Tcap || T >= INT_MAX / 2 || (a.bm_smem_words > 0 && ((T + 31) >> 5) > a.bm_smem_words))
+                status = HESP_ERR_CAPACITY;
         }
         if (status == HESP_OK) {
             int64_t off = 0;
             for (int64_t t0 = 0; t0 < nb; t0 += 32) {
-                int64_t t = t0 + lane;
+                const int64_t t = t0 + lane;
                 int op = 0, K = 0, I = 0, J = 0, l = 0, cnt = 0;
                 if (t < nb) {
                     decode_base(n, t, op, K, I, J);
@@ -522,7 +562,7 @@ __global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsig
                     int pos = 0;
 #pragma unroll
                     for (int step = 16; step >= 1; step >>= 1) {
-                        int v = __shfl_sync(FULL, incl, pos + step - 1);
+                        const int v = __shfl_sync(FULL, incl, pos + step - 1);
                         if (v <= g) pos += step;
                     }
                     const int owner = min(pos, 31);
@@ -532,7 +572,7 @@ __global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsig
                     const int oI = __shfl_sync(FULL, I, owner);
                     const int oJ = __shfl_sync(FULL, J, owner);
                     const int ol = __shfl_sync(FULL, l, owner);
-                    if (g < total) P.desc[off + g] = decode_sub(oop, oK, oI, oJ, ol, q, Lc, n);
+                    if (g < total) desc[off + g] = decode_sub(oop, oK, oI, oJ, ol, q, Lc, n);
                 }
                 off += total;
             }
@@ -542,48 +582,59 @@ __global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsig
         // ---- 2. dependences from per-atom last writers
         int64_t E = 0;
         if (status == HESP_OK) {
-            for (int64_t x = lane; x < A; x += 32) P.lw[x] = -1;
+            int32_t *const lw = at<int32_t>(base, a.ar.off_lw);
+            int32_t *const mark = at<int32_t>(base, a.ar.off_link);  // FIFO links are not in use yet
+            int32_t *const scnt = at<int32_t>(base, a.ar.off_next);
+            int32_t *const epred = at<int32_t>(base, a.ar.off_epred);
+            int32_t *const esucc = at<int32_t>(base, a.ar.off_esucc);
+            uint16_t *const pending = at<uint16_t>(base, a.ar.off_pending);
+            for (int64_t x = lane; x < A; x += 32) lw[x] = -1;
             for (int64_t j = lane; j < T; j += 32) {
-                P.mark[j] = -1;
-                P.next[j] = 0;
+                mark[j] = -1;
+                scnt[j] = 0;
             }
             __syncwarp();
             const unsigned lt_mask = (1u << lane) - 1u;
+            uint64_t dn = T > 0 ? desc[0] : 0;
             for (int j = 0; j < (int)T; ++j) {
-                const uint64_t d = P.desc[j];
+                const uint64_t d = dn;
+                if (j + 1 < (int)T) dn = desc[j + 1];  // prefetch
                 const int op = (int)(d & 3);
                 const int lvl = (int)((d >> 2) & 7);
                 const int nr = nreg_of(op);
                 const int sh = 2 * (Lc - lvl);
                 const int na = 1 << sh;
                 const int tot = nr << sh;
+                // a task whose atoms fit one round is deduplicated inside the
+                // warp; larger ones also use the per-task mark across rounds
+                const bool multi = tot > 32;
                 int cnt = 0;
                 for (int i0 = 0; i0 < tot; i0 += 32) {
                     const int i = i0 + lane;
                     int w = -1;
-                    if (i < tot) w = P.lw[desc_atom(d, i >> sh) + (uint32_t)(i & (na - 1))];
+                    if (i < tot) w = lw[desc_atom(d, i >> sh) + (uint32_t)(i & (na - 1))];
                     const unsigned grp = __match_any_sync(FULL, w);
-                    bool isnew = false;
-                    if (lane == __ffs(grp) - 1 && w >= 0 && P.mark[w] != j) {
-                        P.mark[w] = j;
-                        isnew = true;
+                    bool isnew = lane == __ffs(grp) - 1 && w >= 0;
+                    if (multi && isnew) {
+                        if (mark[w] == j) isnew = false;
+                        else mark[w] = j;
                     }
                     const unsigned nm = __ballot_sync(FULL, isnew);
                     if (isnew) {
                         const int64_t e = E + cnt + __popc(nm & lt_mask);
                         if (e < a.ar.Ecap) {
-                            P.epred[e] = w;
-                            P.esucc[e] = j;
+                            epred[e] = w;
+                            esucc[e] = j;
                         }
-                        P.next[w] += 1;
+                        atomicAdd(&scnt[w], 1);
                     }
                     cnt += __popc(nm);
-                    __syncwarp();
+                    if (multi) __syncwarp();
                 }
-                if (lane == 0) P.pending[j] = (uint16_t)cnt;
+                if (lane == 0) pending[j] = (uint16_t)cnt;
                 E += cnt;
                 const uint32_t xw = desc_atom(d, nr - 1);
-                for (int i = lane; i < na; i += 32) P.lw[xw + i] = j;
+                for (int i = lane; i < na; i += 32) lw[xw + i] = j;
                 __syncwarp();
             }
             if (E > a.ar.Ecap) status = HESP_ERR_CAPACITY;
@@ -591,40 +642,54 @@ __global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsig
 
         // ---- 3. successor lists (CSR)
         if (status == HESP_OK) {
+            int32_t *const scnt = at<int32_t>(base, a.ar.off_next);
+            int32_t *const succoff = at<int32_t>(base, a.ar.off_succoff);
+            int32_t *const succ = at<int32_t>(base, a.ar.off_succ);
+            const int32_t *const epred = at<int32_t>(base, a.ar.off_epred);
+            const int32_t *const esucc = at<int32_t>(base, a.ar.off_esucc);
             int run = 0;
             for (int64_t j0 = 0; j0 < T; j0 += 32) {
                 const int64_t j = j0 + lane;
-                const int v = j < T ? P.next[j] : 0;
+                const int v = j < T ? scnt[j] : 0;
                 const int incl = warp_incl_scan(v, lane);
                 if (j < T) {
-                    P.succoff[j] = run + incl - v;
-                    P.next[j] = run + incl - v;
+                    succoff[j] = run + incl - v;
+                    scnt[j] = run + incl - v;
                 }
                 run += __shfl_sync(FULL, incl, 31);
             }
-            if (lane == 0) P.succoff[T] = run;
+            if (lane == 0) succoff[T] = run;
             __syncwarp();
             for (int64_t e = lane; e < E; e += 32) {
-                const int w = P.epred[e];
-                const int pos = atomicAdd(&P.next[w], 1);
-                P.succ[pos] = P.esucc[e];
+                const int pos = atomicAdd(&scnt[epred[e]], 1);
+                succ[pos] = esucc[e];
             }
             __syncwarp();
         }
 
         // ---- 4. event-driven FCFS + EFT-P simulation
         if (status == HESP_OK) {
+            uint16_t *const pending = at<uint16_t>(base, a.ar.off_pending);
             if (M > 1) {
+                int64_t *const vfrom = at<int64_t>(base, a.ar.off_vfrom);
                 for (int64_t x = lane; x < A; x += 32) {
-                    P.valid[x] = 1;  // every atom valid in host memory from time 0
-                    P.vfrom[x * M + 0] = 0;
+                    // every atom valid in host memory from time 0, nowhere else
+                    longlong2 v0;
+                    v0.x = 0;
+                    v0.y = -1;
+                    *reinterpret_cast<longlong2 *>(vfrom + x * MP) = v0;
+                    if (MP == 4) {
+                        v0.x = -1;
+                        *reinterpret_cast<longlong2 *>(vfrom + x * MP + 2) = v0;
+                    }
                 }
                 // transfer time of k atoms (k * (b >> Lc)^2 elements)
+                int64_t *const xt = at<int64_t>(base, a.ar.off_xt);
                 const int64_t ae = (int64_t)(b >> Lc) * (int64_t)(b >> Lc);
                 const int kmax = 3 << (2 * Lc);
                 for (int k = lane; k <= kmax; k += 32) {
                     const int64_t bytes = (int64_t)k * ae * pl.bpe;
-                    P.xt[k] = k == 0 ? 0 : pl.lat + (bytes + pl.bw - 1) / pl.bw;
+                    xt[k] = k == 0 ? 0 : pl.lat + (bytes + pl.bw - 1) / pl.bw;
                 }
             }
             const int W = (int)((T + 31) >> 5);
@@ -633,9 +698,9 @@ __global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsig
                 // word w0 + q of the bitmap is built by a ballot over its 32 tasks
                 for (int q = 0; q < 32 && w0 + q < W; ++q) {
                     const int64_t j = (int64_t)(w0 + q) * 32 + lane;
-                    const bool rel = j < T && P.pending[j] == 0;
+                    const bool rel = j < T && pending[j] == 0;
                     const unsigned bits = __ballot_sync(FULL, rel);
-                    if (lane == 0) P.bitmap[w0 + q] = bits;
+                    if (lane == 0) bm[w0 + q] = bits;
                     if (bits) {
                         wlo = min(wlo, w0 + q);
                         whi = max(whi, w0 + q);
@@ -653,14 +718,9 @@ __global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsig
                 head[s] = -1;
                 tail[s] = -1;
             }
-            int16_t *sproc = nullptr;
-            int64_t *sstart = nullptr, *sfinish = nullptr;
-            if (a.sched_off) {
-                const int64_t so = a.sched_off[c];
-                sproc = a.sproc + so;
-                sstart = a.sstart + so;
-                sfinish = a.sfinish + so;
-            }
+            const int64_t sched_base = a.sched_off ? a.sched_off[c] : -1;
+            const int32_t *const succ = at<int32_t>(base, a.ar.off_succ);
+            const Link *const link = at<Link>(base, a.ar.off_link);
             int64_t t = 0;
             int64_t iters = 0;
             const int64_t iter_cap = 4 * T + 64;
@@ -668,30 +728,29 @@ __global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsig
             bool ok = true;
             for (;;) {
                 // schedule every released task in ascending id
-                for (int w0 = wlo; w0 <= whi && ok; w0 += 32) {
+                for (int w0 = wlo; w0 <= whi; w0 += 32) {
                     const int w = w0 + lane;
                     uint32_t bits = 0;
                     if (w <= whi) {
-                        bits = P.bitmap[w];
-                        if (bits) P.bitmap[w] = 0;
+                        bits = bm[w];
+                        if (bits) bm[w] = 0;
                     }
                     unsigned nz = __ballot_sync(FULL, bits != 0);
-                    while (nz && ok) {
+                    while (nz) {
                         const int src = __ffs(nz) - 1;
                         nz &= nz - 1;
                         uint32_t wb = __shfl_sync(FULL, bits, src);
                         const int jb = (w0 + src) * 32;
-                        while (wb && ok) {
+                        while (wb) {
                             const int bit = __ffs(wb) - 1;
                             wb &= wb - 1;
-                            ok = schedule_task<M, NS>(jb + bit, t, P, Lc, lb_b, lane, s_exec, s_pmem, s_ptype,
-                                                      pl.n_types, pm, pt, pv, avail, head, tail, hfin, mk, sproc,
-                                                      sstart, sfinish);
+                            schedule_task<M, NS>(jb + bit, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt,
+                                                 pv, avail, head, tail, hfin, mk, ok, sched_base);
                             ++scheduled;
                         }
                     }
                 }
-                if (!ok) {
+                if (!__all_sync(FULL, ok)) {
                     status = HESP_ERR_STATE;
                     break;
                 }
@@ -715,14 +774,20 @@ __global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsig
                         const int src = __ffs(cm) - 1;
                         cm &= cm - 1;
                         const int i = __shfl_sync(FULL, head[s], src);
-                        const int e0 = P.succoff[i], e1 = P.succoff[i + 1];
+                        int4 l0 = make_int4(0, 0, 0, 0);
+                        int64_t lnfin = 0;
+                        if (lane == src) {
+                            l0 = *reinterpret_cast<const int4 *>(&link[i]);
+                            lnfin = link[i].nfin;
+                        }
+                        const int e0 = __shfl_sync(FULL, l0.y, src), e1 = __shfl_sync(FULL, l0.z, src);
                         int lo = INT_MAX, hi = -1;
                         for (int e = e0 + lane; e < e1; e += 32) {
-                            const int sj = P.succ[e];
-                            const int pvv = (int)P.pending[sj] - 1;
-                            P.pending[sj] = (uint16_t)pvv;
+                            const int sj = succ[e];
+                            const int pvv = (int)pending[sj] - 1;
+                            pending[sj] = (uint16_t)pvv;
                             if (pvv == 0) {
-                                atomicOr(&P.bitmap[sj >> 5], 1u << (sj & 31));
+                                atomicOr(&bm[sj >> 5], 1u << (sj & 31));
                                 lo = min(lo, sj >> 5);
                                 hi = max(hi, sj >> 5);
                             }
@@ -730,10 +795,9 @@ __global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsig
                         wlo = min(wlo, __reduce_min_sync(FULL, lo));
                         whi = max(whi, __reduce_max_sync(FULL, hi));
                         if (lane == src) {
-                            const int nx = P.next[i];
-                            head[s] = nx;
-                            hfin[s] = nx >= 0 ? P.finish[nx] : kInf;
-                            if (nx < 0) tail[s] = -1;
+                            head[s] = l0.x;
+                            hfin[s] = l0.x >= 0 ? lnfin : kInf;
+                            if (l0.x < 0) tail[s] = -1;
                         }
                         __syncwarp();
                     }
@@ -747,25 +811,45 @@ __global__ void __launch_bounds__(256) sim_kernel(DevPlatform pl, KArgs a, unsig
             a.makespan[c] = status == HESP_OK ? mk : -1;
             if (a.ntasks) a.ntasks[c] = T;
         }
+        __syncwarp();
     }
 }
 
 template <int M, int NS>
-void occupancy_of(int *blocks) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, sim_kernel<M, NS>, 256, 0);
+void occupancy_of(int *blocks, size_t smem) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, sim_kernel<M, NS>, 256, smem);
+}
+
+template <int M, int NS>
+void set_smem_attr(size_t smem) {
+    cudaFuncSetAttribute(sim_kernel<M, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 }  // namespace
 
-int sim_kernel_occupancy(int n_mem, int n_procs, int *blocks_per_sm, int *threads_per_block) {
+// Shared-memory bitmap words per warp for a workspace sized for Tcap tasks
+// (0 = the bitmap stays in the arena): up to 2048 words (64 Ki tasks).
+int sim_bitmap_smem_words(int64_t Tcap) {
+    const int64_t w = (Tcap + 31) / 32;
+    return w <= 2048 ? (int)w : 0;
+}
+
+int sim_kernel_occupancy(int n_mem, int n_procs, int64_t Tcap, int *blocks_per_sm, int *threads_per_block) {
     *threads_per_block = 256;
+    const size_t smem = (size_t)sim_bitmap_smem_words(Tcap) * 4 * 8;
     const bool two = n_procs > 32;
     switch (n_mem) {
-    case 1: two ? occupancy_of<1, 2>(blocks_per_sm) : occupancy_of<1, 1>(blocks_per_sm); break;
-    case 2: two ? occupancy_of<2, 2>(blocks_per_sm) : occupancy_of<2, 1>(blocks_per_sm); break;
-    case 3: two ? occupancy_of<3, 2>(blocks_per_sm) : occupancy_of<3, 1>(blocks_per_sm); break;
-    case 4: two ? occupancy_of<4, 2>(blocks_per_sm) : occupancy_of<4, 1>(blocks_per_sm); break;
+    case 1: two ? set_smem_attr<1, 2>(smem) : set_smem_attr<1, 1>(smem); break;
+    case 2: two ? set_smem_attr<2, 2>(smem) : set_smem_attr<2, 1>(smem); break;
+    case 3: two ? set_smem_attr<3, 2>(smem) : set_smem_attr<3, 1>(smem); break;
+    case 4: two ? set_smem_attr<4, 2>(smem) : set_smem_attr<4, 1>(smem); break;
     default: return HESP_ERR_ARG;
+    }
+    switch (n_mem) {
+    case 1: two ? occupancy_of<1, 2>(blocks_per_sm, smem) : occupancy_of<1, 1>(blocks_per_sm, smem); break;
+    case 2: two ? occupancy_of<2, 2>(blocks_per_sm, smem) : occupancy_of<2, 1>(blocks_per_sm, smem); break;
+    case 3: two ? occupancy_of<3, 2>(blocks_per_sm, smem) : occupancy_of<3, 1>(blocks_per_sm, smem); break;
+    case 4: two ? occupancy_of<4, 2>(blocks_per_sm, smem) : occupancy_of<4, 1>(blocks_per_sm, smem); break;
     }
     return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
 }
@@ -790,27 +874,29 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
     a.ar = ar;
     a.n_slots = n_slots;
     a.ws = ws + kWsHeaderBytes;
+    a.bm_smem_words = sim_bitmap_smem_words(ar.Tcap);
     unsigned long long *ctr = &((WsHeader *)ws)->work_counter;
     if (cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), stream) != cudaSuccess) return HESP_ERR_CUDA;
     const int threads = 256;
+    const size_t smem = (size_t)a.bm_smem_words * 4 * (threads / 32);
     const int64_t blocks = (n_slots * 32 + threads - 1) / threads;
     const bool two = p->n_procs > 32;
     switch (p->n_mem) {
     case 1:
-        if (two) sim_kernel<1, 2><<<(unsigned)blocks, threads, 0, stream>>>(dp, a, ctr);
-        else sim_kernel<1, 1><<<(unsigned)blocks, threads, 0, stream>>>(dp, a, ctr);
+        if (two) sim_kernel<1, 2><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
+        else sim_kernel<1, 1><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
         break;
     case 2:
-        if (two) sim_kernel<2, 2><<<(unsigned)blocks, threads, 0, stream>>>(dp, a, ctr);
-        else sim_kernel<2, 1><<<(unsigned)blocks, threads, 0, stream>>>(dp, a, ctr);
+        if (two) sim_kernel<2, 2><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
+        else sim_kernel<2, 1><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
         break;
     case 3:
-        if (two) sim_kernel<3, 2><<<(unsigned)blocks, threads, 0, stream>>>(dp, a, ctr);
-        else sim_kernel<3, 1><<<(unsigned)blocks, threads, 0, stream>>>(dp, a, ctr);
+        if (two) sim_kernel<3, 2><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
+        else sim_kernel<3, 1><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
         break;
     case 4:
-        if (two) sim_kernel<4, 2><<<(unsigned)blocks, threads, 0, stream>>>(dp, a, ctr);
-        else sim_kernel<4, 1><<<(unsigned)blocks, threads, 0, stream>>>(dp, a, ctr);
+        if (two) sim_kernel<4, 2><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
+        else sim_kernel<4, 1><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
         break;
     default:
         return HESP_ERR_ARG;
