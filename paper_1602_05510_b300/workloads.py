@@ -197,3 +197,28 @@ def workload_levels(key: str, first: int = 0, count: int | None = None) -> np.nd
     if key == "cfg0":
         return exhaustive_levels(nb)[first:first + count]
     return uniform_levels(w.seed, first, count, nb, w.n_levels)
+
+
+# ----------------------------------------------------------------------------
+# Surrogate initial weights: He-uniform from SplitMix64 (parameter id c,
+# element k in row-major order): w = (2 f - 1) * sqrt(6 / fan_in),
+# f = (u >> 40) * 2^-24, all in float32.
+# ----------------------------------------------------------------------------
+
+def he_uniform(seed: int, pid: int, rows: int, cols: int, fan_in: int, cols_used: int | None = None) -> np.ndarray:
+    cols_used = cols if cols_used is None else cols_used
+    k = np.arange(rows * cols, dtype=np.uint64)
+    u = counter_u64(seed, np.uint64(pid), k)
+    f = ((u >> np.uint64(40)).astype(np.float32) * np.float32(2.0 ** -24)).astype(np.float32)
+    bound = np.sqrt(np.float32(6.0) / np.float32(fan_in)).astype(np.float32)
+    w = ((np.float32(2.0) * f - np.float32(1.0)) * bound).astype(np.float32).reshape(rows, cols)
+    if cols_used < cols:
+        w[:, cols_used:] = 0.0
+    return w
+
+
+def surrogate_init(seed: int, F: int, Fp: int, H: int):
+    """Initial FP32 parameters (W1 [H, Fp], b1, W2 [H, H], b2, w3 [H], b3)."""
+    return dict(W1=he_uniform(seed, 0, H, Fp, F, F), b1=np.zeros(H, np.float32),
+                W2=he_uniform(seed, 1, H, H, H), b2=np.zeros(H, np.float32),
+                w3=he_uniform(seed, 2, 1, H, H).reshape(H), b3=np.zeros(1, np.float32))
