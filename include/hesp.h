@@ -231,6 +231,20 @@ int hesp_generate_candidates(int32_t kind, uint64_t seed, int64_t first, int64_t
 int hesp_generate_uneven(uint64_t seed, int64_t first, int64_t n_cand, hesp_cand *cands_dev, int8_t *levels_dev,
                          int64_t levels_cap, int64_t *levels_used_dev, void *stream);
 
+/* ------------------------------------------------ tensor-core BF16 GEMM
+ * The dense layers of the surrogate (below) run on this kernel; it is
+ * exported for reuse and testing.  C[M, N] = A[M, K] . B[N, K]^T with A, B
+ * bf16 row-major (leading dimensions lda, ldb >= K, multiples of 8 elements,
+ * 16-byte aligned), K a multiple of 64, FP32 accumulation in tensor memory.
+ * epilogue 0: c_dev[M, ldc] (fp32) = acc.
+ * epilogue 1: out_dev[M, ldo] (bf16) = relu(acc + bias_dev[N]) (round to nearest even).
+ * epilogue 2: out_dev[M, ldo] (bf16) = acc where mask_dev[M, ldm] (bf16) > 0, else 0.
+ * out_t_dev (nullable, epilogues 1-2): the same values transposed, [N, ldt].
+ * err_dev (nullable, device int32): set to 1 if a pipeline wait timed out. */
+int hesp_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *a_dev, int64_t lda, const void *b_dev, int64_t ldb,
+                   int32_t epilogue, float *c_dev, int64_t ldc, const float *bias_dev, void *out_dev, int64_t ldo,
+                   void *out_t_dev, int64_t ldt, const void *mask_dev, int64_t ldm, int32_t *err_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

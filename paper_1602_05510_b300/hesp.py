@@ -29,6 +29,7 @@ EXPORTS = (
     "hesp_platform_xfer_ns", "hesp_platform_destroy", "hesp_dag_build", "hesp_dag_n_base",
     "hesp_dag_base_tasks", "hesp_dag_count_tasks", "hesp_dag_destroy", "hesp_sim_workspace_size",
     "hesp_simulate_batch", "hesp_simulate_batch_noalloc", "hesp_generate_candidates", "hesp_generate_uneven",
+    "hesp_gemm_bf16",
 )
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -85,6 +86,8 @@ def lib():
         L.hesp_sim_workspace_size.argtypes = [vp, i32, i32, i64, ctypes.POINTER(sz)]
         L.hesp_simulate_batch.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         L.hesp_simulate_batch_noalloc.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.hesp_gemm_bf16.argtypes = [i32, i32, i32, vp, i64, vp, i64, i32, vp, i64, vp, vp, i64, vp, i64, vp, i64,
+                                     vp, vp]
         L.hesp_generate_candidates.argtypes = [i32, u64, i64, i64, i32, i32, i32, vp, vp, vp]
         L.hesp_generate_uneven.argtypes = [u64, i64, i64, vp, vp, i64, vp, vp]
         _lib = L
@@ -254,3 +257,22 @@ def generate_candidates(kind, seed, first, n_cand, n_tiles, b, n_levels, levels,
 def generate_uneven(seed, first, n_cand, cands, levels, levels_used, stream=None):
     check(lib().hesp_generate_uneven(seed, first, n_cand, _ptr(cands), _ptr(levels), levels.numel(),
                                      _ptr(levels_used), _stream(stream)), "hesp_generate_uneven")
+
+
+GEMM_F32, GEMM_BIAS_RELU, GEMM_MASK = 0, 1, 2
+
+
+def gemm_bf16(A, B, epilogue=GEMM_F32, C=None, bias=None, out=None, out_t=None, mask=None, err=None, K=None,
+              stream=None):
+    """hesp_gemm_bf16: C[M, N] = A[M, K] B[N, K]^T on the tensor cores.
+    A, B: bf16 row-major device tensors (K columns used, a multiple of 64).
+    epilogue 0: fp32 C; 1: bf16 out = relu(acc + bias) (+ transposed out_t);
+    2: bf16 out = acc where mask > 0 else 0 (+ out_t)."""
+    M, N = A.shape[0], B.shape[0]
+    K = A.shape[1] if K is None else K
+    check(lib().hesp_gemm_bf16(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), epilogue, _ptr(C),
+                               C.stride(0) if C is not None else 0, _ptr(bias), _ptr(out),
+                               out.stride(0) if out is not None else 0, _ptr(out_t),
+                               out_t.stride(0) if out_t is not None else 0, _ptr(mask),
+                               mask.stride(0) if mask is not None else 0, _ptr(err), _stream(stream)),
+          "hesp_gemm_bf16")
