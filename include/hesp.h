@@ -245,6 +245,75 @@ int hesp_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *a_dev, int64_t l
                    int32_t epilogue, float *c_dev, int64_t ldc, const float *bias_dev, void *out_dev, int64_t ldo,
                    void *out_t_dev, int64_t ldt, const void *mask_dev, int64_t ldm, int32_t *err_dev, void *stream);
 
+/* ---------------------------------------------------------- surrogate MLP
+ * Not in the paper: a learned model of the simulator that ranks proposals for
+ * the partition stage of HeSP's search (Sec. 2.1 "Iterative solver"), so
+ * that only the best-ranked ones are simulated exactly.
+ * Input: the partition vector (n_base split levels in 0..n_levels-1), one-hot
+ * encoded into F = n_base * n_levels features (padded with zeros to Fp, a
+ * multiple of 64).  Network: F -> H -> H -> 1 with ReLU; bf16 weights and
+ * activations (round to nearest even), FP32 accumulation on the tensor cores;
+ * target t = (ln makespan - mu) / sigma; loss mean (y - t)^2; Adam
+ * (beta 0.9 / 0.999, eps 1e-8) on FP32 masters.  Initial weights: He-uniform
+ * from SplitMix64 (parameter id c = 0 for W1, 1 for W2, 2 for w3, element k
+ * in row-major order: w = (2 f - 1) sqrt(6 / fan_in), f = (u >> 40) 2^-24),
+ * biases 0.  The handle owns its device memory (weights, optimiser state and
+ * activations for max_batch rows). */
+typedef struct hesp_surrogate hesp_surrogate;
+
+/* hidden and max_batch: multiples of 64.  Synchronous. */
+int hesp_surrogate_create(int32_t n_base, int32_t n_levels, int32_t hidden, int32_t max_batch, uint64_t seed,
+                          hesp_surrogate **out);
+void hesp_surrogate_destroy(hesp_surrogate *s);
+int hesp_surrogate_shape(const hesp_surrogate *s, int64_t *F_out, int64_t *Fp_out, int32_t *H_out);
+/* Target standardisation: set directly, or fit (mean and population standard
+ * deviation of ln makespan over makespan_dev[n]; synchronises the stream). */
+int hesp_surrogate_set_stats(hesp_surrogate *s, double mu, double sigma);
+int hesp_surrogate_get_stats(const hesp_surrogate *s, double *mu, double *sigma, int64_t *adam_steps);
+int hesp_surrogate_fit_stats(hesp_surrogate *s, const int64_t *makespan_dev, int64_t n, void *stream);
+/* Host copies of the FP32 tensors in the order W1 [H, Fp], b1 [H], W2 [H, H],
+ * b2 [H], w3 [H], b3 [1], n = total count; which: 0 parameters, 1 gradients,
+ * 2 Adam first moments, 3 second moments (checkpoint / restore). Synchronous. */
+int hesp_surrogate_get(const hesp_surrogate *s, int32_t which, float *host, int64_t n);
+int hesp_surrogate_set(hesp_surrogate *s, int32_t which, const float *host, int64_t n);
+/* Forward and backward on levels_dev [B, n_base] with makespan_dev [B]
+ * (B a multiple of 64, <= max_batch): gradients into the handle; pred_dev [B]
+ * and loss_dev [1] (fp32, nullable) receive y and the loss. */
+int hesp_surrogate_grad(hesp_surrogate *s, const int8_t *levels_dev, const int64_t *makespan_dev, int32_t B,
+                        float *pred_dev, float *loss_dev, void *stream);
+/* One Adam update with the gradients held by the handle. */
+int hesp_surrogate_adam(hesp_surrogate *s, float lr, void *stream);
+/* n_steps updates on minibatches of `batch` rows drawn from n_samples
+ * labelled samples (row i of step k = sample draw(u(seed, k, i), n_samples));
+ * loss_dev [n_steps] (nullable) receives each step's loss. */
+int hesp_surrogate_train(hesp_surrogate *s, const int8_t *levels_dev, const int64_t *makespan_dev, int64_t n_samples,
+                         int32_t batch, int32_t n_steps, float lr, uint64_t seed, float *loss_dev, void *stream);
+/* pred_dev[n] = predicted standardised log-makespan of levels_dev [n, n_base]
+ * (processed in chunks of max_batch rows). */
+int hesp_surrogate_infer(hesp_surrogate *s, const int8_t *levels_dev, int64_t n, float *pred_dev, void *stream);
+/* 1 if a tensor-core pipeline wait of this handle timed out, else 0. */
+int hesp_surrogate_error(hesp_surrogate *s, int32_t *err_host);
+
+/* ------------------------------------------------- select and re-score
+ * hesp_select_topk: indices (ascending) of the k smallest keys of keys_dev[n]
+ * (ties broken by the lower index) into idx_dev[k]; workspace from
+ * hesp_select_workspace_size (device, 16-byte aligned).
+ * hesp_make_cands: cands_dev[k] = candidate (n_tiles, b) whose levels are row
+ * idx_dev[i] of a [*, n_base] level array, for re-simulation.
+ * hesp_gather_f32: dst_dev[i] = src_dev[idx_dev[i]].
+ * hesp_rank_metrics: out_host[0] = mean |exp(pred sigma + mu) - makespan| /
+ * makespan, out_host[1] = Spearman rank correlation (average ranks for ties)
+ * of pred and makespan over k items; synchronises the stream. */
+int hesp_select_workspace_size(int64_t n, size_t *bytes_out);
+int hesp_select_topk(const float *keys_dev, int64_t n, int64_t k, int64_t *idx_dev, void *workspace_dev,
+                     size_t workspace_bytes, void *stream);
+int hesp_make_cands(const int64_t *idx_dev, int64_t k, int32_t n_tiles, int32_t b, hesp_cand *cands_dev,
+                    void *stream);
+int hesp_gather_f32(const float *src_dev, const int64_t *idx_dev, int64_t k, float *dst_dev, void *stream);
+int hesp_rank_metrics_workspace_size(int64_t k, size_t *bytes_out);
+int hesp_rank_metrics(const float *pred_dev, const int64_t *makespan_dev, int64_t k, double mu, double sigma,
+                      void *workspace_dev, size_t workspace_bytes, double *out_host, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,20 +23,6 @@
 
 namespace hesp {
 
-struct GemmArgs {
-    int M, N, K;
-    int epi;
-    float *C;  // EPI_F32: fp32 out [M, ldc]
-    int ldc;
-    const float *bias;       // EPI_BIAS_RELU: bias[N]
-    __nv_bfloat16 *out;      // bf16 out [M, ldo]
-    int ldo;
-    __nv_bfloat16 *out_t;    // optional transposed bf16 out [N, ldt]
-    int ldt;
-    const __nv_bfloat16 *mask;  // EPI_MASK: keep acc where mask[M, ldm] > 0
-    int ldm;
-    int *err;                // raised on a wait timeout (nullable)
-};
 
 namespace {
 
@@ -199,7 +185,7 @@ __global__ void __launch_bounds__(128, 1)
             const bool full = col0 + 16 <= g.N;
             if (g.epi == 0) {
                 float *dst = g.C + (int64_t)row * g.ldc + col0;
-                if (full && (g.ldc & 3) == 0) {
+                if (full && (((uintptr_t)dst) & 15) == 0) {
 #pragma unroll
                     for (int q = 0; q < 16; q += 4) *reinterpret_cast<float4 *>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
                 } else {
@@ -223,7 +209,7 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
             for (int q = 0; q < 16; ++q) h[q] = __float2bfloat16_rn(v[q]);
             __nv_bfloat16 *dst = g.out + (int64_t)row * g.ldo + col0;
-            if (full && (g.ldo & 7) == 0) {
+            if (full && (((uintptr_t)dst) & 15) == 0) {
                 *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(h);
                 *reinterpret_cast<uint4 *>(dst + 8) = *reinterpret_cast<const uint4 *>(h + 8);
             } else {

@@ -1,6 +1,8 @@
 // Internal declarations shared by the CUDA sources of libhesp.so.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "hesp.h"
@@ -72,5 +74,23 @@ int launch_generate(int32_t kind, uint64_t seed, int64_t first, int64_t n_cand, 
                     int32_t n_levels, hesp_cand *cands, int8_t *levels, cudaStream_t stream);
 int launch_generate_uneven(uint64_t seed, int64_t first, int64_t n_cand, hesp_cand *cands, int8_t *levels,
                            int64_t levels_cap, int64_t *levels_used, cudaStream_t stream);
+
+// Arguments of the tensor-core GEMM C = A B^T and its epilogues
+// (0: fp32 C; 1: bf16 relu(acc + bias) (+ transposed); 2: bf16 acc masked by mask > 0 (+ transposed)).
+struct GemmArgs {
+    int M, N, K;
+    int epi;
+    float *C;
+    int ldc;
+    const float *bias;
+    __nv_bfloat16 *out;
+    int ldo;
+    __nv_bfloat16 *out_t;
+    int ldt;
+    const __nv_bfloat16 *mask;
+    int ldm;
+    int *err;
+};
+int launch_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, const GemmArgs &g, cudaStream_t st);
 
 }  // namespace hesp

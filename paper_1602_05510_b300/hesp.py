@@ -29,7 +29,11 @@ EXPORTS = (
     "hesp_platform_xfer_ns", "hesp_platform_destroy", "hesp_dag_build", "hesp_dag_n_base",
     "hesp_dag_base_tasks", "hesp_dag_count_tasks", "hesp_dag_destroy", "hesp_sim_workspace_size",
     "hesp_simulate_batch", "hesp_simulate_batch_noalloc", "hesp_generate_candidates", "hesp_generate_uneven",
-    "hesp_gemm_bf16",
+    "hesp_gemm_bf16", "hesp_surrogate_create", "hesp_surrogate_destroy", "hesp_surrogate_shape",
+    "hesp_surrogate_set_stats", "hesp_surrogate_get_stats", "hesp_surrogate_fit_stats", "hesp_surrogate_get",
+    "hesp_surrogate_set", "hesp_surrogate_grad", "hesp_surrogate_adam", "hesp_surrogate_train",
+    "hesp_surrogate_infer", "hesp_surrogate_error", "hesp_select_workspace_size", "hesp_select_topk",
+    "hesp_make_cands", "hesp_gather_f32", "hesp_rank_metrics_workspace_size", "hesp_rank_metrics",
 )
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -88,6 +92,27 @@ def lib():
         L.hesp_simulate_batch_noalloc.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.hesp_gemm_bf16.argtypes = [i32, i32, i32, vp, i64, vp, i64, i32, vp, i64, vp, vp, i64, vp, i64, vp, i64,
                                      vp, vp]
+        f32, f64 = ctypes.c_float, ctypes.c_double
+        L.hesp_surrogate_create.argtypes = [i32, i32, i32, i32, u64, ctypes.POINTER(vp)]
+        L.hesp_surrogate_destroy.argtypes = [vp]
+        L.hesp_surrogate_destroy.restype = None
+        L.hesp_surrogate_shape.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)]
+        L.hesp_surrogate_set_stats.argtypes = [vp, f64, f64]
+        L.hesp_surrogate_get_stats.argtypes = [vp, ctypes.POINTER(f64), ctypes.POINTER(f64), ctypes.POINTER(i64)]
+        L.hesp_surrogate_fit_stats.argtypes = [vp, vp, i64, vp]
+        L.hesp_surrogate_get.argtypes = [vp, i32, vp, i64]
+        L.hesp_surrogate_set.argtypes = [vp, i32, vp, i64]
+        L.hesp_surrogate_grad.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+        L.hesp_surrogate_adam.argtypes = [vp, f32, vp]
+        L.hesp_surrogate_train.argtypes = [vp, vp, vp, i64, i32, i32, f32, u64, vp, vp]
+        L.hesp_surrogate_infer.argtypes = [vp, vp, i64, vp, vp]
+        L.hesp_surrogate_error.argtypes = [vp, ctypes.POINTER(i32)]
+        L.hesp_select_workspace_size.argtypes = [i64, ctypes.POINTER(sz)]
+        L.hesp_select_topk.argtypes = [vp, i64, i64, vp, vp, sz, vp]
+        L.hesp_make_cands.argtypes = [vp, i64, i32, i32, vp, vp]
+        L.hesp_gather_f32.argtypes = [vp, vp, i64, vp, vp]
+        L.hesp_rank_metrics_workspace_size.argtypes = [i64, ctypes.POINTER(sz)]
+        L.hesp_rank_metrics.argtypes = [vp, vp, i64, f64, f64, vp, sz, ctypes.POINTER(f64), vp]
         L.hesp_generate_candidates.argtypes = [i32, u64, i64, i64, i32, i32, i32, vp, vp, vp]
         L.hesp_generate_uneven.argtypes = [u64, i64, i64, vp, vp, i64, vp, vp]
         _lib = L
@@ -276,3 +301,126 @@ def gemm_bf16(A, B, epilogue=GEMM_F32, C=None, bias=None, out=None, out_t=None, 
                                out_t.stride(0) if out_t is not None else 0, _ptr(mask),
                                mask.stride(0) if mask is not None else 0, _ptr(err), _stream(stream)),
           "hesp_gemm_bf16")
+
+
+class Surrogate:
+    """The MLP surrogate (hesp_surrogate handle): n_base * n_levels one-hot
+    inputs -> hidden -> hidden -> 1, bf16 tensor-core kernels, FP32 masters."""
+
+    PARTS = ("W1", "b1", "W2", "b2", "w3", "b3")
+
+    def __init__(self, n_base, n_levels, hidden=512, max_batch=4096, seed=0):
+        h = ctypes.c_void_p()
+        check(lib().hesp_surrogate_create(n_base, n_levels, hidden, max_batch, seed, ctypes.byref(h)),
+              "hesp_surrogate_create")
+        self.h = h
+        F, Fp, H = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        check(lib().hesp_surrogate_shape(h, ctypes.byref(F), ctypes.byref(Fp), ctypes.byref(H)),
+              "hesp_surrogate_shape")
+        self.n_base, self.n_levels, self.F, self.Fp, self.H = n_base, n_levels, F.value, Fp.value, H.value
+        self.max_batch = max_batch
+        self.sizes = (self.H * self.Fp, self.H, self.H * self.H, self.H, self.H, 1)
+        self.shapes = ((self.H, self.Fp), (self.H,), (self.H, self.H), (self.H,), (self.H,), (1,))
+
+    def _flat(self, parts):
+        return np.concatenate([np.asarray(parts[k], np.float32).reshape(-1) for k in self.PARTS])
+
+    def _split(self, flat):
+        out, o = {}, 0
+        for k, n, sh in zip(self.PARTS, self.sizes, self.shapes):
+            out[k] = flat[o:o + n].reshape(sh)
+            o += n
+        return out
+
+    def get(self, which=0):
+        """which: 0 parameters, 1 gradients, 2 Adam first moments, 3 second moments."""
+        flat = np.zeros(sum(self.sizes), np.float32)
+        check(lib().hesp_surrogate_get(self.h, which, flat.ctypes.data, flat.size), "hesp_surrogate_get")
+        return self._split(flat)
+
+    def set(self, parts, which=0):
+        flat = np.ascontiguousarray(self._flat(parts))
+        check(lib().hesp_surrogate_set(self.h, which, flat.ctypes.data, flat.size), "hesp_surrogate_set")
+
+    def set_stats(self, mu, sigma):
+        check(lib().hesp_surrogate_set_stats(self.h, mu, sigma), "hesp_surrogate_set_stats")
+
+    def stats(self):
+        mu, sg, st = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        check(lib().hesp_surrogate_get_stats(self.h, ctypes.byref(mu), ctypes.byref(sg), ctypes.byref(st)),
+              "hesp_surrogate_get_stats")
+        return mu.value, sg.value, st.value
+
+    def fit_stats(self, makespan, stream=None):
+        check(lib().hesp_surrogate_fit_stats(self.h, _ptr(makespan), makespan.numel(), _stream(stream)),
+              "hesp_surrogate_fit_stats")
+
+    def grad(self, levels, makespan, B, pred=None, loss=None, stream=None):
+        check(lib().hesp_surrogate_grad(self.h, _ptr(levels), _ptr(makespan), B, _ptr(pred), _ptr(loss),
+                                        _stream(stream)), "hesp_surrogate_grad")
+
+    def adam(self, lr=1e-3, stream=None):
+        check(lib().hesp_surrogate_adam(self.h, lr, _stream(stream)), "hesp_surrogate_adam")
+
+    def train(self, levels, makespan, n_samples, batch, n_steps, lr=1e-3, seed=0, loss=None, stream=None):
+        check(lib().hesp_surrogate_train(self.h, _ptr(levels), _ptr(makespan), n_samples, batch, n_steps, lr, seed,
+                                         _ptr(loss), _stream(stream)), "hesp_surrogate_train")
+
+    def infer(self, levels, n, pred, stream=None):
+        check(lib().hesp_surrogate_infer(self.h, _ptr(levels), n, _ptr(pred), _stream(stream)),
+              "hesp_surrogate_infer")
+
+    def error_flag(self):
+        e = ctypes.c_int32()
+        check(lib().hesp_surrogate_error(self.h, ctypes.byref(e)), "hesp_surrogate_error")
+        return e.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hesp_surrogate_destroy(self.h)
+            self.h = None
+
+
+def select_topk(keys, k, idx=None, stream=None):
+    """Indices (ascending) of the k smallest keys (ties to the lowest index)."""
+    import torch
+    n = keys.numel()
+    sz = ctypes.c_size_t()
+    check(lib().hesp_select_workspace_size(n, ctypes.byref(sz)), "hesp_select_workspace_size")
+    ws = torch.empty(sz.value, dtype=torch.uint8, device=keys.device)
+    if idx is None:
+        idx = torch.empty(k, dtype=torch.int64, device=keys.device)
+    check(lib().hesp_select_topk(_ptr(keys), n, k, _ptr(idx), _ptr(ws), sz.value, _stream(stream)),
+          "hesp_select_topk")
+    return idx
+
+
+def make_cands(idx, n_tiles, b, cands=None, stream=None):
+    import torch
+    k = idx.numel()
+    if cands is None:
+        cands = torch.empty(k * 16, dtype=torch.uint8, device=idx.device)
+    check(lib().hesp_make_cands(_ptr(idx), k, n_tiles, b, _ptr(cands), _stream(stream)), "hesp_make_cands")
+    return cands
+
+
+def gather_f32(src, idx, dst=None, stream=None):
+    import torch
+    if dst is None:
+        dst = torch.empty(idx.numel(), dtype=torch.float32, device=src.device)
+    check(lib().hesp_gather_f32(_ptr(src), _ptr(idx), idx.numel(), _ptr(dst), _stream(stream)), "hesp_gather_f32")
+    return dst
+
+
+def rank_metrics(pred, makespan, mu, sigma, stream=None):
+    """(mean relative makespan error, Spearman rank correlation) of the
+    surrogate's predictions against exact makespans."""
+    import torch
+    k = pred.numel()
+    sz = ctypes.c_size_t()
+    check(lib().hesp_rank_metrics_workspace_size(k, ctypes.byref(sz)), "hesp_rank_metrics_workspace_size")
+    ws = torch.empty(sz.value, dtype=torch.uint8, device=pred.device)
+    out = (ctypes.c_double * 2)()
+    check(lib().hesp_rank_metrics(_ptr(pred), _ptr(makespan), k, mu, sigma, _ptr(ws), sz.value, out,
+                                  _stream(stream)), "hesp_rank_metrics")
+    return out[0], out[1]

@@ -1,0 +1,178 @@
+"""GPU surrogate (hesp_surrogate_*) against the FP64 reference oracle/mlp_ref.py
+on identical inputs (weights from the host-side initialiser, seeded levels and
+makespans): initial weights bit-exact, forward outputs, loss and every
+gradient within the tolerance of bf16 operands with FP32 accumulation
+(relative error of each tensor <= 1e-2, cosine >= 0.999), one Adam step,
+training that lowers the loss, and the selection / metric kernels against
+numpy / scipy definitions."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import mlp_ref as R  # noqa: E402
+from paper_1602_05510_b300 import hesp  # noqa: E402
+from paper_1602_05510_b300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1602_05510_b300 import build
+    build.build()
+
+
+def close(got, want, rel=1e-2, cos=0.999):
+    got = np.asarray(got, np.float64).ravel()
+    want = np.asarray(want, np.float64).ravel()
+    nw = np.linalg.norm(want)
+    assert np.linalg.norm(got - want) <= rel * max(nw, 1e-12), (np.linalg.norm(got - want), nw)
+    if nw > 0 and np.linalg.norm(got) > 0:
+        assert got @ want / (np.linalg.norm(got) * nw) >= cos
+
+
+def batch(rng, B, T, NL):
+    lv = rng.integers(0, NL, (B, T)).astype(np.int8)
+    ms = np.exp(rng.normal(20.5, 0.3, B)).astype(np.int64)
+    return lv, ms
+
+
+SHAPES = [(10, 2, 64, 64), (816, 3, 512, 256), (120, 3, 128, 128)]
+
+
+@pytest.mark.parametrize("T,NL,H,B", SHAPES)
+def test_init_matches_host_initialiser(T, NL, H, B):
+    s = hesp.Surrogate(T, NL, H, max_batch=max(B, 64), seed=17)
+    ref = W.surrogate_init(17, T * NL, s.Fp, H)
+    got = s.get(0)
+    for k in s.PARTS:
+        assert np.array_equal(got[k].reshape(-1), ref[k].reshape(-1)), k
+
+
+@pytest.mark.parametrize("T,NL,H,B", SHAPES)
+def test_forward_backward_parity(T, NL, H, B):
+    rng = np.random.default_rng(T + H)
+    s = hesp.Surrogate(T, NL, H, max_batch=B, seed=5)
+    p = W.surrogate_init(5, T * NL, s.Fp, H)
+    p["b1"] = (rng.standard_normal(H) * 0.05).astype(np.float32)
+    p["b2"] = (rng.standard_normal(H) * 0.05).astype(np.float32)
+    p["b3"] = np.array([0.1], np.float32)
+    s.set(p)
+    mu, sigma = 20.4, 0.25
+    s.set_stats(mu, sigma)
+    lv, ms = batch(rng, B, T, NL)
+    pred = torch.empty(B, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    s.grad(torch.from_numpy(lv.reshape(-1).copy()).cuda(), torch.from_numpy(ms).cuda(), B, pred, loss)
+    torch.cuda.synchronize()
+    assert s.error_flag() == 0
+    g = s.get(1)
+    ref = R.MLPRef(p["W1"], p["b1"], p["W2"], p["b2"], p["w3"], float(p["b3"][0]))
+    X = R.one_hot(lv, NL, s.Fp)
+    t = (np.log(ms.astype(np.float64)) - mu) / sigma
+    out = ref.backward(X, t)
+    close(pred.cpu().numpy(), out["y"], rel=2e-3)
+    assert abs(loss.item() - out["loss"]) <= 1e-2 * out["loss"]
+    for k in s.PARTS:
+        close(g[k], out["grads"][k])
+
+
+def test_adam_step_parity():
+    rng = np.random.default_rng(9)
+    T, NL, H, B = 120, 3, 128, 128
+    s = hesp.Surrogate(T, NL, H, max_batch=B, seed=2)
+    p = W.surrogate_init(2, T * NL, s.Fp, H)
+    s.set(p)
+    s.set_stats(20.4, 0.25)
+    lv, ms = batch(rng, B, T, NL)
+    s.grad(torch.from_numpy(lv.reshape(-1).copy()).cuda(), torch.from_numpy(ms).cuda(), B)
+    s.adam(1e-3)
+    torch.cuda.synchronize()
+    new = s.get(0)
+    ref = R.MLPRef(p["W1"], p["b1"], p["W2"], p["b2"], p["w3"], float(p["b3"][0]))
+    X = R.one_hot(lv, NL, s.Fp)
+    g = ref.backward(X, (np.log(ms.astype(np.float64)) - 20.4) / 0.25)["grads"]
+    for k in s.PARTS:
+        want, _, _ = R.adam_step(np.asarray(p[k], np.float64), g[k].reshape(np.shape(p[k])), 0.0, 0.0, 1)
+        d_got = np.asarray(new[k], np.float64) - p[k]
+        d_want = want - p[k]
+        # the first Adam step is lr * g / (|g| + eps): elements whose gradient is
+        # near zero may differ, every other one moves by the same amount
+        big = np.abs(g[k].reshape(np.shape(p[k]))) > 1e-4 * max(np.abs(g[k]).max(), 1e-30)
+        assert np.mean(np.abs(d_got - d_want)[big] <= 1e-6) >= 0.99, k
+        assert np.abs(d_got).max() <= 1.0001e-3
+
+
+def test_training_lowers_loss_and_infer_is_consistent():
+    rng = np.random.default_rng(1)
+    T, NL, H = 120, 3, 256
+    n = 8192
+    lv = rng.integers(0, NL, (n, T)).astype(np.int8)
+    # a target with structure: log makespan grows with the number of splits
+    ms = np.exp(20.0 + 0.01 * lv.sum(1) + rng.normal(0, 0.01, n)).astype(np.int64)
+    s = hesp.Surrogate(T, NL, H, max_batch=1024, seed=3)
+    d_lv = torch.from_numpy(lv.reshape(-1).copy()).cuda()
+    d_ms = torch.from_numpy(ms).cuda()
+    s.fit_stats(d_ms)
+    mu, sigma, _ = s.stats()
+    assert abs(mu - np.log(ms).mean()) < 1e-9 and abs(sigma - np.log(ms).std()) < 1e-9
+    losses = torch.empty(200, dtype=torch.float32, device="cuda")
+    s.train(d_lv, d_ms, n, 1024, 200, lr=1e-3, seed=11, loss=losses)
+    torch.cuda.synchronize()
+    L = losses.cpu().numpy()
+    assert s.error_flag() == 0
+    assert L[-20:].mean() < 0.2 * L[:5].mean()
+    pred = torch.empty(n, dtype=torch.float32, device="cuda")
+    s.infer(d_lv, n, pred)
+    torch.cuda.synchronize()
+    t = (np.log(ms) - mu) / sigma
+    assert np.corrcoef(pred.cpu().numpy(), t)[0, 1] > 0.9
+    p = s.get(0)
+    ref = R.MLPRef(p["W1"], p["b1"], p["W2"], p["b2"], p["w3"], float(p["b3"][0]))
+    close(pred.cpu().numpy()[:512], ref.forward(R.one_hot(lv[:512], NL, s.Fp))["y"], rel=5e-3)
+
+
+def test_select_topk_matches_definition():
+    rng = np.random.default_rng(4)
+    for n, k in ((1000, 10), (100000, 1000), (4 << 20, 40000)):
+        keys = rng.standard_normal(n).astype(np.float32)
+        keys[rng.choice(n, n // 10, replace=False)] = 0.25  # many ties
+        d = torch.from_numpy(keys).cuda()
+        idx = hesp.select_topk(d, k)
+        torch.cuda.synchronize()
+        want = np.sort(np.lexsort((np.arange(n), keys))[:k])
+        assert np.array_equal(idx.cpu().numpy(), want)
+
+
+def test_rank_metrics_match_scipy():
+    import scipy.stats
+    rng = np.random.default_rng(2)
+    k = 5000
+    pred = rng.standard_normal(k).astype(np.float32)
+    pred[:100] = pred[100:200]  # ties
+    ms = np.exp(20 + 0.3 * pred.astype(np.float64) + rng.normal(0, 0.2, k)).astype(np.int64)
+    ms[300:320] = ms[320:340]
+    mu, sigma = 20.0, 0.3
+    rel, rho = hesp.rank_metrics(torch.from_numpy(pred).cuda(), torch.from_numpy(ms).cuda(), mu, sigma)
+    want_rel = np.mean(np.abs(np.exp(pred.astype(np.float64) * sigma + mu) - ms) / ms)
+    assert abs(rel - want_rel) <= 1e-9 * max(1.0, want_rel)
+    assert abs(rho - scipy.stats.spearmanr(pred, ms).correlation) <= 1e-9
+
+
+def test_make_cands_resimulates_selected_rows():
+    lv = W.workload_levels("cfg1", 0, 512)
+    d_lv = torch.from_numpy(lv.reshape(-1).copy()).cuda()
+    keys = torch.from_numpy(np.random.default_rng(0).standard_normal(512).astype(np.float32)).cuda()
+    idx = hesp.select_topk(keys, 40)
+    cands = hesp.make_cands(idx, 8, 2048)
+    plat = hesp.Platform(W.PLATFORMS["cfg1a"])
+    ws = hesp.alloc_workspace(plat, 8, 2, 512)
+    ms_sel, st_sel, _ = hesp.simulate_batch(plat, cands, d_lv, 40, 8, 2, ws)
+    all_c = hesp.cands_tensor(8, 2048, np.arange(512) * 120)
+    ms_all, st_all, _ = hesp.simulate_batch(plat, all_c, d_lv, 512, 8, 2, ws)
+    torch.cuda.synchronize()
+    assert (st_sel == 0).all() and (st_all == 0).all()
+    assert torch.equal(ms_sel, ms_all[idx])
