@@ -373,6 +373,123 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------- other workload lines
+
+
+def run_surrogate_pipeline(args):
+    """16 x 16 tiles (816 base tasks, levels 0..2) on 16 CPU + 2 GPU-type
+    processors: label n_labels uniform partitions by exact simulation, train
+    the 2448 -> 512 -> 512 -> 1 surrogate on them, rank 4M proposals, re-simulate
+    the best 1 % exactly and report the surrogate's relative makespan error
+    and Spearman rank correlation on that slice, with the throughput of each
+    stage."""
+    import torch
+
+    from paper_1602_05510_b300 import build, hesp
+    from paper_1602_05510_b300 import search as S
+
+    build.build()
+    n, b, NL = 16, 2048, 3
+    nb = W.base_count(n)
+    spec = W.PLATFORMS["cfg3"]
+    N = args.labels
+    P = args.proposals
+    K = P // 100
+    sim = S.Simulator(spec, n, b, NL - 1, min(N, 65536))
+    lab_lv = torch.empty(N * nb, dtype=torch.int8, device="cuda")
+    lab_ms = torch.empty(N, dtype=torch.int64, device="cuda")
+    ev = 0
+
+    def sync():
+        torch.cuda.synchronize()
+        return time.perf_counter()
+
+    t0 = sync()
+    for i in range(0, N, sim.per_launch):
+        c = min(sim.per_launch, N - i)
+        hesp.generate_candidates(hesp.GEN_UNIFORM, 3, i, c, n, b, NL, lab_lv[i * nb:])
+        ms, st, nt = sim.run(lab_lv[i * nb:], c)
+        lab_ms[i:i + c].copy_(ms)
+        ev += int(hesp.best_makespan(ms, st, nt).cpu().numpy()[1])
+    t_label = sync() - t0
+    sur = hesp.Surrogate(nb, NL, 512, 65536, seed=3)  # inference in chunks of 65,536 rows
+    sur.fit_stats(lab_ms)
+    mu, sigma, _ = sur.stats()
+    t0 = sync()
+    losses = torch.empty(args.train_steps, dtype=torch.float32, device="cuda")
+    sur.train(lab_lv, lab_ms, N, 4096, args.train_steps, 1e-3, seed=7, loss=losses)
+    t_train = sync() - t0
+    prop = torch.empty(P * nb, dtype=torch.int8, device="cuda")
+    hesp.generate_candidates(hesp.GEN_UNIFORM, 33, 0, P, n, b, NL, prop)
+    pred = torch.empty(P, dtype=torch.float32, device="cuda")
+    sur.infer(prop, min(P, 65536), pred)  # warm-up
+    t0 = sync()
+    sur.infer(prop, P, pred)
+    idx = hesp.select_topk(pred, K)
+    t_infer = sync() - t0
+    cands = hesp.make_cands(idx, n, b)
+    sim2 = S.Simulator(spec, n, b, NL - 1, K)
+    t0 = sync()
+    ms, st, nt = sim2.run(prop, K, cands)
+    t_resim = sync() - t0
+    rel, rho = hesp.rank_metrics(hesp.gather_f32(pred, idx), ms, mu, sigma)
+    flops = 2.0 * P * (sur.Fp * 512 + 512 * 512 + 512)
+    L = losses.cpu().numpy()
+    line = {"metric": "surrogate proposals ranked/s (2448-512-512-1 bf16 MLP + top-1% select)",
+            "value": P / t_infer, "unit": "proposals/s", "n_gpus": 1, "higher_is_better": True,
+            "workload": "16x16 tiles, levels 0..2, 16 CPU + 2 GPU; %d labels, %d proposals, top %d" % (N, P, K),
+            "labelling_task_events_per_s": ev / t_label, "label_s": t_label,
+            "train_steps": args.train_steps, "train_step_ms": 1e3 * t_train / max(args.train_steps, 1),
+            "train_loss_first_last": [float(L[:10].mean()), float(L[-10:].mean())],
+            "infer_tflops": flops / t_infer / 1e12, "resim_s": t_resim,
+            "top1pct_rel_makespan_error": rel, "top1pct_spearman": rho, "mu": mu, "sigma": sigma,
+            "error_flag": sur.error_flag()}
+    print(json.dumps(line))
+
+
+def run_search(args):
+    """32 x 32 tiles (5984 base tasks, levels 0..3) on 32 CPU + 2 GPU-type
+    processors: plain batched random search against surrogate-guided search,
+    each for the same wall-time budget on one GPU."""
+    import torch
+
+    from paper_1602_05510_b300 import build
+    from paper_1602_05510_b300 import search as S
+
+    build.build()
+    n, b, NL = 32, 2048, 4
+    spec = W.PLATFORMS["cfg4"]
+    cap = 1 << 20
+    ws = int(args.ws_gb * (1 << 30))
+    sim = S.Simulator(spec, n, b, NL - 1, args.per_launch, task_cap=cap, ws_bytes=ws)
+    rlog = S.random_search(spec, n, b, NL, seed=4, budget_s=args.budget, per_launch=args.per_launch, sim=sim)
+    cfg = S.SurrogateConfig(hidden=512, batch=2048, warmup_launches=1, warmup_steps=args.warmup_steps,
+                            steps_per_round=args.round_steps, proposals=args.round_proposals, elites=32,
+                            p_mut=args.p_mut, label_cap=1 << 17)
+    sim2 = S.Simulator(spec, n, b, NL - 1, args.round_sims, task_cap=cap, ws_bytes=ws)
+    slog = S.surrogate_search(spec, n, b, NL, seed=5, budget_s=args.budget, per_launch=args.round_sims, cfg=cfg,
+                              sim=sim2)
+    cfg_m = S.SurrogateConfig(**dict(cfg.__dict__, use_surrogate=False))
+    mlog = S.surrogate_search(spec, n, b, NL, seed=5, budget_s=args.budget, per_launch=args.round_sims, cfg=cfg_m,
+                              sim=sim2)
+    target = rlog.best[-1]
+    t_reach = slog.time_to_reach(target)
+    line = {"metric": "best makespan in %.0f s, surrogate vs plain search" % args.budget, "unit": "ns",
+            "higher_is_better": False, "n_gpus": 1,
+            "workload": "32x32 tiles, b=2048, levels 0..3, 32 CPU + 2 GPU-type processors",
+            "random": {"best": rlog.best[-1], "candidates": rlog.simulated[-1], "task_events": rlog.events[-1],
+                       "task_events_per_s": rlog.events[-1] / rlog.times[-1], "trace": list(zip(rlog.times, rlog.best))},
+            "surrogate": {"best": slog.best[-1], "candidates_simulated": slog.simulated[-1],
+                          "task_events": slog.events[-1], "trace": list(zip(slog.times, slog.best)),
+                          "rounds": slog.metrics},
+            "mutation_without_surrogate": {"best": mlog.best[-1], "candidates_simulated": mlog.simulated[-1],
+                                           "trace": list(zip(mlog.times, mlog.best)),
+                                           "time_to_random_best_s": mlog.time_to_reach(target)},
+            "surrogate_time_to_random_best_s": t_reach,
+            "time_ratio": (t_reach / rlog.times[-1]) if t_reach is not None else None}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,7 +502,25 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=256)
     ap.add_argument("--candidates", type=int, default=N_CAND,
                     help="candidates per step (default: the workload's 65,536; smaller only for profiling)")
+    ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search"],
+                    help="random: the default benchmark line; surrogate: label/train/rank/re-score "
+                         "pipeline; search: surrogate-guided vs random search")
+    ap.add_argument("--labels", type=int, default=1 << 20)
+    ap.add_argument("--proposals", type=int, default=1 << 22)
+    ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--budget", type=float, default=60.0)
+    ap.add_argument("--per-launch", type=int, default=4096)
+    ap.add_argument("--round-sims", type=int, default=1024)
+    ap.add_argument("--round-proposals", type=int, default=65536)
+    ap.add_argument("--round-steps", type=int, default=40)
+    ap.add_argument("--warmup-steps", type=int, default=200)
+    ap.add_argument("--p-mut", type=float, default=0.004)
+    ap.add_argument("--ws-gb", type=float, default=100.0)
     args = ap.parse_args()
+    if args.workload == "surrogate":
+        return run_surrogate_pipeline(args)
+    if args.workload == "search":
+        return run_search(args)
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -138,10 +138,13 @@ typedef struct {
 /* Bytes of device workspace needed to simulate candidates with at most
  * `max_tiles` tiles and split levels <= `max_level` on platform `p`, using up
  * to `n_cand` concurrent candidates (the library caps it at the number of
- * resident warps of the current device).  The workspace is caller-owned
- * device memory, 256-byte aligned, reused across calls on one stream. */
-int hesp_sim_workspace_size(const hesp_platform *p, int32_t max_tiles, int32_t max_level, int64_t n_cand,
-                            size_t *bytes_out);
+ * resident warps of the current device).  task_cap = 0 sizes each candidate's
+ * arena for the largest DAG these bounds allow; task_cap > 0 sizes it for
+ * that many tasks (and 4 dependence edges per task), and candidates that do
+ * not fit get HESP_ERR_CAPACITY.  The workspace is caller-owned device
+ * memory, 256-byte aligned, reused across calls on one stream. */
+int hesp_sim_workspace_size(const hesp_platform *p, int32_t max_tiles, int32_t max_level, int64_t task_cap,
+                            int64_t n_cand, size_t *bytes_out);
 
 /* Simulate n_cand candidates (HeSP Sec. 2.1: FCFS task order at release time,
  * EFT-P processor selection, write-back caching with prefetching transfers).
@@ -162,8 +165,8 @@ int hesp_sim_workspace_size(const hesp_platform *p, int32_t max_tiles, int32_t m
  * time.  The makespan is the largest finish time.
  *
  * Inputs (device): cands_dev[n_cand], levels_dev (int8, addressed through
- * level_offset).  max_tiles / max_level bound every candidate and must match
- * the workspace sizing.
+ * level_offset).  max_tiles / max_level / task_cap bound every candidate and
+ * must match the workspace sizing.
  * Outputs (device): makespan_dev[n_cand] (-1 on error), status_dev[n_cand]
  * (HESP_OK or HESP_ERR_ARG / _CAPACITY / _TIMEOUT / _STATE for that
  * candidate), ntasks_dev[n_cand] (nullable: task count of each candidate).
@@ -175,8 +178,8 @@ int hesp_sim_workspace_size(const hesp_platform *p, int32_t max_tiles, int32_t m
  * max_level; any size >= the size for n_cand = 1 works (fewer candidates then
  * run concurrently). */
 int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands_dev, const int8_t *levels_dev,
-                        int64_t n_cand, int32_t max_tiles, int32_t max_level, int64_t *makespan_dev,
-                        int32_t *status_dev, int64_t *ntasks_dev, const int64_t *sched_offsets_dev,
+                        int64_t n_cand, int32_t max_tiles, int32_t max_level, int64_t task_cap,
+                        int64_t *makespan_dev, int32_t *status_dev, int64_t *ntasks_dev, const int64_t *sched_offsets_dev,
                         int16_t *proc_dev, int64_t *start_dev, int64_t *finish_dev, void *workspace_dev,
                         size_t workspace_bytes, void *stream);
 
@@ -221,6 +224,14 @@ int hesp_simulate_batch_noalloc(const hesp_platform *p, const hesp_cand *cands_d
 int hesp_generate_candidates(int32_t kind, uint64_t seed, int64_t first, int64_t n_cand, int32_t n_tiles,
                              int32_t b, int32_t n_levels, hesp_cand *cands_dev, int8_t *levels_dev,
                              void *stream);
+
+/* Local proposals around parents (the "repartition" moves of the partition
+ * stage): proposal c copies parent (c mod n_parents) of parents_dev
+ * [n_parents, n_base] and redraws each level with probability p_mut
+ * (rounded to a multiple of 2^-16): the redraw test uses output k = 2t and
+ * the new level draw(n_levels) output k = 2t + 1 of candidate first + c. */
+int hesp_generate_mutants(const int8_t *parents_dev, int32_t n_parents, int32_t n_base, int32_t n_levels,
+                          double p_mut, uint64_t seed, int64_t first, int64_t n, int8_t *levels_dev, void *stream);
 
 /* Ragged batch: n = 4 + draw(29) at k = 0, b = {512, 1024, 2048}[draw(3)] at
  * k = 1, level of base task t from r = draw(10) at k = 2 + t mapped 0-4 -> 0,
@@ -310,6 +321,14 @@ int hesp_select_topk(const float *keys_dev, int64_t n, int64_t k, int64_t *idx_d
 int hesp_make_cands(const int64_t *idx_dev, int64_t k, int32_t n_tiles, int32_t b, hesp_cand *cands_dev,
                     void *stream);
 int hesp_gather_f32(const float *src_dev, const int64_t *idx_dev, int64_t k, float *dst_dev, void *stream);
+/* out_dev[0] = smallest makespan among candidates with status HESP_OK
+ * (INT64_MAX if none), out_dev[1] = their total task count (ntasks_dev
+ * nullable: 0). */
+int hesp_best_makespan(const int64_t *makespan_dev, const int32_t *status_dev, const int64_t *ntasks_dev, int64_t n,
+                       int64_t *out_dev, void *stream);
+/* dst_dev[i, :] = src_dev[idx_dev[i], :] for int8 rows of `width` bytes. */
+int hesp_gather_rows(const int8_t *src_dev, const int64_t *idx_dev, int64_t k, int64_t width, int8_t *dst_dev,
+                     void *stream);
 int hesp_rank_metrics_workspace_size(int64_t k, size_t *bytes_out);
 int hesp_rank_metrics(const float *pred_dev, const int64_t *makespan_dev, int64_t k, double mu, double sigma,
                       void *workspace_dev, size_t workspace_bytes, double *out_host, void *stream);

@@ -25,23 +25,27 @@ int64_t regions_uniform(int64_t n, int level) {
 
 static int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
 
-Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem) {
+Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem, int64_t task_cap) {
     Arena a;
     memset(&a, 0, sizeof a);
-    a.Tcap = tasks_uniform(max_tiles, max_level);
-    a.Ecap = regions_uniform(max_tiles, max_level);
+    const int64_t tb = tasks_uniform(max_tiles, max_level), eb = regions_uniform(max_tiles, max_level);
+    // without a cap the closed-form bounds hold every candidate; with one,
+    // larger candidates are reported as HESP_ERR_CAPACITY
+    a.Tcap = task_cap > 0 && task_cap < tb ? task_cap : tb;
+    a.Ecap = task_cap > 0 && 4 * a.Tcap < eb ? 4 * a.Tcap : eb;
     a.Acap = ((int64_t)max_tiles * (max_tiles + 1) / 2) << (2 * max_level);
     a.Kcap = (3LL << (2 * max_level)) + 1;
-    int64_t o = 0;
     const int64_t mp = n_mem <= 1 ? 0 : (n_mem == 2 ? 2 : 4);  // int64 words of coherence state per atom
+    const int64_t link_bytes = 32 * a.Tcap > 8 * a.Ecap ? 32 * a.Tcap : 8 * a.Ecap;
+    int64_t o = 0;
     a.off_desc = o; o = align256(o + 8 * a.Tcap);
     a.off_pending = o; o = align256(o + 2 * a.Tcap);
-    a.off_link = o; o = align256(o + 32 * a.Tcap);
+    a.off_link = o; o = align256(o + link_bytes);
+    a.off_epred = a.off_link;
+    a.off_esucc = a.off_link + 4 * a.Ecap;
     a.off_next = o; o = align256(o + 4 * a.Tcap);
     a.off_succoff = o; o = align256(o + 4 * (a.Tcap + 1));
     a.off_succ = o; o = align256(o + 4 * a.Ecap);
-    a.off_epred = o; o = align256(o + 4 * a.Ecap);
-    a.off_esucc = o; o = align256(o + 4 * a.Ecap);
     a.off_lw = o; o = align256(o + 4 * a.Acap);
     a.off_vfrom = o; o = align256(o + 8 * a.Acap * mp);
     a.off_bitmap = o; o = align256(o + 4 * ((a.Tcap + 31) / 32));
@@ -282,12 +286,12 @@ void hesp_dag_destroy(hesp_dag *d) {
 
 // ---------------------------------------------------------- simulation
 
-int hesp_sim_workspace_size(const hesp_platform *p, int32_t max_tiles, int32_t max_level, int64_t n_cand,
-                            size_t *bytes_out) {
-    if (!p || !bytes_out || n_cand < 0) return HESP_ERR_ARG;
+int hesp_sim_workspace_size(const hesp_platform *p, int32_t max_tiles, int32_t max_level, int64_t task_cap,
+                            int64_t n_cand, size_t *bytes_out) {
+    if (!p || !bytes_out || n_cand < 0 || task_cap < 0) return HESP_ERR_ARG;
     if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_level < 0 || max_level > HESP_MAX_LEVEL)
         return HESP_ERR_UNSUPPORTED;
-    const Arena ar = make_arena(max_tiles, max_level, p->n_mem);
+    const Arena ar = make_arena(max_tiles, max_level, p->n_mem, task_cap);
     int64_t resident = 0;
     const int rc = sim_slots_for(p, ar, &resident);
     if (rc) return rc;
@@ -298,10 +302,11 @@ int hesp_sim_workspace_size(const hesp_platform *p, int32_t max_tiles, int32_t m
 }
 
 int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands, const int8_t *levels, int64_t n_cand,
-                        int32_t max_tiles, int32_t max_level, int64_t *makespan, int32_t *status, int64_t *ntasks,
+                        int32_t max_tiles, int32_t max_level, int64_t task_cap, int64_t *makespan, int32_t *status,
+                        int64_t *ntasks,
                         const int64_t *sched_off, int16_t *sproc, int64_t *sstart, int64_t *sfinish, void *ws,
                         size_t ws_bytes, void *stream) {
-    if (!p || n_cand < 0) return HESP_ERR_ARG;
+    if (!p || n_cand < 0 || task_cap < 0) return HESP_ERR_ARG;
     if (n_cand == 0) return HESP_OK;
     if (!cands || !levels || !makespan || !status || !ws) return HESP_ERR_ARG;
     if (((uintptr_t)ws & 255) != 0) return HESP_ERR_ARG;
@@ -310,7 +315,7 @@ int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands, const in
     if (any_s && !all_s) return HESP_ERR_ARG;
     if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_level < 0 || max_level > HESP_MAX_LEVEL)
         return HESP_ERR_UNSUPPORTED;
-    const Arena ar = make_arena(max_tiles, max_level, p->n_mem);
+    const Arena ar = make_arena(max_tiles, max_level, p->n_mem, task_cap);
     if ((int64_t)ws_bytes < kWsHeaderBytes + ar.slot_bytes) return HESP_ERR_ARG;
     int64_t resident = 0;
     int rc = sim_slots_for(p, ar, &resident);
@@ -329,6 +334,16 @@ int hesp_generate_candidates(int32_t kind, uint64_t seed, int64_t first, int64_t
     if (kind != HESP_GEN_EXHAUSTIVE && kind != HESP_GEN_UNIFORM) return HESP_ERR_ARG;
     if (kind == HESP_GEN_UNIFORM && (n_levels < 1 || n_levels > HESP_MAX_LEVEL + 1)) return HESP_ERR_ARG;
     return launch_generate(kind, seed, first, n_cand, n_tiles, b, n_levels, cands, levels, (cudaStream_t)stream);
+}
+
+int hesp_generate_mutants(const int8_t *parents_dev, int32_t n_parents, int32_t n_base, int32_t n_levels,
+                          double p_mut, uint64_t seed, int64_t first, int64_t n, int8_t *levels_dev, void *stream) {
+    if (!parents_dev || !levels_dev || n_parents < 1 || n_base < 1 || n_levels < 1 || n_levels > 127 || n < 0 ||
+        first < 0 || !(p_mut >= 0.0 && p_mut <= 1.0))
+        return HESP_ERR_ARG;
+    const uint32_t p_num = (uint32_t)(p_mut * 65536.0 + 0.5);
+    return launch_mutate(parents_dev, n_parents, n_base, n_levels, p_num, seed, first, n, levels_dev,
+                         (cudaStream_t)stream);
 }
 
 int hesp_generate_uneven(uint64_t seed, int64_t first, int64_t n_cand, hesp_cand *cands, int8_t *levels,

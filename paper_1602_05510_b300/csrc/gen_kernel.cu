@@ -101,6 +101,24 @@ __global__ void uneven_fill_kernel(uint64_t seed, int64_t first, int64_t n_cand,
     }
 }
 
+// Mutants of parent partition vectors: proposal c copies parent
+// (c mod n_parents) and redraws each level with probability p_num / 2^16
+// (draw at k = 2 t from SplitMix64(seed, first + c); new level at k = 2 t + 1).
+__global__ void mutate_kernel(const int8_t *parents, int n_parents, int nb, int n_levels, uint32_t p_num,
+                              uint64_t seed, int64_t first, int64_t n, int8_t *out) {
+    const int64_t c = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    if (c >= n) return;
+    const uint64_t cg = (uint64_t)(first + c);
+    const int8_t *par = parents + (c % n_parents) * (int64_t)nb;
+    int8_t *row = out + c * nb;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+        int8_t v = par[t];
+        if (draw(sm64_at(seed, cg, 2 * (uint64_t)t), 65536u) < p_num)
+            v = (int8_t)draw(sm64_at(seed, cg, 2 * (uint64_t)t + 1), (uint32_t)n_levels);
+        row[t] = v;
+    }
+}
+
 dim3 cand_grid(int64_t n_cand) {
     const int64_t gx = n_cand < 65535 ? n_cand : 65535;
     return dim3((unsigned)gx, (unsigned)((n_cand + gx - 1) / gx));
@@ -114,6 +132,13 @@ int launch_generate(int32_t kind, uint64_t seed, int64_t first, int64_t n_cand, 
     const int nb = n_tiles * (n_tiles + 1) * (n_tiles + 2) / 6;
     gen_fixed_kernel<<<cand_grid(n_cand), 128, 0, stream>>>(kind, seed, first, n_cand, nb, n_levels, n_tiles, b,
                                                              cands, levels);
+    return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
+}
+
+int launch_mutate(const int8_t *parents, int32_t n_parents, int32_t n_base, int32_t n_levels, uint32_t p_num,
+                  uint64_t seed, int64_t first, int64_t n, int8_t *out, cudaStream_t stream) {
+    if (n == 0) return HESP_OK;
+    mutate_kernel<<<cand_grid(n), 128, 0, stream>>>(parents, n_parents, n_base, n_levels, p_num, seed, first, n, out);
     return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
 }
 

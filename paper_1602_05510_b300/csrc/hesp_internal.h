@@ -46,6 +46,9 @@ struct Arena {
     int64_t Ecap;  // dependence edges
     int64_t Acap;  // atoms
     int64_t Kcap;  // transfer-table entries (atoms per task + 1)
+    // The edge lists of the dependence build (epred, esucc) live in the FIFO
+    // link area and the per-task marks in the successor offsets: neither is
+    // in use at the same time as what it shares memory with.
     int64_t off_desc, off_pending, off_link, off_next, off_succoff, off_succ, off_epred, off_esucc, off_lw,
         off_vfrom, off_bitmap, off_xt;
 };
@@ -60,7 +63,7 @@ constexpr int64_t kWsHeaderBytes = 256;
 // Closed forms used to size arenas (host side).
 int64_t tasks_uniform(int64_t n, int level);  // tasks when every base task is split `level` times
 int64_t regions_uniform(int64_t n, int level); // sum over those tasks of their region count
-Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem);
+Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem, int64_t task_cap);
 
 int sim_slots_for(const hesp_platform *p, const Arena &ar, int64_t *resident_warps);  // device resident warps
 int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, int64_t n_slots,
@@ -72,6 +75,8 @@ int sim_bitmap_smem_words(int64_t Tcap);
 
 int launch_generate(int32_t kind, uint64_t seed, int64_t first, int64_t n_cand, int32_t n_tiles, int32_t b,
                     int32_t n_levels, hesp_cand *cands, int8_t *levels, cudaStream_t stream);
+int launch_mutate(const int8_t *parents, int32_t n_parents, int32_t n_base, int32_t n_levels, uint32_t p_num,
+                  uint64_t seed, int64_t first, int64_t n, int8_t *out, cudaStream_t stream);
 int launch_generate_uneven(uint64_t seed, int64_t first, int64_t n_cand, hesp_cand *cands, int8_t *levels,
                            int64_t levels_cap, int64_t *levels_used, cudaStream_t stream);
 

@@ -53,7 +53,7 @@ extern "C" int hesp_simulate_batch_noalloc(const hesp_platform *p, const hesp_ca
     if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_level < 0 || max_level > HESP_MAX_LEVEL)
         return HESP_ERR_UNSUPPORTED;
     // One candidate arena (plus the work-counter header) must fit the array.
-    const hesp::Arena ar = hesp::make_arena(max_tiles, max_level, p->n_mem);
+    const hesp::Arena ar = hesp::make_arena(max_tiles, max_level, p->n_mem, 0);
     if (hesp::kWsHeaderBytes + ar.slot_bytes > (int64_t)HESP_NOALLOC_SCRATCH_BYTES) return HESP_ERR_CAPACITY;
     if (n_cand == 0) return HESP_OK;
     void *scratch = nullptr;
@@ -62,7 +62,7 @@ extern "C" int hesp_simulate_batch_noalloc(const hesp_platform *p, const hesp_ca
     // The work counter at the head of the array is reset by every launch and
     // every arena is fully re-initialised per candidate, so nothing left by an
     // earlier call is read.
-    return hesp_simulate_batch(p, cands_dev, levels_dev, n_cand, max_tiles, max_level, makespan_dev, status_dev,
+    return hesp_simulate_batch(p, cands_dev, levels_dev, n_cand, max_tiles, max_level, 0, makespan_dev, status_dev,
                                ntasks_dev, sched_offsets_dev, proc_dev, start_dev, finish_dev, scratch,
                                (size_t)HESP_NOALLOC_SCRATCH_BYTES, stream);
 }

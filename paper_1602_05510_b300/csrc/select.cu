@@ -142,6 +142,14 @@ __global__ void cands_kernel(const int64_t *idx, int64_t k, int n_tiles, int b, 
     out[i] = c;
 }
 
+__global__ void gather_rows_kernel(const int8_t *src, const int64_t *idx, int64_t k, int64_t width, int8_t *dst) {
+    const int64_t r = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    if (r >= k) return;
+    const int8_t *s = src + idx[r] * width;
+    int8_t *d = dst + r * width;
+    for (int64_t c = threadIdx.x; c < width; c += blockDim.x) d[c] = s[c];
+}
+
 __global__ void gather_float_kernel(const float *src, const int64_t *idx, int64_t k, float *dst) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < k) dst[i] = src[idx[i]];
@@ -220,6 +228,32 @@ __global__ void final_kernel(const double *rel, const double *rp, const double *
     }
 }
 
+// out[0] = min makespan over candidates with status 0 (INT64_MAX if none),
+// out[1] = their task count (one block, deterministic).
+__global__ void best_kernel(const int64_t *ms, const int32_t *status, const int64_t *ntasks, int64_t n, int64_t *out) {
+    __shared__ int64_t sm[1024], se[1024];
+    int64_t m = INT64_MAX, e = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+        if (status[i] == 0) {
+            m = min(m, ms[i]);
+            if (ntasks) e += ntasks[i];
+        }
+    sm[threadIdx.x] = m;
+    se[threadIdx.x] = e;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sm[threadIdx.x] = min(sm[threadIdx.x], sm[threadIdx.x + o]);
+            se[threadIdx.x] += se[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sm[0];
+        out[1] = se[0];
+    }
+}
+
 constexpr int64_t kChunk = 4096;
 
 }  // namespace
@@ -279,6 +313,23 @@ int hesp_gather_f32(const float *src_dev, const int64_t *idx_dev, int64_t k, flo
     if (!src_dev || !idx_dev || !dst_dev || k < 0) return HESP_ERR_ARG;
     if (k == 0) return HESP_OK;
     gather_float_kernel<<<(unsigned)((k + 255) / 256), 256, 0, (cudaStream_t)stream>>>(src_dev, idx_dev, k, dst_dev);
+    return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
+}
+
+int hesp_gather_rows(const int8_t *src_dev, const int64_t *idx_dev, int64_t k, int64_t width, int8_t *dst_dev,
+                     void *stream) {
+    if (!src_dev || !idx_dev || !dst_dev || k < 0 || width < 1) return HESP_ERR_ARG;
+    if (k == 0) return HESP_OK;
+    const int64_t gx = k < 65535 ? k : 65535;
+    gather_rows_kernel<<<dim3((unsigned)gx, (unsigned)((k + gx - 1) / gx)), 128, 0, (cudaStream_t)stream>>>(
+        src_dev, idx_dev, k, width, dst_dev);
+    return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
+}
+
+int hesp_best_makespan(const int64_t *makespan_dev, const int32_t *status_dev, const int64_t *ntasks_dev, int64_t n,
+                       int64_t *out_dev, void *stream) {
+    if (!makespan_dev || !status_dev || !out_dev || n < 0) return HESP_ERR_ARG;
+    best_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(makespan_dev, status_dev, ntasks_dev, n, out_dev);
     return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
 }
 

@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
         int64_t E = 0;
         if (status == HESP_OK) {
             int32_t *const lw = at<int32_t>(base, a.ar.off_lw);
-            int32_t *const mark = at<int32_t>(base, a.ar.off_link);  // FIFO links are not in use yet
+            int32_t *const mark = at<int32_t>(base, a.ar.off_succoff);  // offsets are built after this phase
             int32_t *const scnt = at<int32_t>(base, a.ar.off_next);
             int32_t *const epred = at<int32_t>(base, a.ar.off_epred);
             int32_t *const esucc = at<int32_t>(base, a.ar.off_esucc);

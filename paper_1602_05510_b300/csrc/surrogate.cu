@@ -81,25 +81,44 @@ __global__ void to_bf16_kernel(const float *src, __nv_bfloat16 *dst, __nv_bfloat
     }
 }
 
-// X[b, f] = (levels[b, f / NL] == f % NL); optionally XT[f, b].
-__global__ void onehot_kernel(const int8_t *lv, int64_t lv_stride, int B, int n_base, int NL, int64_t Fp,
-                              __nv_bfloat16 *X, __nv_bfloat16 *XT, int ldt) {
-    const int64_t total = (int64_t)B * Fp;
-    const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
+// X[b, f] = (levels[b, f / NL] == f % NL): one thread writes 8 columns
+// (16 bytes) of one row.
+__global__ void onehot_kernel(const int8_t *lv, int lv_stride, int B, int n_base, int NL, int Fp, __nv_bfloat16 *X) {
+    const int chunks = Fp >> 3;
+    const int64_t total = (int64_t)B * chunks;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = i / Fp, f = i % Fp;
-        const int t = (int)(f / NL);
-        const bool on = t < n_base && lv[b * lv_stride + t] == (int8_t)(f % NL);
-        X[i] = on ? one : zero;
-    }
-    if (XT) {
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-             i += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t f = i / B, b = i % B;
-            const int t = (int)(f / NL);
-            const bool on = t < n_base && lv[b * lv_stride + t] == (int8_t)(f % NL);
-            XT[f * ldt + b] = on ? one : zero;
+        const int b = (int)(i / chunks), f0 = (int)(i % chunks) << 3;
+        int t = f0 / NL, v = f0 - t * NL;
+        int cur = t < n_base ? lv[(int64_t)b * lv_stride + t] : -1;
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+            uint32_t lo = (cur == v) ? 0x3F80u : 0u;  // bf16 1.0
+            if (++v == NL) { v = 0; ++t; cur = t < n_base ? lv[(int64_t)b * lv_stride + t] : -1; }
+            uint32_t hi = (cur == v) ? 0x3F80u : 0u;
+            if (++v == NL) { v = 0; ++t; cur = t < n_base ? lv[(int64_t)b * lv_stride + t] : -1; }
+            w[q >> 1] = lo | (hi << 16);
         }
+        *reinterpret_cast<uint4 *>(X + (int64_t)b * Fp + f0) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// XT[f, b] = X[b, f]: one thread writes 8 rows-of-b (16 bytes) of one feature.
+__global__ void onehot_t_kernel(const int8_t *lv, int lv_stride, int B, int n_base, int NL, int Fp,
+                                __nv_bfloat16 *XT) {
+    const int chunks = B >> 3;
+    const int64_t total = (int64_t)Fp * chunks;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int f = (int)(i / chunks), b0 = (int)(i % chunks) << 3;
+        const int t = f / NL, v = f - t * NL;
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+            const bool a = t < n_base && lv[(int64_t)(b0 + q) * lv_stride + t] == v;
+            const bool c = t < n_base && lv[(int64_t)(b0 + q + 1) * lv_stride + t] == v;
+            w[q >> 1] = (a ? 0x3F80u : 0u) | ((c ? 0x3F80u : 0u) << 16);
+        }
+        *reinterpret_cast<uint4 *>(XT + (int64_t)f * B + b0) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
@@ -278,8 +297,11 @@ int forward(hesp_surrogate *s, const int8_t *lv, int B, const int64_t *ms, float
             bool backward) {
     const int H = s->H;
     const int64_t Fp = s->Fp;
-    onehot_kernel<<<grid_for((int64_t)B * Fp), 256, 0, st>>>(lv, s->n_base, B, s->n_base, s->n_levels, Fp, s->X,
-                                                              backward ? s->XT : nullptr, B);
+    onehot_kernel<<<grid_for((int64_t)B * (Fp / 8)), 256, 0, st>>>(lv, s->n_base, B, s->n_base, s->n_levels,
+                                                                    (int)Fp, s->X);
+    if (backward)
+        onehot_t_kernel<<<grid_for((int64_t)Fp * (B / 8)), 256, 0, st>>>(lv, s->n_base, B, s->n_base, s->n_levels,
+                                                                          (int)Fp, s->XT);
     CK(cudaGetLastError());
     RC(gemm(s->X, Fp, s->W1b, Fp, B, H, (int)Fp, 1, nullptr, 0, s->b1, s->A1, H, backward ? s->A1T : nullptr, B,
             nullptr, 0, s->err, st));

@@ -34,6 +34,7 @@ EXPORTS = (
     "hesp_surrogate_set", "hesp_surrogate_grad", "hesp_surrogate_adam", "hesp_surrogate_train",
     "hesp_surrogate_infer", "hesp_surrogate_error", "hesp_select_workspace_size", "hesp_select_topk",
     "hesp_make_cands", "hesp_gather_f32", "hesp_rank_metrics_workspace_size", "hesp_rank_metrics",
+    "hesp_generate_mutants", "hesp_gather_rows", "hesp_best_makespan",
 )
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -87,8 +88,8 @@ def lib():
         L.hesp_dag_count_tasks.argtypes = [vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.hesp_dag_destroy.argtypes = [vp]
         L.hesp_dag_destroy.restype = None
-        L.hesp_sim_workspace_size.argtypes = [vp, i32, i32, i64, ctypes.POINTER(sz)]
-        L.hesp_simulate_batch.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.hesp_sim_workspace_size.argtypes = [vp, i32, i32, i64, i64, ctypes.POINTER(sz)]
+        L.hesp_simulate_batch.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         L.hesp_simulate_batch_noalloc.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.hesp_gemm_bf16.argtypes = [i32, i32, i32, vp, i64, vp, i64, i32, vp, i64, vp, vp, i64, vp, i64, vp, i64,
                                      vp, vp]
@@ -113,6 +114,9 @@ def lib():
         L.hesp_gather_f32.argtypes = [vp, vp, i64, vp, vp]
         L.hesp_rank_metrics_workspace_size.argtypes = [i64, ctypes.POINTER(sz)]
         L.hesp_rank_metrics.argtypes = [vp, vp, i64, f64, f64, vp, sz, ctypes.POINTER(f64), vp]
+        L.hesp_best_makespan.argtypes = [vp, vp, vp, i64, vp, vp]
+        L.hesp_gather_rows.argtypes = [vp, vp, i64, i64, vp, vp]
+        L.hesp_generate_mutants.argtypes = [vp, i32, i32, i32, ctypes.c_double, u64, i64, i64, vp, vp]
         L.hesp_generate_candidates.argtypes = [i32, u64, i64, i64, i32, i32, i32, vp, vp, vp]
         L.hesp_generate_uneven.argtypes = [u64, i64, i64, vp, vp, i64, vp, vp]
         _lib = L
@@ -218,20 +222,27 @@ def cands_tensor(n_tiles, b, offsets, device="cuda"):
     return torch.from_numpy(a.view(np.uint8).copy()).to(device)
 
 
-def workspace_bytes(platform: Platform, max_tiles, max_level, n_cand):
+def workspace_bytes(platform: Platform, max_tiles, max_level, n_cand, task_cap=0):
     v = ctypes.c_size_t()
-    check(lib().hesp_sim_workspace_size(platform.h, max_tiles, max_level, n_cand, ctypes.byref(v)),
+    check(lib().hesp_sim_workspace_size(platform.h, max_tiles, max_level, task_cap, n_cand, ctypes.byref(v)),
           "hesp_sim_workspace_size")
     return v.value
 
 
-def alloc_workspace(platform: Platform, max_tiles, max_level, n_cand):
+def alloc_workspace(platform: Platform, max_tiles, max_level, n_cand, task_cap=0, max_bytes=None):
+    """Workspace for up to n_cand concurrent candidates (fewer if max_bytes
+    would be exceeded)."""
     import torch
-    return torch.empty(workspace_bytes(platform, max_tiles, max_level, n_cand), dtype=torch.uint8, device="cuda")
+    nbytes = workspace_bytes(platform, max_tiles, max_level, n_cand, task_cap)
+    if max_bytes is not None and nbytes > max_bytes:
+        one = workspace_bytes(platform, max_tiles, max_level, 1, task_cap)
+        slot = max(1, workspace_bytes(platform, max_tiles, max_level, 2, task_cap) - one)
+        nbytes = max(one, one + (max_bytes - one) // slot * slot)
+    return torch.empty(nbytes, dtype=torch.uint8, device="cuda")
 
 
 def simulate_batch(platform: Platform, cands, levels, n_cand, max_tiles, max_level, workspace,
-                   makespan=None, status=None, ntasks=None, schedule=None, stream=None):
+                   makespan=None, status=None, ntasks=None, schedule=None, stream=None, task_cap=0):
     """Launch hesp_simulate_batch on the current stream.  `cands` is a byte
     tensor of hesp_cand, `levels` an int8 device tensor.  `schedule` is None
     or (offsets int64, proc int16, start int64, finish int64) device tensors.
@@ -245,7 +256,7 @@ def simulate_batch(platform: Platform, cands, levels, n_cand, max_tiles, max_lev
     so = sp = ss = sf = None
     if schedule is not None:
         so, sp, ss, sf = schedule
-    check(lib().hesp_simulate_batch(platform.h, _ptr(cands), _ptr(levels), n_cand, max_tiles, max_level,
+    check(lib().hesp_simulate_batch(platform.h, _ptr(cands), _ptr(levels), n_cand, max_tiles, max_level, task_cap,
                                     _ptr(makespan), _ptr(status), _ptr(ntasks), _ptr(so), _ptr(sp), _ptr(ss),
                                     _ptr(sf), _ptr(workspace), workspace.numel(), _stream(stream)),
           "hesp_simulate_batch")
@@ -277,6 +288,11 @@ def simulate_batch_noalloc(platform: Platform, cands, levels, n_cand, max_tiles,
 def generate_candidates(kind, seed, first, n_cand, n_tiles, b, n_levels, levels, cands=None, stream=None):
     check(lib().hesp_generate_candidates(kind, seed, first, n_cand, n_tiles, b, n_levels, _ptr(cands),
                                          _ptr(levels), _stream(stream)), "hesp_generate_candidates")
+
+
+def generate_mutants(parents, n_parents, n_base, n_levels, p_mut, seed, first, n, levels, stream=None):
+    check(lib().hesp_generate_mutants(_ptr(parents), n_parents, n_base, n_levels, p_mut, seed, first, n,
+                                      _ptr(levels), _stream(stream)), "hesp_generate_mutants")
 
 
 def generate_uneven(seed, first, n_cand, cands, levels, levels_used, stream=None):
@@ -424,3 +440,24 @@ def rank_metrics(pred, makespan, mu, sigma, stream=None):
     check(lib().hesp_rank_metrics(_ptr(pred), _ptr(makespan), k, mu, sigma, _ptr(ws), sz.value, out,
                                   _stream(stream)), "hesp_rank_metrics")
     return out[0], out[1]
+
+
+def gather_rows(src, idx, width, dst=None, stream=None):
+    """dst[i, :] = src[idx[i], :] for int8 rows (device tensors)."""
+    import torch
+    k = idx.numel()
+    if dst is None:
+        dst = torch.empty(k * width, dtype=torch.int8, device=src.device)
+    check(lib().hesp_gather_rows(_ptr(src), _ptr(idx), k, width, _ptr(dst), _stream(stream)), "hesp_gather_rows")
+    return dst
+
+
+def best_makespan(makespan, status, ntasks=None, out=None, stream=None):
+    """Device int64 [2]: smallest makespan among successful candidates, and
+    their task count."""
+    import torch
+    if out is None:
+        out = torch.empty(2, dtype=torch.int64, device=makespan.device)
+    check(lib().hesp_best_makespan(_ptr(makespan), _ptr(status), _ptr(ntasks), makespan.numel(), _ptr(out),
+                                   _stream(stream)), "hesp_best_makespan")
+    return out

@@ -1,0 +1,206 @@
+"""Partition search on the GPU: plain batched random search, and
+surrogate-guided search (the partition stage of HeSP's iterative solver,
+Sec. 2.1, with proposals ranked by the learned surrogate and only the
+best-ranked slice simulated exactly).
+
+Orchestration only: every step runs in libhesp.so kernels (candidate and
+mutant generation, simulation, surrogate training and inference, top-k
+selection, gathers, rank metrics).  The host keeps the bookkeeping that
+needs a few bytes per candidate: the best makespan found and the elite set.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+from . import hesp
+from . import workloads as W
+
+
+@dataclass
+class SearchLog:
+    arm: str
+    times: List[float] = field(default_factory=list)    # seconds since start
+    best: List[int] = field(default_factory=list)       # best makespan so far (ns)
+    events: List[int] = field(default_factory=list)     # task-events simulated so far
+    simulated: List[int] = field(default_factory=list)  # candidates simulated so far
+    metrics: List[dict] = field(default_factory=list)   # per-round surrogate metrics
+
+    def best_at(self, t: float) -> Optional[int]:
+        b = None
+        for tt, v in zip(self.times, self.best):
+            if tt <= t:
+                b = v
+        return b
+
+    def time_to_reach(self, target: int) -> Optional[float]:
+        for tt, v in zip(self.times, self.best):
+            if v <= target:
+                return tt
+        return None
+
+
+class Simulator:
+    """Batched exact simulation of fixed-size candidates of one workload."""
+
+    def __init__(self, spec, n_tiles, b, max_level, per_launch, task_cap=0, ws_bytes=None):
+        import torch
+        self.plat = hesp.Platform(spec)
+        self.n_tiles, self.b, self.max_level, self.per_launch, self.task_cap = n_tiles, b, max_level, per_launch, task_cap
+        self.nb = W.base_count(n_tiles)
+        self.ws = hesp.alloc_workspace(self.plat, n_tiles, max_level, per_launch, task_cap, max_bytes=ws_bytes)
+        self.cands = hesp.cands_tensor(n_tiles, b, np.arange(per_launch, dtype=np.int64) * self.nb)
+        self.ms = torch.empty(per_launch, dtype=torch.int64, device="cuda")
+        self.st = torch.empty(per_launch, dtype=torch.int32, device="cuda")
+        self.nt = torch.empty(per_launch, dtype=torch.int64, device="cuda")
+
+    def run(self, levels, n=None, cands=None):
+        n = self.per_launch if n is None else n
+        hesp.simulate_batch(self.plat, self.cands if cands is None else cands, levels, n, self.n_tiles,
+                            self.max_level, self.ws, makespan=self.ms, status=self.st, ntasks=self.nt,
+                            task_cap=self.task_cap)
+        return self.ms[:n], self.st[:n], self.nt[:n]
+
+
+def random_search(spec, n_tiles, b, n_levels, seed, budget_s, per_launch=4096, task_cap=0, ws_bytes=None,
+                  sim: Optional[Simulator] = None) -> SearchLog:
+    """Uniform random partition vectors, per_launch per simulation launch,
+    until budget_s of wall time have passed."""
+    import torch
+    sim = sim or Simulator(spec, n_tiles, b, n_levels - 1, per_launch, task_cap, ws_bytes)
+    nb = sim.nb
+    levels = torch.empty(per_launch * nb, dtype=torch.int8, device="cuda")
+    log = SearchLog("random")
+    best, events, done, k = None, 0, 0, 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while True:
+        hesp.generate_candidates(hesp.GEN_UNIFORM, seed, k * per_launch, per_launch, n_tiles, b, n_levels, levels)
+        ms, st, nt = sim.run(levels)
+        m, ev = (int(v) for v in hesp.best_makespan(ms, st, nt).cpu().numpy())
+        events += ev
+        done += per_launch
+        best = m if best is None else min(best, m)
+        el = time.perf_counter() - t0
+        log.times.append(el)
+        log.best.append(best)
+        log.events.append(events)
+        log.simulated.append(done)
+        k += 1
+        if el >= budget_s:
+            break
+    return log
+
+
+@dataclass
+class SurrogateConfig:
+    hidden: int = 512
+    batch: int = 4096
+    lr: float = 1e-3
+    warmup_launches: int = 2       # random launches labelled before the first training
+    warmup_steps: int = 300
+    steps_per_round: int = 60
+    proposals: int = 131072        # proposals ranked per round
+    random_fraction: float = 0.25  # share of proposals drawn uniformly (the rest mutate elites)
+    elites: int = 64
+    p_mut: float = 0.01
+    label_cap: int = 1 << 20
+    infer_chunk: int = 16384       # rows per inference launch (activation buffers)
+    use_surrogate: bool = True     # False: simulate random mutants (the same search without the model)
+
+
+def surrogate_search(spec, n_tiles, b, n_levels, seed, budget_s, per_launch=4096, cfg: SurrogateConfig = None,
+                     task_cap=0, ws_bytes=None, sim: Optional[Simulator] = None) -> SearchLog:
+    """Each round: mutate the elite partitions (and draw some uniform ones),
+    rank all proposals with the surrogate, simulate the per_launch best-ranked
+    exactly, add them to the labels, retrain briefly."""
+    import torch
+    cfg = cfg or SurrogateConfig()
+    sim = sim or Simulator(spec, n_tiles, b, n_levels - 1, per_launch, task_cap, ws_bytes)
+    nb = sim.nb
+    P = cfg.proposals
+    n_rand = int(P * cfg.random_fraction) // 64 * 64
+    lab_lv = torch.empty(cfg.label_cap * nb, dtype=torch.int8, device="cuda")
+    lab_ms = torch.empty(cfg.label_cap, dtype=torch.int64, device="cuda")
+    host_ms = np.empty(cfg.label_cap, np.int64)
+    prop = torch.empty(P * nb, dtype=torch.int8, device="cuda")
+    pred = torch.empty(P, dtype=torch.float32, device="cuda")
+    parents = torch.empty(cfg.elites * nb, dtype=torch.int8, device="cuda")
+    sur = hesp.Surrogate(nb, n_levels, cfg.hidden, max(cfg.batch, cfg.infer_chunk), seed=seed)
+    log = SearchLog("surrogate" if cfg.use_surrogate else "mutation")
+    n_lab, best, events, done, rnd = 0, None, 0, 0, 0
+    big = np.iinfo(np.int64).max
+
+    def add(levels_rows, ms, st, nt, count):
+        # failed candidates (none are expected) keep the largest makespan
+        nonlocal n_lab, best, events, done
+        take = min(count, cfg.label_cap - n_lab)
+        if take > 0:
+            lab_lv[n_lab * nb:(n_lab + take) * nb].copy_(levels_rows[:take * nb])
+            lab_ms[n_lab:n_lab + take].copy_(ms[:take])
+            h_ms, h_st = ms[:take].cpu().numpy(), st[:take].cpu().numpy()
+            host_ms[n_lab:n_lab + take] = np.where(h_st == 0, h_ms, big)
+            n_lab += take
+        m, ev = (int(v) for v in hesp.best_makespan(ms, st, nt).cpu().numpy())
+        events += ev
+        done += count
+        best = m if best is None else min(best, m)
+
+    def record(t0, extra=None):
+        log.times.append(time.perf_counter() - t0)
+        log.best.append(best)
+        log.events.append(events)
+        log.simulated.append(done)
+        if extra is not None:
+            log.metrics.append(extra)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    # warm-up labels from uniform random partitions
+    for w in range(cfg.warmup_launches):
+        hesp.generate_candidates(hesp.GEN_UNIFORM, seed, w * per_launch, per_launch, n_tiles, b, n_levels, prop)
+        ms, st, nt = sim.run(prop)
+        add(prop, ms, st, nt, per_launch)
+        record(t0)
+    sur.fit_stats(lab_ms[:n_lab])
+    mu, sigma, _ = sur.stats()
+    if cfg.use_surrogate:
+        sur.train(lab_lv, lab_ms, n_lab, cfg.batch, cfg.warmup_steps, cfg.lr, seed=seed + 1)
+    first_prop = 1 << 40
+    while time.perf_counter() - t0 < budget_s:
+        # proposals: mutants of the elites, plus some uniform draws
+        el_idx = np.argsort(host_ms[:n_lab], kind="stable")[:cfg.elites]
+        hesp.gather_rows(lab_lv, torch.from_numpy(el_idx.astype(np.int64)).cuda(), nb, parents)
+        n_mut = P - n_rand
+        hesp.generate_mutants(parents, len(el_idx), nb, n_levels, cfg.p_mut, seed + 7, first_prop + rnd * P, n_mut,
+                              prop)
+        if n_rand:
+            hesp.generate_candidates(hesp.GEN_UNIFORM, seed + 3, rnd * n_rand, n_rand, n_tiles, b, n_levels,
+                                     prop[n_mut * nb:])
+        if cfg.use_surrogate:
+            sur.infer(prop, P, pred)
+            idx = hesp.select_topk(pred, per_launch)
+        else:
+            # the same proposals, a random sample of them simulated (proposals
+            # are independent draws, so the first ones of each kind are one)
+            k_rand = int(per_launch * cfg.random_fraction) if n_rand else 0
+            idx = torch.from_numpy(np.concatenate([np.arange(per_launch - k_rand),
+                                                   n_mut + np.arange(k_rand)]).astype(np.int64)).cuda()
+        cands = hesp.make_cands(idx, n_tiles, b)
+        ms, st, nt = sim.run(prop, per_launch, cands)
+        rel = rho = float("nan")
+        if cfg.use_surrogate:
+            sel_pred = hesp.gather_f32(pred, idx)
+            okm = st == 0
+            if int(okm.sum().item()) > 1:
+                rel, rho = hesp.rank_metrics(sel_pred[okm], ms[okm], mu, sigma)
+        rows = hesp.gather_rows(prop, idx, nb)
+        add(rows, ms, st, nt, per_launch)
+        record(t0, {"round": rnd, "rel_err": rel, "spearman": rho, "labels": n_lab})
+        if cfg.use_surrogate:
+            sur.train(lab_lv, lab_ms, n_lab, cfg.batch, cfg.steps_per_round, cfg.lr, seed=seed + 100 + rnd)
+        rnd += 1
+    return log

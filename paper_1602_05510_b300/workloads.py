@@ -222,3 +222,18 @@ def surrogate_init(seed: int, F: int, Fp: int, H: int):
     return dict(W1=he_uniform(seed, 0, H, Fp, F, F), b1=np.zeros(H, np.float32),
                 W2=he_uniform(seed, 1, H, H, H), b2=np.zeros(H, np.float32),
                 w3=he_uniform(seed, 2, 1, H, H).reshape(H), b3=np.zeros(1, np.float32))
+
+
+def mutants(parents: np.ndarray, n_levels: int, p_mut: float, seed: int, first: int, n: int) -> np.ndarray:
+    """Proposal c copies parent c mod len(parents) and redraws each level with
+    probability round(p_mut 2^16) / 2^16 (test at output k = 2t, new level at
+    k = 2t + 1 of candidate first + c)."""
+    parents = np.asarray(parents, np.int8)
+    P, nb = parents.shape
+    p_num = np.uint64(int(p_mut * 65536.0 + 0.5))
+    c = np.arange(first, first + n, dtype=np.uint64)[:, None]
+    t = np.arange(nb, dtype=np.uint64)[None, :]
+    redraw = draw(counter_u64(seed, c, 2 * t), 65536) < p_num
+    new = draw(counter_u64(seed, c, 2 * t + np.uint64(1)), n_levels).astype(np.int8)
+    base = parents[np.arange(n) % P]
+    return np.where(redraw, new, base).astype(np.int8)

@@ -1,0 +1,40 @@
+"""Search drivers on the GPU (small budgets): plain random search and
+surrogate-guided search both return monotone best-so-far traces whose best
+makespans are real simulation results, and the surrogate rounds report
+finite relative error and rank correlation."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1602_05510_b300 import search as S  # noqa: E402
+from paper_1602_05510_b300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1602_05510_b300 import build
+    build.build()
+
+
+def test_random_and_surrogate_search_small():
+    spec = W.PLATFORMS["cfg1a"]
+    r = S.random_search(spec, 8, 2048, 3, seed=5, budget_s=0.0, per_launch=2048)  # one launch
+    cfg = S.SurrogateConfig(hidden=128, batch=1024, warmup_launches=2, warmup_steps=50, steps_per_round=10,
+                            proposals=16384, elites=16, label_cap=1 << 16)
+    s = S.surrogate_search(spec, 8, 2048, 3, seed=5, budget_s=3.0, per_launch=2048, cfg=cfg)
+    assert len(r.best) == 1 and len(s.best) >= 3
+    for log in (r, s):
+        assert all(a >= b for a, b in zip(log.best, log.best[1:]))
+        assert all(a <= b for a, b in zip(log.events, log.events[1:]))
+    assert s.metrics and all(np.isfinite(m["rel_err"]) and -1 <= m["spearman"] <= 1 for m in s.metrics)
+    # the random arm's best is the makespan of one of its uniform candidates
+    lv = W.uniform_levels(5, 0, 2048, 120, 3)
+    pl = O.make_platform(spec)
+    first = min(O.simulate(pl, 8, 2048, lv[c], schedule=False)["makespan"] for c in range(0, 2048, 97))
+    assert r.best[0] <= first

@@ -29,7 +29,7 @@ def _cuda():
     build.build()
 
 
-def gpu_sim(spec, n, b, levels, max_level=None, schedule=False, max_tiles=None, ws_cands=None):
+def gpu_sim(spec, n, b, levels, max_level=None, schedule=False, max_tiles=None, ws_cands=None, task_cap=0):
     """Run one batch of candidates of the same (n, b) on the GPU."""
     levels = np.ascontiguousarray(levels, np.int8)
     C, nb = levels.shape
@@ -38,7 +38,8 @@ def gpu_sim(spec, n, b, levels, max_level=None, schedule=False, max_tiles=None, 
     plat = hesp.Platform(spec)
     lv = torch.from_numpy(levels.reshape(-1).copy()).cuda()
     cands = hesp.cands_tensor(n, b, np.arange(C, dtype=np.int64) * nb)
-    ws = hesp.alloc_workspace(plat, max_tiles, max_level, C if ws_cands is None else ws_cands)
+    ws = hesp.alloc_workspace(plat, max_tiles, max_level, C if ws_cands is None else ws_cands, task_cap,
+                              max_bytes=8 << 30)
     ntasks = torch.empty(C, dtype=torch.int64, device="cuda")
     sched = None
     offs = None
@@ -50,7 +51,8 @@ def gpu_sim(spec, n, b, levels, max_level=None, schedule=False, max_tiles=None, 
         tot = int(offs[-1])
         sched = (torch.from_numpy(offs[:-1].copy()).cuda(), torch.empty(tot, dtype=torch.int16, device="cuda"),
                  torch.empty(tot, dtype=torch.int64, device="cuda"), torch.empty(tot, dtype=torch.int64, device="cuda"))
-    ms, st, nt = hesp.simulate_batch(plat, cands, lv, C, max_tiles, max_level, ws, ntasks=ntasks, schedule=sched)
+    ms, st, nt = hesp.simulate_batch(plat, cands, lv, C, max_tiles, max_level, ws, ntasks=ntasks, schedule=sched,
+                                     task_cap=task_cap)
     torch.cuda.synchronize()
     out = dict(makespan=ms.cpu().numpy(), status=st.cpu().numpy(), ntasks=nt.cpu().numpy())
     if schedule:
@@ -228,3 +230,32 @@ def test_bad_candidates_get_status_not_fault():
     assert st == [0, -1, -1, -1, -1, 0]
     with pytest.raises(hesp.HespError):
         hesp.simulate_batch(plat, cands, lv, 6, 3, 2, ws[:100])
+
+
+def test_task_cap_reports_capacity_and_keeps_others_exact():
+    lv = W.workload_levels("cfg1", 0, 96)
+    spec = W.PLATFORMS["cfg1a"]
+    plat = hesp.Platform(spec)
+    C = lv.shape[0]
+    ws = hesp.alloc_workspace(plat, 8, 2, C, task_cap=2300)
+    nt = torch.empty(C, dtype=torch.int64, device="cuda")
+    ms, st, _ = hesp.simulate_batch(plat, hesp.cands_tensor(8, 2048, np.arange(C) * 120),
+                                    torch.from_numpy(lv.reshape(-1).copy()).cuda(), C, 8, 2, ws, ntasks=nt,
+                                    task_cap=2300)
+    torch.cuda.synchronize()
+    st, ms = st.cpu().numpy(), ms.cpu().numpy()
+    dag = hesp.Dag(8, 2048, 2)
+    T = np.array([dag.count_tasks(r)[0] for r in lv])
+    assert ((T > 2300) == (st == -2)).all() and (st[T <= 2300] == 0).all()
+    assert (T > 2300).any() and (T <= 2300).any()
+    pl = O.make_platform(spec)
+    for c in np.nonzero(T <= 2300)[0][:12]:
+        assert O.simulate(pl, 8, 2048, lv[c], schedule=False)["makespan"] == ms[c]
+
+
+def test_cfg4_full_size_candidates():
+    """n = 32 tiles, levels 0..3 (about 8e5 tasks per candidate) on the
+    32 CPU + 2 GPU platform, checked against the oracle."""
+    lv = W.workload_levels("cfg4", 0, 2)
+    g = gpu_sim(W.PLATFORMS["cfg4"], 32, 2048, lv, max_level=3, task_cap=1 << 20)
+    check_parity(W.PLATFORMS["cfg4"], 32, 2048, lv, g, schedule=False)
