@@ -271,6 +271,23 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# ncu figures of the simulation kernel (profiles/sim_kernel_cfg1_small.md), valid only
+# for the kernel source they were taken on: DRAM bytes per 4,096 candidates on the
+# CPU+GPU platform (scaled to a launch by candidates; traffic grows in proportion)
+# and the share of issue slots busy.
+SIM_NCU = {"source_sha1_12": "3a7171750211", "dram_bytes_per_4096": 1.356322e9 + 1.196373e9,
+           "issue_active_pct": 59.77, "warps_per_sm": 23.5, "alu_pipe_pct": 47.3}
+
+
+def sim_source_matches():
+    import hashlib
+    p = os.path.join(ROOT, "paper_1602_05510_b300", "csrc", "sim_kernel.cu")
+    try:
+        return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12] == SIM_NCU["source_sha1_12"]
+    except OSError:
+        return False
+
+
 def roofline(plats, t_kern, K, task_events_rank, clk, peaks):
     """Dominant kernel: the simulation kernel on the CPU+GPU platform.  It is
     bound by integer/control issue, not by HBM or tensor cores; `achieved`
@@ -285,10 +302,19 @@ def roofline(plats, t_kern, K, task_events_rank, clk, peaks):
     peak = 148 * 128 * sm_max * 1e6 / 2 / 1e12  # T int64-op/s
     ev_a = task_events_rank / 2  # both platforms run the same candidates
     achieved = alg * ev_a / t / 1e12 if t > 0 and alg else None
+    fresh = sim_source_matches()
+    C = N_CAND
     return {"bound": "alu", "kernel": "sim_kernel<M=2> (cpu12_gpu1)", "achieved": achieved, "peak": peak,
             "unit": "T int64-op/s", "frac": achieved / peak if achieved else None,
-            "peak_source": "derived: 148 SMs x 128 INT32 lanes x %.0f MHz / 2 (of MEASURED_PEAKS sm_max_mhz)" % sm_max,
-            "kernel_ms": 1e3 * t, "traffic": None,
+            "peak_source": "derived: 148 SMs x 128 INT32 lanes x %.0f MHz / 2 (sm_max_mhz of MEASURED_PEAKS)" % sm_max,
+            "kernel_ms": 1e3 * t,
+            "traffic": SIM_NCU["dram_bytes_per_4096"] * C / 4096 if fresh else None,
+            "traffic_note": "DRAM bytes per launch from one ncu capture of 4,096 candidates, scaled by candidates; "
+                            "all of it is per-candidate arena state (algorithmic I/O is 120 B in + 20 B out per "
+                            "candidate)",
+            "issue_slots": {"busy_pct": SIM_NCU["issue_active_pct"] if fresh else None,
+                            "warps_per_sm": SIM_NCU["warps_per_sm"], "alu_pipe_pct": SIM_NCU["alu_pipe_pct"],
+                            "source": "ncu smsp__issue_active.avg.pct_of_peak_sustained_active"},
             "alg_ops_per_task_event": alg}
 
 
