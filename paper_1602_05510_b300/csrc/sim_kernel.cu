@@ -726,36 +726,49 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
             const int64_t iter_cap = 4 * T + 64;
             int64_t scheduled = 0;
             bool ok = true;
+            // Released tasks wait either in the bitmap (several completions at
+            // one time, or a long successor list) or, when a single task
+            // completed and released at most 32 successors, in the lanes (dj).
+            int dj = INT_MAX;
+            bool direct = false;
             for (;;) {
                 // schedule every released task in ascending id
-                for (int w0 = wlo; w0 <= whi; w0 += 32) {
-                    const int w = w0 + lane;
-                    uint32_t bits = 0;
-                    if (w <= whi) {
-                        bits = bm[w];
-                        if (bits) bm[w] = 0;
+                if (direct) {
+                    for (;;) {
+                        const int j = __reduce_min_sync(FULL, dj);
+                        if (j == INT_MAX) break;
+                        if (dj == j) dj = INT_MAX;
+                        schedule_task<M, NS>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
+                                             avail, head, tail, hfin, mk, ok, sched_base);
+                        ++scheduled;
                     }
-                    unsigned nz = __ballot_sync(FULL, bits != 0);
-                    while (nz) {
-                        const int src = __ffs(nz) - 1;
-                        nz &= nz - 1;
-                        uint32_t wb = __shfl_sync(FULL, bits, src);
-                        const int jb = (w0 + src) * 32;
-                        while (wb) {
-                            const int bit = __ffs(wb) - 1;
-                            wb &= wb - 1;
-                            schedule_task<M, NS>(jb + bit, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt,
-                                                 pv, avail, head, tail, hfin, mk, ok, sched_base);
-                            ++scheduled;
+                    direct = false;
+                } else {
+                    for (int w0 = wlo; w0 <= whi; w0 += 32) {
+                        const int w = w0 + lane;
+                        uint32_t bits = 0;
+                        if (w <= whi) {
+                            bits = bm[w];
+                            if (bits) bm[w] = 0;
+                        }
+                        unsigned nz = __ballot_sync(FULL, bits != 0);
+                        while (nz) {
+                            const int src = __ffs(nz) - 1;
+                            nz &= nz - 1;
+                            uint32_t wb = __shfl_sync(FULL, bits, src);
+                            const int jb = (w0 + src) * 32;
+                            while (wb) {
+                                const int bit = __ffs(wb) - 1;
+                                wb &= wb - 1;
+                                schedule_task<M, NS>(jb + bit, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype,
+                                                     pm, pt, pv, avail, head, tail, hfin, mk, ok, sched_base);
+                                ++scheduled;
+                            }
                         }
                     }
+                    wlo = INT_MAX;
+                    whi = -1;
                 }
-                if (!__all_sync(FULL, ok)) {
-                    status = HESP_ERR_STATE;
-                    break;
-                }
-                wlo = INT_MAX;
-                whi = -1;
                 // next completion time
                 uint64_t nk = ~0ull;
 #pragma unroll
@@ -767,9 +780,16 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                     status = HESP_ERR_TIMEOUT;
                     break;
                 }
+                unsigned cms[NS];
+                int ncomp = 0;
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
-                    unsigned cm = __ballot_sync(FULL, hfin[s] == t);
+                    cms[s] = __ballot_sync(FULL, hfin[s] == t);
+                    ncomp += __popc(cms[s]);
+                }
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    unsigned cm = cms[s];
                     while (cm) {
                         const int src = __ffs(cm) - 1;
                         cm &= cm - 1;
@@ -781,19 +801,31 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                             lnfin = link[i].nfin;
                         }
                         const int e0 = __shfl_sync(FULL, l0.y, src), e1 = __shfl_sync(FULL, l0.z, src);
-                        int lo = INT_MAX, hi = -1;
-                        for (int e = e0 + lane; e < e1; e += 32) {
-                            const int sj = succ[e];
-                            const int pvv = (int)pending[sj] - 1;
-                            pending[sj] = (uint16_t)pvv;
-                            if (pvv == 0) {
-                                atomicOr(&bm[sj >> 5], 1u << (sj & 31));
-                                lo = min(lo, sj >> 5);
-                                hi = max(hi, sj >> 5);
+                        if (ncomp == 1 && e1 - e0 <= 32) {
+                            // the only completion: its released successors wait in the lanes
+                            const int e = e0 + lane;
+                            if (e < e1) {
+                                const int sj = succ[e];
+                                const int pvv = (int)pending[sj] - 1;
+                                pending[sj] = (uint16_t)pvv;
+                                if (pvv == 0) dj = sj;
                             }
+                            direct = true;
+                        } else {
+                            int lo = INT_MAX, hi = -1;
+                            for (int e = e0 + lane; e < e1; e += 32) {
+                                const int sj = succ[e];
+                                const int pvv = (int)pending[sj] - 1;
+                                pending[sj] = (uint16_t)pvv;
+                                if (pvv == 0) {
+                                    atomicOr(&bm[sj >> 5], 1u << (sj & 31));
+                                    lo = min(lo, sj >> 5);
+                                    hi = max(hi, sj >> 5);
+                                }
+                            }
+                            wlo = min(wlo, __reduce_min_sync(FULL, lo));
+                            whi = max(whi, __reduce_max_sync(FULL, hi));
                         }
-                        wlo = min(wlo, __reduce_min_sync(FULL, lo));
-                        whi = max(whi, __reduce_max_sync(FULL, hi));
                         if (lane == src) {
                             head[s] = l0.x;
                             hfin[s] = l0.x >= 0 ? lnfin : kInf;
@@ -803,6 +835,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                     }
                 }
             }
+            if (!__all_sync(FULL, ok)) status = HESP_ERR_STATE;
             if (status == HESP_OK && scheduled != T) status = HESP_ERR_STATE;
         }
 
