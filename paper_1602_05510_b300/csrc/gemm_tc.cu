@@ -3,13 +3,15 @@
 // with fused epilogues for the surrogate MLP's layers.
 //
 // One CTA computes a 128 x 128 tile of C.  Warp 0 (one elected lane) streams
-// 128 x 64 tiles of A and B into a 4-stage shared-memory ring with TMA
+// 128 x 64 tiles of A and B into a 3-stage shared-memory ring with TMA
 // (cp.async.bulk.tensor, 128-byte swizzle); warp 1 (one lane) issues
 // tcgen05.mma (M = 128, N = 128, K = 16 per instruction) into a TMEM
 // accumulator and releases each stage with tcgen05.commit on its "empty"
 // mbarrier; warp 2 owns the TMEM allocation; all four warps then drain the
 // accumulator with tcgen05.ld (warp w reads TMEM lanes 32w .. 32w+31 = rows)
-// and apply the epilogue.  Every mbarrier wait is bounded: on expiry the CTA
+// and apply the epilogue.  Two CTAs fit one SM (~100 KB of shared memory and
+// 128 TMEM columns each), so one CTA's epilogue overlaps the other's main
+// loop.  Every mbarrier wait is bounded: on expiry the CTA
 // raises the caller's error flag, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -26,7 +28,7 @@ namespace hesp {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
 constexpr int TILE_BYTES = BM * BK * 2;  // 16 KiB per operand per stage
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
@@ -94,7 +96,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
