@@ -473,6 +473,62 @@ def run_surrogate_pipeline(args):
     print(json.dumps(line))
 
 
+def run_uneven(args):
+    """Ragged batch: 16,384 candidates per launch with n in [4, 32] tiles,
+    b in {512, 1024, 2048}, levels {0: .5, 1: .3, 2: .2} on 16 CPU + 2 GPU-type
+    processors; the launch shape is autotuned on a sample, then
+    generation + simulation is captured once as a CUDA graph and replayed."""
+    import torch
+
+    from paper_1602_05510_b300 import build, hesp
+
+    build.build()
+    C = 16384
+    spec = W.PLATFORMS["cfg2"]
+    plat = hesp.Platform(spec)
+    cap = 100000  # the largest DAG of this distribution has 88,272 tasks
+    ws = hesp.alloc_workspace(plat, 32, 2, C, task_cap=cap)
+    s = torch.cuda.Stream()
+    cands = torch.empty(C * 16, dtype=torch.uint8, device="cuda")
+    lcap = C * W.base_count(32)
+    levels = torch.empty(lcap, dtype=torch.int8, device="cuda")
+    used = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ms = torch.empty(C, dtype=torch.int64, device="cuda")
+    st = torch.empty(C, dtype=torch.int32, device="cuda")
+    nt = torch.empty(C, dtype=torch.int64, device="cuda")
+    hesp.generate_uneven(2, 0, C, cands, levels, used, stream=s)
+    s.synchronize()
+    (tc, tb), times = hesp.autotune(plat, cands, levels, C, 32, 2, ws, task_cap=cap, stream=s)
+
+    def step():
+        hesp.generate_uneven(2, 0, C, cands, levels, used, stream=s)
+        hesp.simulate_batch(plat, cands, levels, C, 32, 2, ws, makespan=ms, status=st, ntasks=nt, task_cap=cap,
+                            stream=s)
+
+    step()
+    s.synchronize()
+    g = hesp.Graph.capture(s, step)
+    for _ in range(args.warmup):
+        g.launch(s)
+    s.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b_ in ev:
+        a.record(s)
+        g.launch(s)
+        b_.record(s)
+    s.synchronize()
+    t = sum(a.elapsed_time(b_) for a, b_ in ev) / 1e3
+    ok = int((st == 0).sum().item())
+    tasks = int(nt[st == 0].sum().item())
+    line = {"metric": "sim task-events/s (bit-exact)", "value": tasks * args.steps / t, "unit": "task-events/s",
+            "n_gpus": 1, "steps": args.steps, "higher_is_better": True,
+            "workload": "ragged batch of 16,384 candidates (n 4..32 tiles, b 512..2048, levels .5/.3/.2), "
+                        "16 CPU + 2 GPU-type processors, CUDA-graph replay",
+            "ms_per_launch": 1e3 * t / args.steps, "candidates_ok": ok, "task_events_per_launch": tasks,
+            "autotuned": {"ctas_per_sm": tc, "bitmap": "global" if tb == 1 else "shared", "ms_by_shape": times}}
+    print(json.dumps(line))
+
+
 def run_search(args):
     """32 x 32 tiles (5984 base tasks, levels 0..3) on 32 CPU + 2 GPU-type
     processors: plain batched random search against surrogate-guided search,
@@ -528,7 +584,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=256)
     ap.add_argument("--candidates", type=int, default=N_CAND,
                     help="candidates per step (default: the workload's 65,536; smaller only for profiling)")
-    ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search"],
+    ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search", "uneven"],
                     help="random: the default benchmark line; surrogate: label/train/rank/re-score "
                          "pipeline; search: surrogate-guided vs random search")
     ap.add_argument("--labels", type=int, default=1 << 20)
@@ -547,6 +603,8 @@ def main():
         return run_surrogate_pipeline(args)
     if args.workload == "search":
         return run_search(args)
+    if args.workload == "uneven":
+        return run_uneven(args)
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -209,6 +209,35 @@ int hesp_simulate_batch_noalloc(const hesp_platform *p, const hesp_cand *cands_d
                                 int32_t *status_dev, int64_t *ntasks_dev, const int64_t *sched_offsets_dev,
                                 int16_t *proc_dev, int64_t *start_dev, int64_t *finish_dev, void *stream);
 
+/* ------------------------------------------------- runtime: graphs, tuning
+ * Capture any sequence of asynchronous hesp_* calls issued on `stream` (not
+ * the legacy default stream) between hesp_graph_begin and hesp_graph_end into
+ * a CUDA graph, and replay it with hesp_graph_launch (same buffers, current
+ * contents).  Calls that synchronise (hesp_surrogate_fit_stats,
+ * hesp_rank_metrics, hesp_sim_autotune, host copies) cannot be captured.
+ * The first simulation call on a platform and device should come before a
+ * capture (it sets the kernel's shared-memory attribute). */
+typedef struct hesp_graph hesp_graph;
+int hesp_graph_begin(void *stream);
+int hesp_graph_end(void *stream, hesp_graph **out);
+int hesp_graph_launch(const hesp_graph *g, void *stream);
+void hesp_graph_destroy(hesp_graph *g);
+
+/* Launch shape of the simulator for a platform: CTAs of 8 candidate warps per
+ * SM (0 = as many as fit) and the place of the released-task bitmap (0 auto,
+ * 1 global memory, 2 shared memory when it fits).  hesp_sim_autotune times a
+ * sample batch (cands_dev, levels_dev, n_sample) under every shape, keeps the
+ * fastest in `p` and appends it to cache_path (nullable); a cached entry for
+ * the same GPU, bounds and platform shape is reused without timing.  ms_out
+ * (nullable, [8]) receives the time of each shape (bitmap-major, -1 if not
+ * run).  Synchronous; the workspace must hold the sample. */
+int hesp_platform_set_tuning(hesp_platform *p, int32_t ctas_per_sm, int32_t bitmap_place);
+int hesp_platform_get_tuning(const hesp_platform *p, int32_t *ctas_per_sm, int32_t *bitmap_place);
+int hesp_sim_autotune(hesp_platform *p, const hesp_cand *cands_dev, const int8_t *levels_dev, int64_t n_sample,
+                      int32_t max_tiles, int32_t max_level, int64_t task_cap, int64_t *makespan_dev,
+                      int32_t *status_dev, void *workspace_dev, size_t workspace_bytes, const char *cache_path,
+                      int32_t *best_ctas, int32_t *best_bitmap, float *ms_out, void *stream);
+
 /* --------------------------------------------------- candidate generation
  * Partition vectors drawn on the device from SplitMix64 (Steele, Lea, Flood,
  * OOPSLA 2014) used as a counter-based generator: output k of candidate c is

@@ -83,6 +83,7 @@ int sim_slots_for(const hesp_platform *p, const Arena &ar, int64_t *resident_war
     int rc = sim_kernel_occupancy(p->n_mem, p->n_procs, ar.Tcap, &blocks, &threads);
     if (rc) return rc;
     if (blocks < 1) blocks = 1;
+    if (p->tune_ctas_per_sm > 0 && p->tune_ctas_per_sm < blocks) blocks = p->tune_ctas_per_sm;
     *resident_warps = (int64_t)sms * blocks * (threads / 32);
     return HESP_OK;
 }

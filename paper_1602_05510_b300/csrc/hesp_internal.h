@@ -17,6 +17,9 @@ struct hesp_platform {
     // exec[op][type][log2 block] in ns; -1 where the model does not fit in
     // 56 bits (the simulator then flags the candidate with HESP_ERR_ARG).
     int64_t exec[4][HESP_MAX_TYPES][HESP_LB];
+    // launch shape chosen by hesp_sim_autotune or set by the caller (0 = default)
+    int32_t tune_ctas_per_sm;
+    int32_t tune_bitmap;  // 0 auto, 1 arena (global memory), 2 shared memory when it fits
 };
 
 struct hesp_dag {

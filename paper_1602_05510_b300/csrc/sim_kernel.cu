@@ -907,7 +907,7 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
     a.ar = ar;
     a.n_slots = n_slots;
     a.ws = ws + kWsHeaderBytes;
-    a.bm_smem_words = sim_bitmap_smem_words(ar.Tcap);
+    a.bm_smem_words = p->tune_bitmap == 1 ? 0 : sim_bitmap_smem_words(ar.Tcap);
     unsigned long long *ctr = &((WsHeader *)ws)->work_counter;
     if (cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), stream) != cudaSuccess) return HESP_ERR_CUDA;
     const int threads = 256;

@@ -34,7 +34,9 @@ EXPORTS = (
     "hesp_surrogate_set", "hesp_surrogate_grad", "hesp_surrogate_adam", "hesp_surrogate_train",
     "hesp_surrogate_infer", "hesp_surrogate_error", "hesp_select_workspace_size", "hesp_select_topk",
     "hesp_make_cands", "hesp_gather_f32", "hesp_rank_metrics_workspace_size", "hesp_rank_metrics",
-    "hesp_generate_mutants", "hesp_gather_rows", "hesp_best_makespan",
+    "hesp_generate_mutants", "hesp_gather_rows", "hesp_best_makespan", "hesp_graph_begin", "hesp_graph_end",
+    "hesp_graph_launch", "hesp_graph_destroy", "hesp_platform_set_tuning", "hesp_platform_get_tuning",
+    "hesp_sim_autotune",
 )
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -114,6 +116,15 @@ def lib():
         L.hesp_gather_f32.argtypes = [vp, vp, i64, vp, vp]
         L.hesp_rank_metrics_workspace_size.argtypes = [i64, ctypes.POINTER(sz)]
         L.hesp_rank_metrics.argtypes = [vp, vp, i64, f64, f64, vp, sz, ctypes.POINTER(f64), vp]
+        L.hesp_graph_begin.argtypes = [vp]
+        L.hesp_graph_end.argtypes = [vp, ctypes.POINTER(vp)]
+        L.hesp_graph_launch.argtypes = [vp, vp]
+        L.hesp_graph_destroy.argtypes = [vp]
+        L.hesp_graph_destroy.restype = None
+        L.hesp_platform_set_tuning.argtypes = [vp, i32, i32]
+        L.hesp_platform_get_tuning.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.hesp_sim_autotune.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, sz, ctypes.c_char_p,
+                                        ctypes.POINTER(i32), ctypes.POINTER(i32), vp, vp]
         L.hesp_best_makespan.argtypes = [vp, vp, vp, i64, vp, vp]
         L.hesp_gather_rows.argtypes = [vp, vp, i64, i64, vp, vp]
         L.hesp_generate_mutants.argtypes = [vp, i32, i32, i32, ctypes.c_double, u64, i64, i64, vp, vp]
@@ -461,3 +472,58 @@ def best_makespan(makespan, status, ntasks=None, out=None, stream=None):
     check(lib().hesp_best_makespan(_ptr(makespan), _ptr(status), _ptr(ntasks), makespan.numel(), _ptr(out),
                                    _stream(stream)), "hesp_best_makespan")
     return out
+
+
+class Graph:
+    """A CUDA graph of hesp_* calls captured on a (non-default) stream:
+
+        g = Graph.capture(stream, lambda: ...calls with stream=stream...)
+        g.launch(stream)
+    """
+
+    def __init__(self, h):
+        self.h = h
+
+    @classmethod
+    def capture(cls, stream, fn):
+        check(lib().hesp_graph_begin(ctypes.c_void_p(stream.cuda_stream)), "hesp_graph_begin")
+        try:
+            fn()
+        finally:
+            h = ctypes.c_void_p()
+            rc = lib().hesp_graph_end(ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        check(rc, "hesp_graph_end")
+        return cls(h)
+
+    def launch(self, stream):
+        check(lib().hesp_graph_launch(self.h, ctypes.c_void_p(stream.cuda_stream)), "hesp_graph_launch")
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hesp_graph_destroy(self.h)
+            self.h = None
+
+
+def set_tuning(platform, ctas_per_sm=0, bitmap_place=0):
+    check(lib().hesp_platform_set_tuning(platform.h, ctas_per_sm, bitmap_place), "hesp_platform_set_tuning")
+
+
+def get_tuning(platform):
+    c, b = ctypes.c_int32(), ctypes.c_int32()
+    check(lib().hesp_platform_get_tuning(platform.h, ctypes.byref(c), ctypes.byref(b)), "hesp_platform_get_tuning")
+    return c.value, b.value
+
+
+def autotune(platform, cands, levels, n_sample, max_tiles, max_level, workspace, task_cap=0, cache_path=None,
+             stream=None):
+    """Returns ((ctas_per_sm, bitmap_place), [ms per shape])."""
+    import torch
+    ms = torch.empty(n_sample, dtype=torch.int64, device=levels.device)
+    st = torch.empty(n_sample, dtype=torch.int32, device=levels.device)
+    c, b = ctypes.c_int32(), ctypes.c_int32()
+    times = np.zeros(8, np.float32)
+    check(lib().hesp_sim_autotune(platform.h, _ptr(cands), _ptr(levels), n_sample, max_tiles, max_level, task_cap,
+                                  _ptr(ms), _ptr(st), _ptr(workspace), workspace.numel(),
+                                  cache_path.encode() if cache_path else None, ctypes.byref(c), ctypes.byref(b),
+                                  times.ctypes.data, _stream(stream)), "hesp_sim_autotune")
+    return (c.value, b.value), times.tolist()
