@@ -238,6 +238,16 @@ int hesp_sim_autotune(hesp_platform *p, const hesp_cand *cands_dev, const int8_t
                       int32_t *status_dev, void *workspace_dev, size_t workspace_bytes, const char *cache_path,
                       int32_t *best_ctas, int32_t *best_bitmap, float *ms_out, void *stream);
 
+/* Largest-first ordering of a ragged batch (so that long simulations start
+ * first and the batch ends together): sorted_dev[i] = cands_dev[perm_dev[i]]
+ * in decreasing task count (buckets of 16 tasks; candidates in one bucket in
+ * any order).  perm_dev nullable; workspace from
+ * hesp_sort_cands_workspace_size. */
+int hesp_sort_cands_workspace_size(int64_t n_cand, size_t *bytes_out);
+int hesp_sort_cands_by_size(const hesp_cand *cands_dev, const int8_t *levels_dev, int64_t n_cand,
+                            hesp_cand *sorted_dev, int32_t *perm_dev, void *workspace_dev, size_t workspace_bytes,
+                            void *stream);
+
 /* --------------------------------------------------- candidate generation
  * Partition vectors drawn on the device from SplitMix64 (Steele, Lea, Flood,
  * OOPSLA 2014) used as a counter-based generator: output k of candidate c is

@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/hesp.h.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -345,6 +346,22 @@ int hesp_generate_mutants(const int8_t *parents_dev, int32_t n_parents, int32_t 
     const uint32_t p_num = (uint32_t)(p_mut * 65536.0 + 0.5);
     return launch_mutate(parents_dev, n_parents, n_base, n_levels, p_num, seed, first, n, levels_dev,
                          (cudaStream_t)stream);
+}
+
+int hesp_sort_cands_workspace_size(int64_t n_cand, size_t *bytes_out) {
+    if (n_cand < 0 || !bytes_out) return HESP_ERR_ARG;
+    *bytes_out = (size_t)(65536 + n_cand) * 4;
+    return HESP_OK;
+}
+
+int hesp_sort_cands_by_size(const hesp_cand *cands_dev, const int8_t *levels_dev, int64_t n_cand,
+                            hesp_cand *sorted_dev, int32_t *perm_dev, void *workspace_dev, size_t workspace_bytes,
+                            void *stream) {
+    if (!cands_dev || !levels_dev || !sorted_dev || !workspace_dev || n_cand < 0 || n_cand > INT32_MAX)
+        return HESP_ERR_ARG;
+    if (workspace_bytes < (size_t)(65536 + n_cand) * 4 || ((uintptr_t)workspace_dev & 3)) return HESP_ERR_ARG;
+    return launch_sort_by_size(cands_dev, levels_dev, n_cand, sorted_dev, perm_dev, workspace_dev,
+                               (cudaStream_t)stream);
 }
 
 int hesp_generate_uneven(uint64_t seed, int64_t first, int64_t n_cand, hesp_cand *cands, int8_t *levels,

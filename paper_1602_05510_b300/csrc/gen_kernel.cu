@@ -119,6 +119,88 @@ __global__ void mutate_kernel(const int8_t *parents, int n_parents, int nb, int 
     }
 }
 
+// Task count of each candidate (one warp per candidate) -> descending-size
+// bucket key (65535 - min(65535, T / 16)).
+__constant__ int32_t c_cnt_g[4][HESP_MAX_LEVEL + 1] = {
+    {1, 4, 20, 120, 816}, {1, 6, 40, 288, 2176}, {1, 6, 40, 288, 2176}, {1, 8, 64, 512, 4096}};
+
+__device__ int base_op(int n, int64_t t) {
+    for (int k = 0; k < n; ++k) {
+        const int64_t m = n - k - 1;
+        const int64_t S = 1 + 2 * m + (m * (m - 1)) / 2;
+        if (t < S) {
+            if (t == 0) return 0;
+            if (t <= m) return 1;
+            t -= m + 1;
+            for (int i = k + 1; i < n; ++i) {
+                const int blk = n - i;
+                if (t < blk) return t < blk - 1 ? 3 : 2;
+                t -= blk;
+            }
+            return 2;
+        }
+        t -= S;
+    }
+    return 0;
+}
+
+__global__ void size_key_kernel(const hesp_cand *cands, const int8_t *levels, int64_t n_cand, uint32_t *key,
+                                uint32_t *hist) {
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= n_cand) return;
+    const hesp_cand cd = cands[c];
+    const int n = cd.n_tiles;
+    int64_t T = 0;
+    if (n >= 1 && n <= HESP_MAX_TILES) {
+        const int64_t nb = (int64_t)n * (n + 1) * (n + 2) / 6;
+        for (int64_t t = lane; t < nb; t += 32) {
+            const int l = levels[cd.level_offset + t];
+            T += (l >= 0 && l <= HESP_MAX_LEVEL) ? c_cnt_g[base_op(n, t)][l] : 1;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) T += __shfl_xor_sync(0xFFFFFFFFu, T, o);
+    if (lane == 0) {
+        const uint32_t k = 65535u - (uint32_t)min((int64_t)65535, T >> 4);
+        key[c] = k;
+        atomicAdd(&hist[k], 1u);
+    }
+}
+
+__global__ void bucket_scan_kernel(uint32_t *hist) {
+    // exclusive scan of 65,536 counters by one block of 1,024 threads
+    __shared__ uint32_t part[1024];
+    const int t = threadIdx.x;
+    uint32_t s = 0;
+    for (int i = 0; i < 64; ++i) s += hist[t * 64 + i];
+    part[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        uint32_t run = 0;
+        for (int i = 0; i < 1024; ++i) {
+            const uint32_t v = part[i];
+            part[i] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    uint32_t run = part[t];
+    for (int i = 0; i < 64; ++i) {
+        const uint32_t v = hist[t * 64 + i];
+        hist[t * 64 + i] = run;
+        run += v;
+    }
+}
+
+__global__ void bucket_scatter_kernel(const hesp_cand *in, int64_t n_cand, const uint32_t *key, uint32_t *cursor,
+                                      hesp_cand *out, int32_t *perm) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cand) return;
+    const uint32_t pos = atomicAdd(&cursor[key[c]], 1u);
+    out[pos] = in[c];
+    if (perm) perm[pos] = (int32_t)c;
+}
+
 dim3 cand_grid(int64_t n_cand) {
     const int64_t gx = n_cand < 65535 ? n_cand : 65535;
     return dim3((unsigned)gx, (unsigned)((n_cand + gx - 1) / gx));
@@ -139,6 +221,18 @@ int launch_mutate(const int8_t *parents, int32_t n_parents, int32_t n_base, int3
                   uint64_t seed, int64_t first, int64_t n, int8_t *out, cudaStream_t stream) {
     if (n == 0) return HESP_OK;
     mutate_kernel<<<cand_grid(n), 128, 0, stream>>>(parents, n_parents, n_base, n_levels, p_num, seed, first, n, out);
+    return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
+}
+
+int launch_sort_by_size(const hesp_cand *in, const int8_t *levels, int64_t n, hesp_cand *out, int32_t *perm,
+                        void *ws, cudaStream_t st) {
+    if (n == 0) return HESP_OK;
+    uint32_t *hist = (uint32_t *)ws;
+    uint32_t *key = hist + 65536;
+    if (cudaMemsetAsync(hist, 0, 65536 * 4, st) != cudaSuccess) return HESP_ERR_CUDA;
+    size_key_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(in, levels, n, key, hist);
+    bucket_scan_kernel<<<1, 1024, 0, st>>>(hist);
+    bucket_scatter_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, n, key, hist, out, perm);
     return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
 }
 

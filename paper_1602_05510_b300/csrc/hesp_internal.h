@@ -80,6 +80,8 @@ int launch_generate(int32_t kind, uint64_t seed, int64_t first, int64_t n_cand, 
                     int32_t n_levels, hesp_cand *cands, int8_t *levels, cudaStream_t stream);
 int launch_mutate(const int8_t *parents, int32_t n_parents, int32_t n_base, int32_t n_levels, uint32_t p_num,
                   uint64_t seed, int64_t first, int64_t n, int8_t *out, cudaStream_t stream);
+int launch_sort_by_size(const hesp_cand *in, const int8_t *levels, int64_t n, hesp_cand *out, int32_t *perm,
+                        void *ws, cudaStream_t st);
 int launch_generate_uneven(uint64_t seed, int64_t first, int64_t n_cand, hesp_cand *cands, int8_t *levels,
                            int64_t levels_cap, int64_t *levels_used, cudaStream_t stream);
 

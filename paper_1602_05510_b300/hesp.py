@@ -36,7 +36,7 @@ EXPORTS = (
     "hesp_make_cands", "hesp_gather_f32", "hesp_rank_metrics_workspace_size", "hesp_rank_metrics",
     "hesp_generate_mutants", "hesp_gather_rows", "hesp_best_makespan", "hesp_graph_begin", "hesp_graph_end",
     "hesp_graph_launch", "hesp_graph_destroy", "hesp_platform_set_tuning", "hesp_platform_get_tuning",
-    "hesp_sim_autotune",
+    "hesp_sim_autotune", "hesp_sort_cands_workspace_size", "hesp_sort_cands_by_size",
 )
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
@@ -125,6 +125,8 @@ def lib():
         L.hesp_platform_get_tuning.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.hesp_sim_autotune.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, sz, ctypes.c_char_p,
                                         ctypes.POINTER(i32), ctypes.POINTER(i32), vp, vp]
+        L.hesp_sort_cands_workspace_size.argtypes = [i64, ctypes.POINTER(sz)]
+        L.hesp_sort_cands_by_size.argtypes = [vp, vp, i64, vp, vp, vp, sz, vp]
         L.hesp_best_makespan.argtypes = [vp, vp, vp, i64, vp, vp]
         L.hesp_gather_rows.argtypes = [vp, vp, i64, i64, vp, vp]
         L.hesp_generate_mutants.argtypes = [vp, i32, i32, i32, ctypes.c_double, u64, i64, i64, vp, vp]
@@ -527,3 +529,19 @@ def autotune(platform, cands, levels, n_sample, max_tiles, max_level, workspace,
                                   cache_path.encode() if cache_path else None, ctypes.byref(c), ctypes.byref(b),
                                   times.ctypes.data, _stream(stream)), "hesp_sim_autotune")
     return (c.value, b.value), times.tolist()
+
+
+def sort_cands_by_size(cands, levels, n_cand, sorted_cands=None, perm=None, ws=None, stream=None):
+    """Candidates reordered largest DAG first; returns (sorted_cands, perm)."""
+    import torch
+    sz = ctypes.c_size_t()
+    check(lib().hesp_sort_cands_workspace_size(n_cand, ctypes.byref(sz)), "hesp_sort_cands_workspace_size")
+    if ws is None:
+        ws = torch.empty(sz.value, dtype=torch.uint8, device=levels.device)
+    if sorted_cands is None:
+        sorted_cands = torch.empty(n_cand * 16, dtype=torch.uint8, device=levels.device)
+    if perm is None:
+        perm = torch.empty(n_cand, dtype=torch.int32, device=levels.device)
+    check(lib().hesp_sort_cands_by_size(_ptr(cands), _ptr(levels), n_cand, _ptr(sorted_cands), _ptr(perm), _ptr(ws),
+                                        ws.numel(), _stream(stream)), "hesp_sort_cands_by_size")
+    return sorted_cands, perm

@@ -72,3 +72,28 @@ def test_autotune_picks_a_shape_and_results_do_not_change():
         plat2 = hesp.Platform(W.PLATFORMS["cfg1a"])
         (c2, b2), times2 = hesp.autotune(plat2, cd, lv, C, 8, 2, ws, cache_path=path)
         assert (c2, b2) == (c, b) and all(t < 0 for t in times2)
+
+
+def test_sort_by_size_orders_and_preserves_results():
+    from paper_1602_05510_b300 import workloads as W2
+    C = 512
+    n, b, off, lvh = W2.uneven_candidates(2, 100, C)
+    cands = torch.empty(C * 16, dtype=torch.uint8, device="cuda")
+    lv = torch.empty(int(off[-1]), dtype=torch.int8, device="cuda")
+    used = torch.zeros(1, dtype=torch.int64, device="cuda")
+    hesp.generate_uneven(2, 100, C, cands, lv, used)
+    sc, perm = hesp.sort_cands_by_size(cands, lv, C)
+    plat = hesp.Platform(W2.PLATFORMS["cfg2"])
+    ws = hesp.alloc_workspace(plat, 32, 2, C, task_cap=100000)
+    nt_s = torch.empty(C, dtype=torch.int64, device="cuda")
+    nt_u = torch.empty(C, dtype=torch.int64, device="cuda")
+    ms_s, st_s, _ = hesp.simulate_batch(plat, sc, lv, C, 32, 2, ws, ntasks=nt_s, task_cap=100000)
+    ms_s = ms_s.clone()
+    ms_u, st_u, _ = hesp.simulate_batch(plat, cands, lv, C, 32, 2, ws, ntasks=nt_u, task_cap=100000)
+    torch.cuda.synchronize()
+    p = perm.cpu().numpy().astype(np.int64)
+    assert sorted(p.tolist()) == list(range(C))
+    T = nt_s.cpu().numpy()
+    assert (np.diff(T // 16) <= 0).all()          # non-increasing in buckets of 16 tasks
+    assert (st_s == 0).all() and (st_u == 0).all()
+    assert np.array_equal(ms_s.cpu().numpy(), ms_u.cpu().numpy()[p])
