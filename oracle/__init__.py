@@ -69,6 +69,8 @@ class Platform(ctypes.Structure):
         ("ovr_type", ctypes.c_int32 * MAX_OVR),
         ("ovr_bs", ctypes.c_int64 * MAX_OVR),
         ("ovr_ns", ctypes.c_int64 * MAX_OVR),
+        ("order", ctypes.c_int32),
+        ("select", ctypes.c_int32),
     ]
 
 
@@ -113,7 +115,11 @@ def lib():
     return _lib
 
 
-def make_platform(desc) -> Platform:
+ORDER_FCFS, ORDER_PL = 0, 1
+SELECT_EFT, SELECT_EIT = 0, 1
+
+
+def make_platform(desc, order: int = ORDER_FCFS, select: int = SELECT_EFT) -> Platform:
     """Oracle platform from a plain description (a dict or an object with the
     fields of ``paper_1602_05510_b300.workloads.PlatformSpec``)."""
     g = (lambda k: desc[k]) if isinstance(desc, dict) else (lambda k: getattr(desc, k))
@@ -140,6 +146,7 @@ def make_platform(desc) -> Platform:
     pl.n_ovr = len(ovr)
     for i, (op, ty, bs, ns) in enumerate(ovr):
         pl.ovr_op[i], pl.ovr_type[i], pl.ovr_bs[i], pl.ovr_ns[i] = op, ty, bs, ns
+    pl.order, pl.select = order, select
     return pl
 
 

@@ -69,6 +69,10 @@ typedef struct {
     int32_t n_ovr;
     int32_t ovr_op[OR_MAX_OVR], ovr_type[OR_MAX_OVR];
     int64_t ovr_bs[OR_MAX_OVR], ovr_ns[OR_MAX_OVR];
+    /* scheduling heuristics (Sec. 2.1): task order 0 = FCFS, 1 = PL;
+     * processor selection 0 = EFT-P, 1 = EIT-P */
+    int32_t order;
+    int32_t select;
 } or_platform;
 
 /* A square data region in element coordinates of the full matrix. */
@@ -594,6 +598,131 @@ typedef struct {
     int64_t atom_visits;  /* sum over tasks of atoms in their regions */
 } or_stats;
 
+/* State of one simulation, shared by the task-order loops below. */
+typedef struct {
+    const or_platform *pl;
+    const or_dag *d;
+    const atom_grid *g;
+    int32_t M, P;
+    uint8_t *valid;
+    int64_t *vfrom;
+    int64_t *avail;
+    const int8_t *mem_used;
+    int64_t *ax;
+    int32_t *axw;
+    int32_t *src;
+    or_stats *st;
+    int16_t *proc_out;
+    int64_t *start_out, *finish_out;
+    int32_t *order_out;
+    int32_t n_sched;
+    int64_t finish_j; /* finish time of the task just scheduled */
+} sched_state;
+
+/* Schedule task j at time t (see the rules above or_simulate). */
+static int schedule_task(sched_state *S, int32_t j, int64_t t) {
+    const or_platform *pl = S->pl;
+    const or_task *tk = &S->d->t[j];
+    const atom_grid *g = S->g;
+    const int32_t M = S->M, P = S->P;
+    uint8_t *valid = S->valid;
+    int64_t *vfrom = S->vfrom;
+    int64_t *ax = S->ax;
+    int32_t *axw = S->axw, *src = S->src;
+    /* atoms of j's regions, flagged when written */
+    int64_t na = 0;
+    for (int r = 0; r < tk->nreg; r++) {
+        int64_t k = region_atoms(g, tk->reg[r], ax + na);
+        for (int64_t e = 0; e < k; e++) axw[na + e] = (r == tk->nreg - 1);
+        na += k;
+    }
+    S->st->atom_visits += na;
+    int64_t atom_elems = g->a * g->a;
+    int64_t drt[OR_MAX_MEMS];
+    int64_t arrive[OR_MAX_MEMS][OR_MAX_MEMS];
+    for (int m = 0; m < M; m++) {
+        drt[m] = 0;
+        if (!S->mem_used[m]) continue;
+        int64_t elems_from[OR_MAX_MEMS];
+        for (int sm = 0; sm < M; sm++) elems_from[sm] = 0;
+        for (int64_t e = 0; e < na; e++) {
+            int64_t x = ax[e];
+            src[e * M + m] = -1;
+            if (valid[x * M + m]) {
+                if (vfrom[x * M + m] > drt[m]) drt[m] = vfrom[x * M + m];
+            } else {
+                int found = -1;
+                for (int sm = 0; sm < M; sm++)
+                    if (valid[x * M + sm] && vfrom[x * M + sm] <= t) { found = sm; break; }
+                if (found < 0) return OR_ERR_STATE;
+                src[e * M + m] = found;
+                elems_from[found] += atom_elems;
+            }
+        }
+        for (int sm = 0; sm < M; sm++) {
+            arrive[m][sm] = 0;
+            if (elems_from[sm] > 0) {
+                arrive[m][sm] = t + or_xfer_ns(pl, elems_from[sm]);
+                if (arrive[m][sm] > drt[m]) drt[m] = arrive[m][sm];
+            }
+        }
+    }
+    /* processor selection, ties to the lowest id:
+     *   EFT-P: the earliest finish time max(t, avail, DRT) + exec;
+     *   EIT-P: the processor that becomes idle first, max(t, avail). */
+    int32_t best = -1;
+    int64_t best_key = 0, best_eft = 0, best_exec = 0;
+    for (int p = 0; p < P; p++) {
+        int64_t ready = t;
+        if (S->avail[p] > ready) ready = S->avail[p];
+        int64_t idle = ready;
+        if (drt[pl->proc_mem[p]] > ready) ready = drt[pl->proc_mem[p]];
+        int64_t ex = or_exec_ns(pl, tk->op, pl->proc_type[p], tk->bs);
+        int64_t eft = ready + ex;
+        int64_t key = pl->select == 1 ? idle : eft;
+        if (best < 0 || key < best_key) { best = p; best_key = key; best_eft = eft; best_exec = ex; }
+    }
+    int ms = pl->proc_mem[best];
+    /* commit: transfers, then write-back invalidation of written atoms */
+    int64_t elems_from2[OR_MAX_MEMS];
+    for (int sm = 0; sm < M; sm++) elems_from2[sm] = 0;
+    for (int64_t e = 0; e < na; e++) {
+        int64_t x = ax[e];
+        int sm = src[e * M + ms];
+        if (sm >= 0) {
+            valid[x * M + ms] = 1;
+            vfrom[x * M + ms] = arrive[ms][sm];
+            elems_from2[sm] += atom_elems;
+        }
+    }
+    for (int sm = 0; sm < M; sm++)
+        if (elems_from2[sm] > 0) { S->st->n_transfers++; S->st->xfer_elems += elems_from2[sm]; }
+    for (int64_t e = 0; e < na; e++) {
+        if (!axw[e]) continue;
+        int64_t x = ax[e];
+        for (int m = 0; m < M; m++) valid[x * M + m] = 0;
+        valid[x * M + ms] = 1;
+        vfrom[x * M + ms] = best_eft;
+    }
+    S->avail[best] = best_eft;
+    S->finish_j = best_eft;
+    if (S->proc_out) S->proc_out[j] = (int16_t)best;
+    if (S->start_out) S->start_out[j] = best_eft - best_exec;
+    if (S->finish_out) S->finish_out[j] = best_eft;
+    if (S->order_out) S->order_out[S->n_sched] = j;
+    S->n_sched++;
+    if (best_eft > S->st->makespan) S->st->makespan = best_eft;
+    return OR_OK;
+}
+
+/* qsort order of the priority list: decreasing critical time, then id. */
+static const int64_t *g_crit;
+static int by_crit_desc(const void *a, const void *b) {
+    int32_t i = *(const int32_t *)a, j = *(const int32_t *)b;
+    if (g_crit[i] != g_crit[j]) return g_crit[i] > g_crit[j] ? -1 : 1;
+    return i < j ? -1 : (i > j);
+}
+
 /* Simulate one candidate.
  *   code/code_len: split tree (preorder), see or_levels_to_code
  *   atom_level:    atom side = b / 2^atom_level (>= deepest split)
@@ -601,7 +730,8 @@ typedef struct {
  * Optional outputs (NULL to skip), per task in creation order:
  *   proc_out, start_out, finish_out; order_out = task ids in the order they
  *   were scheduled.
- * The scheduling rules (Sec. 2.1, FCFS + EFT-P, WB caching, prefetch):
+ * The scheduling rules (Sec. 2.1, WB caching, prefetch), with task order
+ * FCFS (pl->order 0) -- PL (order 1) is described at its loop below:
  *   1. t = 0; the released set holds the tasks without predecessors.
  *   2. Every released task is scheduled at time t in ascending task id.
  *   3. If nothing is in flight, stop.  Otherwise t = the earliest finish
@@ -615,7 +745,8 @@ typedef struct {
  *     source travel as one message issued at t and arrive at
  *     t + xfer(elements); DRT is the latest of these times;
  *   - EFT(p) = max(t, avail[p], DRT(j, mem(p))) + exec(op, type(p), bs);
- *     p* = argmin EFT, ties to the lowest processor id;
+ *     EFT-P (pl->select 0): p* = argmin EFT, ties to the lowest processor
+ *     id; EIT-P (select 1): p* = argmin max(t, avail[p]), ties likewise;
  *   - commit: start = EFT - exec, avail[p*] = EFT; the fetched atoms become
  *     valid in mem(p*) from their arrival; then the written atoms become
  *     valid only in mem(p*), from the finish time (write-back invalidation).
@@ -695,128 +826,109 @@ int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *c
     memset(mem_used, 0, sizeof mem_used);
     for (int p = 0; p < P; p++) mem_used[pl->proc_mem[p]] = 1;
 
-    int32_t nrel = 0;
-    for (int32_t j = 0; j < T; j++)
-        if (pending[j] == 0) released[nrel++] = j;
-    int64_t t = 0;
-    int32_t n_sched = 0;
+    sched_state S;
+    S.pl = pl;
+    S.d = &d;
+    S.g = &g;
+    S.M = M;
+    S.P = P;
+    S.valid = valid;
+    S.vfrom = vfrom;
+    S.avail = avail;
+    S.mem_used = mem_used;
+    S.ax = ax;
+    S.axw = axw;
+    S.src = src;
+    S.st = &s;
+    S.proc_out = proc_out;
+    S.start_out = start_out;
+    S.finish_out = finish_out;
+    S.order_out = order_out;
+    S.n_sched = 0;
     int32_t n_done = 0;
-    for (;;) {
-        /* schedule the released tasks in ascending id */
-        for (int32_t a1 = 1; a1 < nrel; a1++) {
-            int32_t v = released[a1];
-            int32_t a2 = a1 - 1;
-            while (a2 >= 0 && released[a2] > v) { released[a2 + 1] = released[a2]; a2--; }
-            released[a2 + 1] = v;
+    if (pl->order == 1) {
+        /* PL: a static priority list (HEFT-like).  Critical time of a task =
+         * its processing time summed over all processors (P times the mean:
+         * the same order) plus the largest critical time of its successors,
+         * computed backwards (creation order is topological).  Tasks are
+         * scheduled in decreasing critical time, ties to the lower id, each at
+         * its release time: the latest finish among its predecessors. */
+        int64_t *crit = (int64_t *)malloc(sizeof(int64_t) * (size_t)(T + 1));
+        int64_t *rel = (int64_t *)calloc((size_t)T + 1, sizeof(int64_t));
+        int32_t *list = (int32_t *)malloc(sizeof(int32_t) * (size_t)(T + 1));
+        if (!crit || !rel || !list) {
+            free(crit); free(rel); free(list);
+            rc = OR_ERR_CAPACITY;
+            goto out;
         }
-        for (int32_t q = 0; q < nrel; q++) {
-            int32_t j = released[q];
-            const or_task *tk = &d.t[j];
-            /* atoms of j's regions, flagged when written */
-            int64_t na = 0;
-            for (int r = 0; r < tk->nreg; r++) {
-                int64_t k = region_atoms(&g, tk->reg[r], ax + na);
-                for (int64_t e = 0; e < k; e++) axw[na + e] = (r == tk->nreg - 1);
-                na += k;
-            }
-            s.atom_visits += na;
-            int64_t atom_elems = g.a * g.a;
-            int64_t drt[OR_MAX_MEMS];
-            int64_t arrive[OR_MAX_MEMS][OR_MAX_MEMS];
-            for (int m = 0; m < M; m++) {
-                drt[m] = 0;
-                if (!mem_used[m]) continue;
-                int64_t elems_from[OR_MAX_MEMS];
-                for (int sm = 0; sm < M; sm++) elems_from[sm] = 0;
-                for (int64_t e = 0; e < na; e++) {
-                    int64_t x = ax[e];
-                    src[e * M + m] = -1;
-                    if (valid[x * M + m]) {
-                        if (vfrom[x * M + m] > drt[m]) drt[m] = vfrom[x * M + m];
-                    } else {
-                        int found = -1;
-                        for (int sm = 0; sm < M; sm++)
-                            if (valid[x * M + sm] && vfrom[x * M + sm] <= t) { found = sm; break; }
-                        if (found < 0) { rc = OR_ERR_STATE; goto out; }
-                        src[e * M + m] = found;
-                        elems_from[found] += atom_elems;
-                    }
-                }
-                for (int sm = 0; sm < M; sm++) {
-                    arrive[m][sm] = 0;
-                    if (elems_from[sm] > 0) {
-                        arrive[m][sm] = t + or_xfer_ns(pl, elems_from[sm]);
-                        if (arrive[m][sm] > drt[m]) drt[m] = arrive[m][sm];
-                    }
-                }
-            }
-            /* EFT over processors, ties to the lowest id */
-            int32_t best = -1;
-            int64_t best_eft = 0, best_exec = 0;
-            for (int p = 0; p < P; p++) {
-                int64_t ready = t;
-                if (avail[p] > ready) ready = avail[p];
-                if (drt[pl->proc_mem[p]] > ready) ready = drt[pl->proc_mem[p]];
-                int64_t ex = or_exec_ns(pl, tk->op, pl->proc_type[p], tk->bs);
-                int64_t eft = ready + ex;
-                if (best < 0 || eft < best_eft) { best = p; best_eft = eft; best_exec = ex; }
-            }
-            int ms = pl->proc_mem[best];
-            /* commit: transfers, then write-back invalidation of written atoms */
-            int64_t elems_from2[OR_MAX_MEMS];
-            for (int sm = 0; sm < M; sm++) elems_from2[sm] = 0;
-            for (int64_t e = 0; e < na; e++) {
-                int64_t x = ax[e];
-                int sm = src[e * M + ms];
-                if (sm >= 0) {
-                    valid[x * M + ms] = 1;
-                    vfrom[x * M + ms] = arrive[ms][sm];
-                    elems_from2[sm] += atom_elems;
-                }
-            }
-            for (int sm = 0; sm < M; sm++)
-                if (elems_from2[sm] > 0) { s.n_transfers++; s.xfer_elems += elems_from2[sm]; }
-            for (int64_t e = 0; e < na; e++) {
-                if (!axw[e]) continue;
-                int64_t x = ax[e];
-                for (int m = 0; m < M; m++) valid[x * M + m] = 0;
-                valid[x * M + ms] = 1;
-                vfrom[x * M + ms] = best_eft;
-            }
-            avail[best] = best_eft;
-            finish[j] = best_eft;
-            state[j] = 1;
-            inflight[n_inflight++] = j;
-            if (proc_out) proc_out[j] = (int16_t)best;
-            if (start_out) start_out[j] = best_eft - best_exec;
-            if (finish_out) finish_out[j] = best_eft;
-            if (order_out) order_out[n_sched] = j;
-            n_sched++;
-            if (best_eft > s.makespan) s.makespan = best_eft;
+        for (int32_t j = T - 1; j >= 0; j--) {
+            int64_t w = 0, best = 0;
+            for (int p = 0; p < P; p++) w += or_exec_ns(pl, d.t[j].op, pl->proc_type[p], d.t[j].bs);
+            for (int64_t e = succ_off[j]; e < succ_off[j + 1]; e++)
+                if (crit[succ[e]] > best) best = crit[succ[e]];
+            crit[j] = w + best;
         }
-        nrel = 0;
-        /* next completion time */
-        int64_t tn = -1;
-        for (int32_t q = 0; q < n_inflight; q++)
-            if (tn < 0 || finish[inflight[q]] < tn) tn = finish[inflight[q]];
-        if (tn < 0) break;
-        t = tn;
-        s.n_events++;
-        for (int32_t q = 0; q < n_inflight;) {
-            int32_t j = inflight[q];
-            if (finish[j] == t) {
-                state[j] = 2;
-                n_done++;
-                for (int64_t e = succ_off[j]; e < succ_off[j + 1]; e++) {
-                    int32_t sj = succ[e];
-                    if (--pending[sj] == 0) released[nrel++] = sj;
+        for (int32_t j = 0; j < T; j++) list[j] = j;
+        g_crit = crit;
+        qsort(list, (size_t)T, sizeof(int32_t), by_crit_desc);
+        for (int32_t q = 0; q < T && !rc; q++) {
+            int32_t j = list[q];
+            rc = schedule_task(&S, j, rel[j]);
+            if (rc) break;
+            for (int64_t e = succ_off[j]; e < succ_off[j + 1]; e++)
+                if (S.finish_j > rel[succ[e]]) rel[succ[e]] = S.finish_j;
+            n_done++;
+        }
+        free(crit);
+        free(rel);
+        free(list);
+        if (rc) goto out;
+    } else {
+        int32_t nrel = 0;
+        for (int32_t j = 0; j < T; j++)
+            if (pending[j] == 0) released[nrel++] = j;
+        int64_t t = 0;
+        for (;;) {
+            /* schedule the released tasks in ascending id */
+            for (int32_t a1 = 1; a1 < nrel; a1++) {
+                int32_t v = released[a1];
+                int32_t a2 = a1 - 1;
+                while (a2 >= 0 && released[a2] > v) { released[a2 + 1] = released[a2]; a2--; }
+                released[a2 + 1] = v;
+            }
+            for (int32_t q = 0; q < nrel; q++) {
+                int32_t j = released[q];
+                rc = schedule_task(&S, j, t);
+                if (rc) goto out;
+                finish[j] = S.finish_j;
+                state[j] = 1;
+                inflight[n_inflight++] = j;
+            }
+            nrel = 0;
+            /* next completion time */
+            int64_t tn = -1;
+            for (int32_t q = 0; q < n_inflight; q++)
+                if (tn < 0 || finish[inflight[q]] < tn) tn = finish[inflight[q]];
+            if (tn < 0) break;
+            t = tn;
+            s.n_events++;
+            for (int32_t q = 0; q < n_inflight;) {
+                int32_t j = inflight[q];
+                if (finish[j] == t) {
+                    state[j] = 2;
+                    n_done++;
+                    for (int64_t e = succ_off[j]; e < succ_off[j + 1]; e++) {
+                        int32_t sj = succ[e];
+                        if (--pending[sj] == 0) released[nrel++] = sj;
+                    }
+                    inflight[q] = inflight[--n_inflight];
+                } else {
+                    q++;
                 }
-                inflight[q] = inflight[--n_inflight];
-            } else {
-                q++;
             }
         }
     }
+    int32_t n_sched = S.n_sched;
     if (n_sched != T || n_done != T) rc = OR_ERR_STATE;
     s.n_tasks = T;
 out:
