@@ -51,6 +51,7 @@ Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem, int64_t ta
     a.off_vfrom = o; o = align256(o + 8 * a.Acap * mp);
     a.off_bitmap = o; o = align256(o + 4 * ((a.Tcap + 31) / 32));
     a.off_xt = o; o = align256(o + 8 * a.Kcap);
+    a.off_hist = o; o = align256(o + 4 * 256);  // radix histogram of the priority-list sort
     a.slot_bytes = o;
     return a;
 }
@@ -68,6 +69,17 @@ static DevPlatform dev_platform(const hesp_platform *p) {
         d.proc_mem[i] = (int8_t)p->procs[i].memory;
         d.proc_type[i] = (int8_t)p->procs[i].type;
     }
+    d.order = p->order;
+    d.select = p->select;
+    for (int op = 0; op < 4; ++op)
+        for (int l = 0; l < HESP_LB; ++l) {
+            int64_t s = 0;
+            for (int i = 0; i < p->n_procs && s >= 0; ++i) {
+                const int64_t e = p->exec[op][p->procs[i].type][l];
+                s = (e < 0 || s + e >= (1LL << 40)) ? -1 : s + e;
+            }
+            d.wsum[op * HESP_LB + l] = s;
+        }
     d.lat = p->xfer_latency_ns;
     d.bpe = p->bytes_per_elem;
     d.bw = p->bw_bytes_per_ns;
@@ -170,6 +182,13 @@ int hesp_platform_set_exec_table(hesp_platform *p, int32_t op, int32_t type, int
     const int l = log2_exact(block);
     if (l < 0 || l > HESP_MAX_LOG2_BLOCK) return HESP_ERR_ARG;
     p->exec[op][type][l] = ns;
+    return HESP_OK;
+}
+
+int hesp_platform_set_policy(hesp_platform *p, int32_t order, int32_t select) {
+    if (!p || order < 0 || order > 1 || select < 0 || select > 1) return HESP_ERR_ARG;
+    p->order = order;
+    p->select = select;
     return HESP_OK;
 }
 

@@ -20,6 +20,8 @@ struct hesp_platform {
     // launch shape chosen by hesp_sim_autotune or set by the caller (0 = default)
     int32_t tune_ctas_per_sm;
     int32_t tune_bitmap;  // 0 auto, 1 arena (global memory), 2 shared memory when it fits
+    // scheduling heuristics (Sec. 2.1): task order 0 FCFS / 1 PL, processor choice 0 EFT-P / 1 EIT-P
+    int32_t order, select;
 };
 
 struct hesp_dag {
@@ -34,7 +36,9 @@ namespace hesp {
 // copied to shared memory at kernel start.
 struct DevPlatform {
     int32_t n_mem, n_types, n_procs, pad;
+    int32_t order, select;  // task order (0 FCFS, 1 PL) and processor choice (0 EFT-P, 1 EIT-P)
     int64_t exec[4 * HESP_MAX_TYPES * HESP_LB];
+    int64_t wsum[4 * HESP_LB];  // task time summed over all processors, per (op, log2 block); -1 if any is -1
     int8_t proc_mem[HESP_MAX_PROCS];
     int8_t proc_type[HESP_MAX_PROCS];
     int64_t lat, bpe, bw;
@@ -53,7 +57,7 @@ struct Arena {
     // link area and the per-task marks in the successor offsets: neither is
     // in use at the same time as what it shares memory with.
     int64_t off_desc, off_pending, off_link, off_next, off_succoff, off_succ, off_epred, off_esucc, off_lw,
-        off_vfrom, off_bitmap, off_xt;
+        off_vfrom, off_bitmap, off_xt, off_hist;
 };
 
 // Header at the start of the workspace.

@@ -28,6 +28,8 @@
 #include <limits.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "hesp_internal.h"
 
 namespace hesp {
@@ -199,6 +201,14 @@ __device__ __forceinline__ uint64_t warp_min_u64(uint64_t k) {
     return ((uint64_t)hmin << 32) | lmin;
 }
 
+// Max over the warp of a 64-bit unsigned value, via two 32-bit reductions.
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t k) {
+    unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
+    unsigned hmax = __reduce_max_sync(FULL, hi);
+    unsigned lmax = __reduce_max_sync(FULL, hi == hmax ? lo : 0u);
+    return ((uint64_t)hmax << 32) | lmax;
+}
+
 // Per-processor FIFO of tasks in flight, threaded through the tasks.  For a
 // task in flight: its successor in the FIFO and that successor's finish time,
 // and the range of its own successor list, all read together when it
@@ -289,12 +299,13 @@ struct Counts {
 // Schedule task j at time t: data-ready time per memory, EFT over the
 // processors (ties to the lowest id), commit of the coherence state, append
 // to the chosen processor's FIFO.  Clears `ok` on an internal inconsistency.
-template <int M, int NS>
-__device__ __forceinline__ void schedule_task(int j, int64_t t, char *base, const KArgs &a, int Lc, int lb_b,
-                                              int lane, const int64_t *s_exec, const int8_t *s_pmem,
-                                              const int8_t *s_ptype, const int pm[NS], const int pt[NS],
-                                              const bool pv[NS], int64_t avail[NS], int head[NS], int tail[NS],
-                                              int64_t hfin[NS], int64_t &mk, bool &ok, int64_t sched_base) {
+template <int M, int NS, bool FIFO>
+__device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, const KArgs &a, int Lc, int lb_b,
+                                                 int lane, const int64_t *s_exec, const int8_t *s_pmem,
+                                                 const int8_t *s_ptype, const int pm[NS], const int pt[NS],
+                                                 const bool pv[NS], int64_t avail[NS], int head[NS], int tail[NS],
+                                                 int64_t hfin[NS], int64_t &mk, bool &ok, int64_t sched_base,
+                                                 bool eit) {
     const uint64_t d = at<uint64_t>(base, a.ar.off_desc)[j];
     const int32_t *const succoff = at<int32_t>(base, a.ar.off_succoff);
     const int se0 = succoff[j], se1 = succoff[j + 1];  // kept with the task while it is in flight
@@ -314,7 +325,13 @@ __device__ __forceinline__ void schedule_task(int j, int64_t t, char *base, cons
 #pragma unroll
     for (int m = 0; m < M; ++m) drt_off[m] = 0;
     if (M > 1) {
-        unsigned amax[M];
+        // latest (usable-from time - t) of a valid copy per memory.  Under
+        // FCFS a task starts once all its predecessors finished, so a copy can
+        // lead t by one message time at most (31 bits, else an error status);
+        // under the priority-list order a copy issued for a task placed
+        // earlier may arrive far beyond t, so 64 bits.
+        using Lead = typename std::conditional<FIFO, unsigned, uint64_t>::type;
+        Lead amax[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) amax[m] = 0;
         for (int i0 = 0; i0 < tot; i0 += 32) {
@@ -329,8 +346,12 @@ __device__ __forceinline__ void schedule_task(int j, int64_t t, char *base, cons
                     if (st.v[m] >= 0) {
                         const int64_t dd = st.v[m] - t;
                         if (dd > 0) {
-                            ok &= dd <= 0x7FFFFFFFLL;
-                            amax[m] = max(amax[m], (unsigned)min(dd, (int64_t)0x7FFFFFFF));
+                            if (FIFO) {
+                                ok &= dd <= 0x7FFFFFFFLL;
+                                amax[m] = max(amax[m], (Lead)min(dd, (int64_t)0x7FFFFFFF));
+                            } else {
+                                amax[m] = max(amax[m], (Lead)dd);
+                            }
                         }
                     } else {
                         ok &= src >= 0;
@@ -343,7 +364,8 @@ __device__ __forceinline__ void schedule_task(int j, int64_t t, char *base, cons
         for (int k = 0; k < Counts<M>::NW; ++k) cnt.w[k] = __reduce_add_sync(FULL, cnt.w[k]);
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-            int64_t off = (int64_t)__reduce_max_sync(FULL, amax[m]);
+            int64_t off = FIFO ? (int64_t)__reduce_max_sync(FULL, (unsigned)amax[m])
+                               : (int64_t)warp_max_u64((uint64_t)amax[m]);
 #pragma unroll
             for (int s = 0; s < M; ++s) {
                 if (s == m) continue;
@@ -353,13 +375,17 @@ __device__ __forceinline__ void schedule_task(int j, int64_t t, char *base, cons
             drt_off[m] = off;
         }
     }
-    // EFT over processors; key = EFT << 6 | proc, ties to the lowest id.
+    // Processor choice, key = value << 6 | proc (ties to the lowest id):
+    // EFT-P by the finish time, EIT-P by the time the processor is idle.
     uint64_t key = ~0ull;
+    int64_t emine[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
+        emine[s] = 0;
         if (pv[s]) {
             const int64_t ex = s_exec[(op * HESP_MAX_TYPES + pt[s]) * HESP_LB + lb];
             int64_t ready = max(t, avail[s]);
+            const int64_t idle = ready;
             if (M > 1) {
                 int64_t off = 0;
 #pragma unroll
@@ -368,13 +394,21 @@ __device__ __forceinline__ void schedule_task(int j, int64_t t, char *base, cons
                 ready = max(ready, t + off);
             }
             const int64_t e = ready + ex;
+            emine[s] = e;
             ok &= ex >= 0 && e < (1ll << 57);
-            key = min(key, ((uint64_t)e << 6) | (uint64_t)(lane + 32 * s));
+            key = min(key, ((uint64_t)(eit ? idle : e) << 6) | (uint64_t)(lane + 32 * s));
         }
     }
     key = warp_min_u64(key);
     const int pbest = (int)(key & 63);
-    const int64_t eft = (int64_t)(key >> 6);
+    int64_t eft = (int64_t)(key >> 6);
+    if (eit) {
+        int64_t mine = emine[0];
+#pragma unroll
+        for (int s = 1; s < NS; ++s)
+            if ((pbest >> 5) == s) mine = emine[s];
+        eft = __shfl_sync(FULL, mine, pbest & 31);
+    }
     const int ms = s_pmem[pbest];
 
     if (M > 1) {
@@ -422,7 +456,8 @@ __device__ __forceinline__ void schedule_task(int j, int64_t t, char *base, cons
         const int s = pbest >> 5;
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
-            if (q == s) {
+            if (q == s && !FIFO) avail[q] = eft;
+            if (q == s && FIFO) {
                 avail[q] = eft;
                 if (head[q] < 0) {
                     head[q] = j;
@@ -448,15 +483,18 @@ __device__ __forceinline__ void schedule_task(int j, int64_t t, char *base, cons
     }
     mk = max(mk, eft);
     __syncwarp();
+    return eft;
 }
 
-template <int M, int NS>
+template <int M, int NS, bool GEN>
 __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, unsigned long long *work_counter) {
     __shared__ int64_t s_exec[4 * HESP_MAX_TYPES * HESP_LB];
+    __shared__ int64_t s_wsum[4 * HESP_LB];
     __shared__ int8_t s_pmem[HESP_MAX_PROCS];
     __shared__ int8_t s_ptype[HESP_MAX_PROCS];
     extern __shared__ uint32_t s_bitmap[];
     for (int i = threadIdx.x; i < 4 * HESP_MAX_TYPES * HESP_LB; i += blockDim.x) s_exec[i] = pl.exec[i];
+    for (int i = threadIdx.x; i < 4 * HESP_LB; i += blockDim.x) s_wsum[i] = pl.wsum[i];
     for (int i = threadIdx.x; i < HESP_MAX_PROCS; i += blockDim.x) {
         s_pmem[i] = pl.proc_mem[i];
         s_ptype[i] = pl.proc_type[i];
@@ -692,6 +730,106 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                     xt[k] = k == 0 ? 0 : pl.lat + (bytes + pl.bw - 1) / pl.bw;
                 }
             }
+            // GEN = false: the FCFS + EFT-P instantiation; GEN = true: every
+            // policy, chosen at run time from the platform.
+            const bool eit = GEN && pl.select == HESP_SELECT_EIT;
+            if (GEN && pl.order == HESP_ORDER_PL) {
+                // ---- PL: a priority list by critical time (HEFT-like); each task
+                // is scheduled at its release time, the latest finish among its
+                // predecessors.  Critical times, release times and the two sort
+                // buffers use the FIFO link area (no FIFOs in this order).
+                int64_t *const crit = at<int64_t>(base, a.ar.off_link);
+                int64_t *const rel = crit + T;
+                uint64_t *const keyA = reinterpret_cast<uint64_t *>(crit + 2 * T);
+                uint64_t *const keyB = reinterpret_cast<uint64_t *>(crit + 3 * T);
+                uint32_t *const hist = at<uint32_t>(base, a.ar.off_hist);
+                const int32_t *const succoff = at<int32_t>(base, a.ar.off_succoff);
+                const int32_t *const succ = at<int32_t>(base, a.ar.off_succ);
+                const unsigned lt_mask = (1u << lane) - 1u;
+                bool okp = T < (1 << 22);
+                // critical time = time summed over the processors + largest successor's, backwards
+                for (int j = (int)T - 1; j >= 0 && okp; --j) {
+                    const uint64_t d = desc[j];
+                    const int e0 = succoff[j], e1 = succoff[j + 1];
+                    uint64_t mx = 0;
+                    for (int e = e0 + lane; e < e1; e += 32) mx = max(mx, (uint64_t)crit[succ[e]]);
+                    mx = warp_max_u64(mx);
+                    const int64_t w = s_wsum[(int)(d & 3) * HESP_LB + lb_b - (int)((d >> 2) & 7)];
+                    const int64_t cj = (int64_t)mx + w;
+                    okp = okp && w > 0 && cj < (1ll << 41);
+                    if (lane == 0) crit[j] = cj;
+                    __syncwarp();
+                }
+                // sort keys (2^41 - 1 - crit) << 22 | id ascending: decreasing critical time, then id
+                for (int64_t j = lane; j < T && okp; j += 32) {
+                    keyA[j] = ((uint64_t)((1ll << 41) - 1 - crit[j]) << 22) | (uint64_t)j;
+                    rel[j] = 0;
+                }
+                __syncwarp();
+                uint64_t *src = keyA, *dst = keyB;
+                for (int pass = 0; pass < 8 && okp; ++pass) {  // LSD radix sort, 8-bit digits
+                    const int sh = pass * 8;
+                    for (int k = lane; k < 256; k += 32) hist[k] = 0;
+                    __syncwarp();
+                    for (int64_t i = lane; i < T; i += 32) atomicAdd(&hist[(src[i] >> sh) & 255], 1u);
+                    __syncwarp();
+                    uint32_t v[8], sum = 0;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        v[q] = hist[lane * 8 + q];
+                        sum += v[q];
+                    }
+                    uint32_t run = (uint32_t)warp_incl_scan((int)sum, lane) - sum;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        hist[lane * 8 + q] = run;
+                        run += v[q];
+                    }
+                    __syncwarp();
+                    for (int64_t i0 = 0; i0 < T; i0 += 32) {
+                        const int64_t i = i0 + lane;
+                        const bool act = i < T;
+                        const uint64_t k = act ? src[i] : 0;
+                        const int dg = act ? (int)((k >> sh) & 255) : 256 + lane;
+                        const unsigned grp = __match_any_sync(FULL, dg);
+                        const int rank = __popc(grp & lt_mask);
+                        const uint32_t b0 = act ? hist[dg] : 0;
+                        __syncwarp();
+                        if (act) {
+                            dst[b0 + rank] = k;
+                            if (rank == 0) hist[dg] = b0 + __popc(grp);
+                        }
+                        __syncwarp();
+                    }
+                    uint64_t *tmp = src;
+                    src = dst;
+                    dst = tmp;
+                }
+                int64_t avail[NS], hfin[NS];
+                int head[NS], tail[NS];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    avail[s] = 0;
+                    hfin[s] = kInf;
+                    head[s] = -1;
+                    tail[s] = -1;
+                }
+                const int64_t sched_base = a.sched_off ? a.sched_off[c] : -1;
+                bool ok = true;
+                for (int64_t q = 0; q < T && okp; ++q) {
+                    const int j = (int)(src[q] & ((1u << 22) - 1));
+                    const int64_t fj = schedule_task<M, NS, false>(j, rel[j], base, a, Lc, lb_b, lane, s_exec, s_pmem,
+                                                                   s_ptype, pm, pt, pv, avail, head, tail, hfin, mk,
+                                                                   ok, sched_base, eit);
+                    const int e0 = succoff[j], e1 = succoff[j + 1];
+                    for (int e = e0 + lane; e < e1; e += 32) {
+                        const int sj = succ[e];
+                        if (fj > rel[sj]) rel[sj] = fj;
+                    }
+                    __syncwarp();
+                }
+                if (!__all_sync(FULL, ok && okp)) status = HESP_ERR_STATE;
+            } else {
             const int W = (int)((T + 31) >> 5);
             int wlo = INT_MAX, whi = -1;
             for (int w0 = 0; w0 < W; w0 += 32) {
@@ -738,8 +876,8 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                         const int j = __reduce_min_sync(FULL, dj);
                         if (j == INT_MAX) break;
                         if (dj == j) dj = INT_MAX;
-                        schedule_task<M, NS>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
-                                             avail, head, tail, hfin, mk, ok, sched_base);
+                        schedule_task<M, NS, true>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
+                                                   avail, head, tail, hfin, mk, ok, sched_base, eit);
                         ++scheduled;
                     }
                     direct = false;
@@ -760,8 +898,9 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                             while (wb) {
                                 const int bit = __ffs(wb) - 1;
                                 wb &= wb - 1;
-                                schedule_task<M, NS>(jb + bit, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype,
-                                                     pm, pt, pv, avail, head, tail, hfin, mk, ok, sched_base);
+                                schedule_task<M, NS, true>(jb + bit, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype,
+                                                           pm, pt, pv, avail, head, tail, hfin, mk, ok, sched_base,
+                                                           eit);
                                 ++scheduled;
                             }
                         }
@@ -837,6 +976,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
             }
             if (!__all_sync(FULL, ok)) status = HESP_ERR_STATE;
             if (status == HESP_OK && scheduled != T) status = HESP_ERR_STATE;
+            }
         }
 
         if (lane == 0) {
@@ -850,12 +990,20 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
 
 template <int M, int NS>
 void occupancy_of(int *blocks, size_t smem) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, sim_kernel<M, NS>, 256, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, sim_kernel<M, NS, false>, 256, smem);
 }
 
 template <int M, int NS>
 void set_smem_attr(size_t smem) {
-    cudaFuncSetAttribute(sim_kernel<M, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(sim_kernel<M, NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(sim_kernel<M, NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int M, int NS>
+void launch_one(bool gen, unsigned blocks, int threads, size_t smem, cudaStream_t stream, const DevPlatform &dp,
+                const KArgs &a, unsigned long long *ctr) {
+    if (gen) sim_kernel<M, NS, true><<<blocks, threads, smem, stream>>>(dp, a, ctr);
+    else sim_kernel<M, NS, false><<<blocks, threads, smem, stream>>>(dp, a, ctr);
 }
 
 }  // namespace
@@ -914,23 +1062,17 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
     const size_t smem = (size_t)a.bm_smem_words * 4 * (threads / 32);
     const int64_t blocks = (n_slots * 32 + threads - 1) / threads;
     const bool two = p->n_procs > 32;
+    const unsigned ub = (unsigned)blocks;
+    const bool gen = p->order != HESP_ORDER_FCFS || p->select != HESP_SELECT_EFT;
     switch (p->n_mem) {
-    case 1:
-        if (two) sim_kernel<1, 2><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
-        else sim_kernel<1, 1><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
-        break;
-    case 2:
-        if (two) sim_kernel<2, 2><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
-        else sim_kernel<2, 1><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
-        break;
-    case 3:
-        if (two) sim_kernel<3, 2><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
-        else sim_kernel<3, 1><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
-        break;
-    case 4:
-        if (two) sim_kernel<4, 2><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
-        else sim_kernel<4, 1><<<(unsigned)blocks, threads, smem, stream>>>(dp, a, ctr);
-        break;
+    case 1: two ? launch_one<1, 2>(gen, ub, threads, smem, stream, dp, a, ctr)
+                : launch_one<1, 1>(gen, ub, threads, smem, stream, dp, a, ctr); break;
+    case 2: two ? launch_one<2, 2>(gen, ub, threads, smem, stream, dp, a, ctr)
+                : launch_one<2, 1>(gen, ub, threads, smem, stream, dp, a, ctr); break;
+    case 3: two ? launch_one<3, 2>(gen, ub, threads, smem, stream, dp, a, ctr)
+                : launch_one<3, 1>(gen, ub, threads, smem, stream, dp, a, ctr); break;
+    case 4: two ? launch_one<4, 2>(gen, ub, threads, smem, stream, dp, a, ctr)
+                : launch_one<4, 1>(gen, ub, threads, smem, stream, dp, a, ctr); break;
     default:
         return HESP_ERR_ARG;
     }

@@ -36,8 +36,9 @@ EXPORTS = (
     "hesp_make_cands", "hesp_gather_f32", "hesp_rank_metrics_workspace_size", "hesp_rank_metrics",
     "hesp_generate_mutants", "hesp_gather_rows", "hesp_best_makespan", "hesp_graph_begin", "hesp_graph_end",
     "hesp_graph_launch", "hesp_graph_destroy", "hesp_platform_set_tuning", "hesp_platform_get_tuning",
-    "hesp_sim_autotune", "hesp_sort_cands_workspace_size", "hesp_sort_cands_by_size",
+    "hesp_sim_autotune", "hesp_sort_cands_workspace_size", "hesp_sort_cands_by_size", "hesp_platform_set_policy",
 )
+ORDER_FCFS, ORDER_PL, SELECT_EFT, SELECT_EIT = 0, 1, 0, 1
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 CAND_DTYPE = np.dtype([("n_tiles", "<i4"), ("b", "<i4"), ("level_offset", "<i8")])
@@ -127,6 +128,7 @@ def lib():
                                         ctypes.POINTER(i32), ctypes.POINTER(i32), vp, vp]
         L.hesp_sort_cands_workspace_size.argtypes = [i64, ctypes.POINTER(sz)]
         L.hesp_sort_cands_by_size.argtypes = [vp, vp, i64, vp, vp, vp, sz, vp]
+        L.hesp_platform_set_policy.argtypes = [vp, i32, i32]
         L.hesp_best_makespan.argtypes = [vp, vp, vp, i64, vp, vp]
         L.hesp_gather_rows.argtypes = [vp, vp, i64, i64, vp, vp]
         L.hesp_generate_mutants.argtypes = [vp, i32, i32, i32, ctypes.c_double, u64, i64, i64, vp, vp]
@@ -156,7 +158,7 @@ class Platform:
     """A simulated platform (hesp_platform handle) built from a
     ``workloads.PlatformSpec``."""
 
-    def __init__(self, spec):
+    def __init__(self, spec, order=0, select=0):
         self.spec = spec
         L = lib()
         types = (_PType * len(spec.types))()
@@ -174,6 +176,7 @@ class Platform:
         self.h = h
         for (op, ty, bs, ns) in getattr(spec, "exec_overrides", ()):
             check(L.hesp_platform_set_exec_table(h, op, ty, bs, ns), "hesp_platform_set_exec_table")
+        check(L.hesp_platform_set_policy(h, order, select), "hesp_platform_set_policy")
 
     @property
     def n_mem(self):

@@ -259,3 +259,39 @@ def test_cfg4_full_size_candidates():
     lv = W.workload_levels("cfg4", 0, 2)
     g = gpu_sim(W.PLATFORMS["cfg4"], 32, 2048, lv, max_level=3, task_cap=1 << 20)
     check_parity(W.PLATFORMS["cfg4"], 32, 2048, lv, g, schedule=False)
+
+
+@pytest.mark.parametrize("order,select", [(0, 1), (1, 0), (1, 1)])
+def test_policies_parity(order, select):
+    """PL task order and EIT-P processor choice (Sec. 2.1) against the oracle:
+    schedules bit-exact on every workload shape."""
+    cases = [("cfg0", 3, 1024, W.workload_levels("cfg0")[::8], 1),
+             ("cfg1a", 8, 2048, W.workload_levels("cfg1", 300, 48), 2),
+             ("cfg1b", 8, 2048, W.workload_levels("cfg1", 900, 48), 2),
+             ("cfg2", 6, 512, np.random.default_rng(1).integers(0, 3, (24, W.base_count(6))).astype(np.int8), 2),
+             ("cfg4", 5, 2048, np.random.default_rng(2).integers(0, 4, (16, W.base_count(5))).astype(np.int8), 3)]
+    for key, n, b, lv, L in cases:
+        spec = W.PLATFORMS[key]
+        plat = hesp.Platform(spec, order=order, select=select)
+        C, nb = lv.shape
+        d_lv = torch.from_numpy(np.ascontiguousarray(lv).reshape(-1).copy()).cuda()
+        cands = hesp.cands_tensor(n, b, np.arange(C, dtype=np.int64) * nb)
+        ws = hesp.alloc_workspace(plat, n, L, C)
+        dag = hesp.Dag(n, b, L)
+        cnt = np.array([dag.count_tasks(lv[c])[0] for c in range(C)], np.int64)
+        offs = np.zeros(C + 1, np.int64)
+        offs[1:] = np.cumsum(cnt)
+        tot = int(offs[-1])
+        sched = (torch.from_numpy(offs[:-1].copy()).cuda(), torch.empty(tot, dtype=torch.int16, device="cuda"),
+                 torch.empty(tot, dtype=torch.int64, device="cuda"), torch.empty(tot, dtype=torch.int64, device="cuda"))
+        ms, st, _ = hesp.simulate_batch(plat, cands, d_lv, C, n, L, ws, schedule=sched)
+        torch.cuda.synchronize()
+        ms, st = ms.cpu().numpy(), st.cpu().numpy()
+        proc, start, fin = (x.cpu().numpy() for x in sched[1:])
+        pl = O.make_platform(spec, order=order, select=select)
+        for c in range(C):
+            r = O.simulate(pl, n, b, lv[c])
+            assert st[c] == 0 and ms[c] == r["makespan"], (key, c)
+            a, e = offs[c], offs[c + 1]
+            assert np.array_equal(proc[a:e], r["proc"]) and np.array_equal(start[a:e], r["start"]), (key, c)
+            assert np.array_equal(fin[a:e], r["finish"]), (key, c)
