@@ -71,6 +71,7 @@ class Platform(ctypes.Structure):
         ("ovr_ns", ctypes.c_int64 * MAX_OVR),
         ("order", ctypes.c_int32),
         ("select", ctypes.c_int32),
+        ("rp_seed", ctypes.c_uint64),
     ]
 
 
@@ -105,10 +106,10 @@ def lib():
         L.or_deps.argtypes = [i32, i64, vp, i64, i64, i32, i32, i64, vp, vp, vp]
         L.or_simulate.restype = i32
         L.or_simulate.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i64, i64, i32, i32,
-                                  vp, vp, vp, vp, ctypes.POINTER(Stats)]
+                                  vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
         L.or_simulate_levels.restype = i32
         L.or_simulate_levels.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i32, i32,
-                                         vp, vp, vp, vp, ctypes.POINTER(Stats)]
+                                         vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
         L.or_simulate_many.restype = i32
         L.or_simulate_many.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i64, vp, vp, vp]
         _lib = L
@@ -116,12 +117,14 @@ def lib():
 
 
 ORDER_FCFS, ORDER_PL = 0, 1
-SELECT_EFT, SELECT_EIT = 0, 1
+SELECT_EFT, SELECT_EIT, SELECT_FP, SELECT_RP = 0, 1, 2, 3
 
 
-def make_platform(desc, order: int = ORDER_FCFS, select: int = SELECT_EFT) -> Platform:
+def make_platform(desc, order: int = ORDER_FCFS, select: int = SELECT_EFT, rp_seed: int = 0) -> Platform:
     """Oracle platform from a plain description (a dict or an object with the
-    fields of ``paper_1602_05510_b300.workloads.PlatformSpec``)."""
+    fields of ``paper_1602_05510_b300.workloads.PlatformSpec``), with the
+    task order (FCFS / PL), the processor selection (EFT-P / EIT-P / F-P /
+    R-P) and the seed of R-P's draws."""
     g = (lambda k: desc[k]) if isinstance(desc, dict) else (lambda k: getattr(desc, k))
     pl = Platform()
     pl.n_mem = g("n_mem")
@@ -146,7 +149,7 @@ def make_platform(desc, order: int = ORDER_FCFS, select: int = SELECT_EFT) -> Pl
     pl.n_ovr = len(ovr)
     for i, (op, ty, bs, ns) in enumerate(ovr):
         pl.ovr_op[i], pl.ovr_type[i], pl.ovr_bs[i], pl.ovr_ns[i] = op, ty, bs, ns
-    pl.order, pl.select = order, select
+    pl.order, pl.select, pl.rp_seed = order, select, rp_seed
     return pl
 
 
@@ -229,23 +232,25 @@ def simulate_code(pl: Platform, n: int, b: int, code, atom_level: int, dep_mode:
     start = np.zeros(cap, np.int64) if schedule else None
     fin = np.zeros(cap, np.int64) if schedule else None
     order = np.zeros(cap, np.int32) if schedule else None
+    issue = np.zeros(cap, np.int64) if schedule else None
     st = Stats()
     rc = lib().or_simulate(ctypes.byref(pl), n, b, code.ctypes.data, len(code), cap, atom_level, dep_mode,
                            proc.ctypes.data if schedule else None,
                            start.ctypes.data if schedule else None,
                            fin.ctypes.data if schedule else None,
-                           order.ctypes.data if schedule else None, ctypes.byref(st))
-    return _result(rc, st, proc, start, fin, order)
+                           order.ctypes.data if schedule else None,
+                           issue.ctypes.data if schedule else None, ctypes.byref(st))
+    return _result(rc, st, proc, start, fin, order, issue)
 
 
-def _result(rc, st, proc, start, fin, order):
+def _result(rc, st, proc, start, fin, order, issue):
     T = int(st.n_tasks)
     out = dict(status=int(rc), makespan=int(st.makespan), n_tasks=T, n_events=int(st.n_events),
                n_transfers=int(st.n_transfers), xfer_elems=int(st.xfer_elems),
                atom_visits=int(st.atom_visits))
     if proc is not None:
         out.update(proc=proc[:T].copy(), start=start[:T].copy(), finish=fin[:T].copy(),
-                   order=order[:T].copy())
+                   order=order[:T].copy(), issue=issue[:T].copy())
     return out
 
 
@@ -258,13 +263,15 @@ def simulate(pl: Platform, n: int, b: int, levels, atom_level: int = -1, dep_mod
     start = np.zeros(cap, np.int64) if schedule else None
     fin = np.zeros(cap, np.int64) if schedule else None
     order = np.zeros(cap, np.int32) if schedule else None
+    issue = np.zeros(cap, np.int64) if schedule else None
     st = Stats()
     rc = lib().or_simulate_levels(ctypes.byref(pl), n, b, lv.ctypes.data, atom_level, dep_mode,
                                   proc.ctypes.data if schedule else None,
                                   start.ctypes.data if schedule else None,
                                   fin.ctypes.data if schedule else None,
-                                  order.ctypes.data if schedule else None, ctypes.byref(st))
-    return _result(rc, st, proc, start, fin, order)
+                                  order.ctypes.data if schedule else None,
+                                  issue.ctypes.data if schedule else None, ctypes.byref(st))
+    return _result(rc, st, proc, start, fin, order, issue)
 
 
 def simulate_many(pl: Platform, n: int, b: int, levels: np.ndarray, threads: int = 1):

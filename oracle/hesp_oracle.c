@@ -21,10 +21,10 @@
  *     both as the plain all-pairs definition and via per-atom last writers.
  *   - Sec. 2.1 "Performance and data transfer models": integer task times
  *     ceil(flops / rate) and transfer times latency + ceil(bytes / bw).
- *   - Sec. 2.1 "Task and data scheduling heuristics": FCFS task order at
- *     release time with the EFT-P processor choice, accelerator memories as
- *     write-back software caches of host memory (MSI), transfers issued at
- *     scheduling time (prefetch).
+ *   - Sec. 2.1 "Task and data scheduling heuristics": FCFS or priority-list
+ *     (PL) task order at release time with the EFT-P, EIT-P, F-P or R-P
+ *     processor choice, accelerator memories as write-back software caches
+ *     of host memory (MSI), transfers issued at scheduling time (prefetch).
  *   - Sec. 2 (problem statement): output is the task set, the task-to-
  *     processor mapping, and the makespan.
  *
@@ -70,9 +70,10 @@ typedef struct {
     int32_t ovr_op[OR_MAX_OVR], ovr_type[OR_MAX_OVR];
     int64_t ovr_bs[OR_MAX_OVR], ovr_ns[OR_MAX_OVR];
     /* scheduling heuristics (Sec. 2.1): task order 0 = FCFS, 1 = PL;
-     * processor selection 0 = EFT-P, 1 = EIT-P */
+     * processor selection 0 = EFT-P, 1 = EIT-P, 2 = F-P, 3 = R-P */
     int32_t order;
     int32_t select;
+    uint64_t rp_seed; /* R-P: seed of the per-task processor draws */
 } or_platform;
 
 /* A square data region in element coordinates of the full matrix. */
@@ -615,9 +616,32 @@ typedef struct {
     int16_t *proc_out;
     int64_t *start_out, *finish_out;
     int32_t *order_out;
+    int64_t *issue_out;
     int32_t n_sched;
     int64_t finish_j; /* finish time of the task just scheduled */
 } sched_state;
+
+/* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the stream value for
+ * counter (c, k) is the published output function applied to
+ * seed + ((c << 32) + k + 1) * 0x9E3779B97F4A7C15; a draw in [0, m) takes
+ * the high 32 bits times m, shifted down by 32 (Lemire). */
+static uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+static uint32_t sm64_draw(uint64_t seed, uint64_t c, uint64_t k, uint32_t m) {
+    uint64_t u = sm64_mix(seed + ((c << 32) + k + 1) * 0x9E3779B97F4A7C15ULL);
+    return (uint32_t)(((u >> 32) * (uint64_t)m) >> 32);
+}
+
+/* Is some processor idle at t (nothing running or queued on it after t)? */
+static int any_idle(const int64_t *avail, int32_t P, int64_t t) {
+    for (int p = 0; p < P; p++)
+        if (avail[p] <= t) return 1;
+    return 0;
+}
 
 /* Schedule task j at time t (see the rules above or_simulate). */
 static int schedule_task(sched_state *S, int32_t j, int64_t t) {
@@ -669,17 +693,33 @@ static int schedule_task(sched_state *S, int32_t j, int64_t t) {
     }
     /* processor selection, ties to the lowest id:
      *   EFT-P: the earliest finish time max(t, avail, DRT) + exec;
-     *   EIT-P: the processor that becomes idle first, max(t, avail). */
-    int32_t best = -1;
+     *   EIT-P: the processor that becomes idle first, max(t, avail);
+     *   F-P:   among the processors idle at t, the fastest for this task;
+     *   R-P:   among the processors idle at t, the k-th in id order, k drawn
+     *          uniformly from the SplitMix64 stream (rp_seed, task id j). */
+    int32_t n_idle = 0, pick = -1;
+    if (pl->select >= 2) {
+        for (int p = 0; p < P; p++)
+            if (S->avail[p] <= t) n_idle++;
+        if (n_idle == 0) return OR_ERR_STATE;
+        if (pl->select == 3) pick = (int32_t)sm64_draw(pl->rp_seed, (uint64_t)j, 0, (uint32_t)n_idle);
+    }
+    int32_t best = -1, idle_seen = 0;
     int64_t best_key = 0, best_eft = 0, best_exec = 0;
     for (int p = 0; p < P; p++) {
+        if (pl->select >= 2 && S->avail[p] > t) continue;
         int64_t ready = t;
         if (S->avail[p] > ready) ready = S->avail[p];
         int64_t idle = ready;
         if (drt[pl->proc_mem[p]] > ready) ready = drt[pl->proc_mem[p]];
         int64_t ex = or_exec_ns(pl, tk->op, pl->proc_type[p], tk->bs);
         int64_t eft = ready + ex;
-        int64_t key = pl->select == 1 ? idle : eft;
+        int64_t key;
+        if (pl->select == 0) key = eft;
+        else if (pl->select == 1) key = idle;
+        else if (pl->select == 2) key = ex;
+        else key = (idle_seen == pick) ? 0 : 1;
+        idle_seen++;
         if (best < 0 || key < best_key) { best = p; best_key = key; best_eft = eft; best_exec = ex; }
     }
     int ms = pl->proc_mem[best];
@@ -710,6 +750,7 @@ static int schedule_task(sched_state *S, int32_t j, int64_t t) {
     if (S->start_out) S->start_out[j] = best_eft - best_exec;
     if (S->finish_out) S->finish_out[j] = best_eft;
     if (S->order_out) S->order_out[S->n_sched] = j;
+    if (S->issue_out) S->issue_out[j] = t;
     S->n_sched++;
     if (best_eft > S->st->makespan) S->st->makespan = best_eft;
     return OR_OK;
@@ -728,15 +769,21 @@ static int by_crit_desc(const void *a, const void *b) {
  *   atom_level:    atom side = b / 2^atom_level (>= deepest split)
  *   dep_mode:      0 = all-pairs dependences, 1 = atom last-writer
  * Optional outputs (NULL to skip), per task in creation order:
- *   proc_out, start_out, finish_out; order_out = task ids in the order they
- *   were scheduled.
+ *   proc_out, start_out, finish_out, issue_out (the time at which the task
+ *   was scheduled and its messages issued); order_out = task ids in the
+ *   order they were scheduled.
  * The scheduling rules (Sec. 2.1, WB caching, prefetch), with task order
  * FCFS (pl->order 0) -- PL (order 1) is described at its loop below:
  *   1. t = 0; the released set holds the tasks without predecessors.
- *   2. Every released task is scheduled at time t in ascending task id.
+ *   2. The released tasks join the back of a first-come first-served queue
+ *      in ascending task id; tasks are taken from its front and scheduled
+ *      at time t.  Under EFT-P and EIT-P every task is taken at once; under
+ *      F-P and R-P (which choose among idle processors only) the front task
+ *      waits while no processor is idle at t, and the tasks behind it wait
+ *      with it.
  *   3. If nothing is in flight, stop.  Otherwise t = the earliest finish
  *      time in flight; every task finishing at t completes, and the tasks
- *      whose predecessors have now all completed form the released set.
+ *      whose predecessors have now all completed are released.
  * Scheduling task j at time t:
  *   - for each memory m holding a processor, the data ready time DRT(j, m):
  *     every atom x of j's regions that is valid in m is usable from
@@ -747,13 +794,18 @@ static int by_crit_desc(const void *a, const void *b) {
  *   - EFT(p) = max(t, avail[p], DRT(j, mem(p))) + exec(op, type(p), bs);
  *     EFT-P (pl->select 0): p* = argmin EFT, ties to the lowest processor
  *     id; EIT-P (select 1): p* = argmin max(t, avail[p]), ties likewise;
+ *     F-P (select 2): among the processors idle at t (avail[p] <= t) the
+ *     one with the least exec time, ties likewise; R-P (select 3): among
+ *     the idle processors in id order, the one at a uniform draw from the
+ *     SplitMix64 stream (rp_seed, j); the task still waits for its data;
  *   - commit: start = EFT - exec, avail[p*] = EFT; the fetched atoms become
  *     valid in mem(p*) from their arrival; then the written atoms become
  *     valid only in mem(p*), from the finish time (write-back invalidation).
  *   - the makespan is the largest finish time. */
 int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *code, int64_t code_len,
                     int64_t cap_t, int32_t atom_level, int32_t dep_mode, int16_t *proc_out,
-                    int64_t *start_out, int64_t *finish_out, int32_t *order_out, or_stats *st) {
+                    int64_t *start_out, int64_t *finish_out, int32_t *order_out, int64_t *issue_out,
+                    or_stats *st) {
     if (!pl || pl->n_mem < 1 || pl->n_mem > OR_MAX_MEMS || pl->n_procs < 1 || pl->n_procs > OR_MAX_PROCS)
         return OR_ERR_ARG;
     if (pl->n_mem > 1 && pl->bw_bytes_per_ns < 1) return OR_ERR_ARG;
@@ -789,6 +841,7 @@ int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *c
     int32_t *inflight = (int32_t *)malloc(sizeof(int32_t) * (size_t)(T + 1)); /* tasks in flight */
     int32_t n_inflight = 0;
     int32_t *released = (int32_t *)malloc(sizeof(int32_t) * (size_t)(T + 1));
+    int32_t *fifo = (int32_t *)malloc(sizeof(int32_t) * (size_t)(T + 1)); /* FCFS queue */
     uint8_t *valid = (uint8_t *)calloc((size_t)(natoms * M), 1);
     int64_t *vfrom = (int64_t *)calloc((size_t)(natoms * M), sizeof(int64_t));
     int64_t maxatoms = 0;
@@ -804,7 +857,7 @@ int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *c
     or_stats s;
     memset(&s, 0, sizeof s);
     if (!succ_off || !succ || !fill || !pending || !finish || !state || !released || !valid || !vfrom || !ax ||
-        !axw || !src || !inflight) {
+        !axw || !src || !inflight || !fifo) {
         rc = OR_ERR_CAPACITY;
         goto out;
     }
@@ -844,7 +897,9 @@ int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *c
     S.start_out = start_out;
     S.finish_out = finish_out;
     S.order_out = order_out;
+    S.issue_out = issue_out;
     S.n_sched = 0;
+    const int waits = pl->select >= 2; /* F-P, R-P: idle processors only */
     int32_t n_done = 0;
     if (pl->order == 1) {
         /* PL: a static priority list (HEFT-like).  Critical time of a task =
@@ -852,7 +907,9 @@ int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *c
          * the same order) plus the largest critical time of its successors,
          * computed backwards (creation order is topological).  Tasks are
          * scheduled in decreasing critical time, ties to the lower id, each at
-         * its release time: the latest finish among its predecessors. */
+         * its release time: the latest finish among its predecessors.  Under
+         * F-P and R-P a task released while no processor is idle is scheduled
+         * when the first one becomes idle (the least avail). */
         int64_t *crit = (int64_t *)malloc(sizeof(int64_t) * (size_t)(T + 1));
         int64_t *rel = (int64_t *)calloc((size_t)T + 1, sizeof(int64_t));
         int32_t *list = (int32_t *)malloc(sizeof(int32_t) * (size_t)(T + 1));
@@ -873,7 +930,13 @@ int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *c
         qsort(list, (size_t)T, sizeof(int32_t), by_crit_desc);
         for (int32_t q = 0; q < T && !rc; q++) {
             int32_t j = list[q];
-            rc = schedule_task(&S, j, rel[j]);
+            int64_t t = rel[j];
+            if (waits && !any_idle(avail, P, t)) {
+                t = avail[0];
+                for (int p = 1; p < P; p++)
+                    if (avail[p] < t) t = avail[p];
+            }
+            rc = schedule_task(&S, j, t);
             if (rc) break;
             for (int64_t e = succ_off[j]; e < succ_off[j + 1]; e++)
                 if (S.finish_j > rel[succ[e]]) rel[succ[e]] = S.finish_j;
@@ -885,26 +948,30 @@ int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *c
         if (rc) goto out;
     } else {
         int32_t nrel = 0;
+        int32_t qh = 0, qt = 0; /* the queue: fifo[qh .. qt) */
         for (int32_t j = 0; j < T; j++)
             if (pending[j] == 0) released[nrel++] = j;
         int64_t t = 0;
         for (;;) {
-            /* schedule the released tasks in ascending id */
+            /* the released tasks join the queue in ascending id */
             for (int32_t a1 = 1; a1 < nrel; a1++) {
                 int32_t v = released[a1];
                 int32_t a2 = a1 - 1;
                 while (a2 >= 0 && released[a2] > v) { released[a2 + 1] = released[a2]; a2--; }
                 released[a2 + 1] = v;
             }
-            for (int32_t q = 0; q < nrel; q++) {
-                int32_t j = released[q];
+            for (int32_t q = 0; q < nrel; q++) fifo[qt++] = released[q];
+            nrel = 0;
+            /* schedule from the front of the queue */
+            while (qh < qt) {
+                if (waits && !any_idle(avail, P, t)) break;
+                int32_t j = fifo[qh++];
                 rc = schedule_task(&S, j, t);
                 if (rc) goto out;
                 finish[j] = S.finish_j;
                 state[j] = 1;
                 inflight[n_inflight++] = j;
             }
-            nrel = 0;
             /* next completion time */
             int64_t tn = -1;
             for (int32_t q = 0; q < n_inflight; q++)
@@ -944,6 +1011,7 @@ out:
     free(state);
     free(inflight);
     free(released);
+    free(fifo);
     free(valid);
     free(vfrom);
     free(ax);
@@ -956,7 +1024,7 @@ out:
  * level is the largest split level unless atom_level >= 0 is given. */
 int32_t or_simulate_levels(const or_platform *pl, int32_t n, int64_t b, const int8_t *levels, int32_t atom_level,
                            int32_t dep_mode, int16_t *proc_out, int64_t *start_out, int64_t *finish_out,
-                           int32_t *order_out, or_stats *st) {
+                           int32_t *order_out, int64_t *issue_out, or_stats *st) {
     if (n < 1) return OR_ERR_ARG;
     int64_t nb = or_base_count(n);
     int32_t lmax = 0;
@@ -981,7 +1049,7 @@ int32_t or_simulate_levels(const or_platform *pl, int32_t n, int64_t b, const in
     int64_t len = or_levels_to_code(n, levels, code, code_cap + 1);
     if (len < 0) { free(code); return (int32_t)len; }
     int32_t rc = or_simulate(pl, n, b, code, len, ntask, atom_level, dep_mode, proc_out, start_out, finish_out,
-                             order_out, st);
+                             order_out, issue_out, st);
     free(code);
     return rc;
 }
@@ -993,7 +1061,7 @@ int32_t or_simulate_many(const or_platform *pl, int32_t n, int64_t b, const int8
     int64_t nb = or_base_count(n);
     for (int64_t c = 0; c < n_cand; c++) {
         or_stats st;
-        int32_t rc = or_simulate_levels(pl, n, b, levels + c * nb, -1, 1, NULL, NULL, NULL, NULL, &st);
+        int32_t rc = or_simulate_levels(pl, n, b, levels + c * nb, -1, 1, NULL, NULL, NULL, NULL, NULL, &st);
         makespan[c] = rc ? -1 : st.makespan;
         status[c] = rc;
         if (tasks) tasks[c] = st.n_tasks;

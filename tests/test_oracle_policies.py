@@ -11,6 +11,25 @@ time, HEFT-like) and the earliest-idle-time processor choice (EIT-P), CPU only.
 * an independent replay of the oracle's own order and choices reproduces
   every start and finish for all four combinations;
 * a hand-derived EIT-P schedule with transfers available.
+
+F-P and R-P (the processor choice among the processors idle at the task's
+release time; a task waits while none is idle):
+
+* on identical processors sharing one memory, F-P equals EIT-P (the idle
+  processor with the lowest id is the one that became idle first) and, in
+  FCFS order, R-P gives the same start and finish times with other
+  processor ids;
+* R-P's choice on a chain (every processor idle) is the SplitMix64 draw of
+  the task id, computed here from the generator's published definition;
+* F-P on the cfg0 chain is the EFT-P worked example (the GPU is idle and
+  fastest every time); at a fork on one big and one LITTLE core F-P puts the
+  second task on the idle LITTLE core where EFT-P would queue it on big;
+* a definition check on shared-memory platforms: every task starts at or
+  after its release, waits only while every processor is busy, is served in
+  first-come first-served order (release time, then id), and takes the
+  fastest (F-P) or the drawn (R-P) processor among those idle for it;
+* with transfers: a replay at the oracle's issue times reproduces every
+  start and finish, and the chosen processor was idle at the issue time.
 """
 import dataclasses
 import json
@@ -118,3 +137,179 @@ def test_eit_hand_example_with_transfers_available():
     r = O.simulate(plat(spec, O.ORDER_FCFS, O.SELECT_EIT), 2, 1024, [0, 0, 0, 0])
     assert r["proc"].tolist() == [0, 0, 0, 0]
     assert r["makespan"] == 10400000 and r["n_transfers"] == 0
+
+
+# ---------------------------------------------------------------- F-P, R-P
+
+def rp_pick(seed, j, m):
+    """R-P's draw for task j among m idle processors: SplitMix64 counter
+    value u(seed, c = j, k = 0), then Lemire's multiply-shift into [0, m)."""
+    u = W.counter_u64(seed, np.array([j], np.uint64), np.array([0], np.uint64))
+    return int(W.draw(u, m)[0])
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 5])
+def test_fp_rp_on_identical_processors(P):
+    spec = identical(P)
+    rng = np.random.default_rng(40 + P)
+    for n in (2, 3, 4):
+        lv = rng.integers(0, 3, O.base_count(n)).astype(np.int8)
+        for order in (O.ORDER_FCFS, O.ORDER_PL):
+            e = O.simulate(plat(spec, order, O.SELECT_EIT), n, 1024, lv)
+            f = O.simulate(plat(spec, order, O.SELECT_FP), n, 1024, lv)
+            r = O.simulate(O.make_platform(spec, order=order, select=O.SELECT_RP, rp_seed=99), n, 1024, lv)
+            assert e["status"] == f["status"] == r["status"] == 0
+            for k in ("proc", "start", "finish"):
+                assert np.array_equal(e[k], f[k])
+            if order == O.ORDER_FCFS:
+                # time only moves forward, so every processor idle at t is as
+                # good as another; under PL a later task may be released
+                # earlier, and then which idle processor was taken matters
+                assert np.array_equal(e["start"], r["start"]) and np.array_equal(e["finish"], r["finish"])
+
+
+@pytest.mark.parametrize("P,seed", [(2, 0), (3, 7), (5, 123456789), (13, 2 ** 63 + 5)])
+def test_rp_draws_on_a_chain(P, seed):
+    for n, lv in ((2, [0, 0, 0, 0]), (1, [1]), (1, [2])):
+        for order in (O.ORDER_FCFS, O.ORDER_PL):
+            r = O.simulate(O.make_platform(identical(P), order=order, select=O.SELECT_RP, rp_seed=seed), n, 1024, lv)
+            assert r["status"] == 0
+            if n == 1 and lv == [2]:
+                continue  # not a chain (the level-1 trsm has parallel halves)
+            want = [rp_pick(seed, j, P) for j in range(r["n_tasks"])]
+            assert r["proc"].tolist() == want
+
+
+def test_fp_chain_is_the_eft_worked_example():
+    g = GOLD["n2_b1024_all_level0_cpu4_gpu1"]
+    for order in (O.ORDER_FCFS, O.ORDER_PL):
+        r = O.simulate(plat(W.PLATFORMS["cfg0"], order, O.SELECT_FP), 2, 1024, [0, 0, 0, 0])
+        assert r["proc"].tolist() == [4, 4, 4, 4]
+        assert r["finish"].tolist() == g["finish"] and r["makespan"] == g["makespan"]
+
+
+def test_fp_fork_takes_the_idle_slow_core():
+    """n = 3, base tasks chol(0), trsm(0,1), trsm(0,2), ... on one big (p0)
+    and one LITTLE (p1) core sharing memory: both trsm are released when the
+    chol ends; F-P gives the first to big and the second to the idle LITTLE
+    core, EFT-P queues the second on big (four times faster)."""
+    spec = W.PlatformSpec("big1_little1", 1, (W.BIG_TYPE, W.LITTLE_TYPE), ((0, 0), (0, 1)))
+    f = O.simulate(plat(spec, O.ORDER_FCFS, O.SELECT_FP), 3, 1024, [0] * 10)
+    e = O.simulate(plat(spec, O.ORDER_FCFS, O.SELECT_EFT), 3, 1024, [0] * 10)
+    c0 = int(f["finish"][0])
+    assert f["proc"][:3].tolist() == [0, 0, 1] and f["start"][1] == f["start"][2] == c0
+    assert e["proc"][:3].tolist() == [0, 0, 0] and e["start"][2] == e["finish"][1]
+    pl = O.make_platform(spec)
+    assert f["finish"][2] - c0 == O.exec_ns(pl, O.OP_TRSM, 1, 1024)
+
+
+def _dag(n, b, lv):
+    code = O.levels_to_code(n, lv)
+    d = O.expand(n, b, code)
+    po, pv, _ = O.deps(n, b, code, 1, int(max(lv)))
+    return d, po, pv
+
+
+def check_fcfs_idle_choice(spec, n, b, lv, r, select, seed):
+    """The FCFS rules for F-P / R-P on one shared memory, from their
+    definition: release r_j = latest predecessor finish; a task starts at or
+    after its release, waits only while every processor is busy, is served
+    in (release, id) order, and takes the fastest (F-P, ties to the lower
+    id) or the drawn (R-P) processor among those idle for it."""
+    pl = O.make_platform(spec)
+    d, po, pv = _dag(n, b, lv)
+    T = r["n_tasks"]
+    P = len(spec.procs)
+    proc, st, fi = r["proc"].astype(int), r["start"].astype(np.int64), r["finish"].astype(np.int64)
+    assert np.array_equal(r["issue"], st)  # one memory: no data to wait for
+    rel = np.array([max([fi[pv[e]] for e in range(po[j], po[j + 1])], default=0) for j in range(T)], np.int64)
+    fifo = sorted(range(T), key=lambda j: (rel[j], j))
+    rank = np.empty(T, np.int64)
+    rank[fifo] = np.arange(T)
+    on = [[k for k in range(T) if proc[k] == p] for p in range(P)]
+
+    def busy(p, tau):
+        return any(st[k] <= tau < fi[k] for k in on[p])
+
+    for j in range(T):
+        assert st[j] >= rel[j]
+        if st[j] > rel[j]:
+            instants = {int(rel[j])} | {int(f) for f in fi if rel[j] < f < st[j]}
+            for tau in instants:
+                assert all(busy(p, tau) for p in range(P)), (j, tau)
+        # idle for j at st[j]: nothing running there, and not taken at that
+        # instant by a task ahead of j in the queue
+        idle = [p for p in range(P)
+                if all(fi[k] <= st[j] or st[k] > st[j] or (st[k] == st[j] and rank[k] > rank[j])
+                       for k in on[p] if k != j)]
+        assert proc[j] in idle
+        if select == O.SELECT_FP:
+            ex = {p: O.exec_ns(pl, int(d["op"][j]), spec.procs[p][1], int(d["bs"][j])) for p in idle}
+            assert proc[j] == min(idle, key=lambda p: (ex[p], p))
+        else:
+            assert proc[j] == idle[rp_pick(seed, j, len(idle))]
+    # first-come first-served: a task queued earlier never starts later
+    for a, b_ in zip(fifo, fifo[1:]):
+        assert st[a] <= st[b_]
+
+
+@pytest.mark.parametrize("select", [2, 3])
+@pytest.mark.parametrize("spec_key,n", [("cfg1b", 3), ("cfg1b", 4), ("id3", 4), ("bl11", 3)])
+def test_fcfs_fp_rp_definition(select, spec_key, n):
+    spec = {"cfg1b": W.PLATFORMS["cfg1b"], "id3": identical(3),
+            "bl11": W.PlatformSpec("big1_little1", 1, (W.BIG_TYPE, W.LITTLE_TYPE), ((0, 0), (0, 1)))}[spec_key]
+    rng = np.random.default_rng(select * 100 + n)
+    for rep_ in range(3):
+        lv = rng.integers(0, 3, O.base_count(n)).astype(np.int8)
+        seed = 1000 + rep_
+        r = O.simulate(O.make_platform(spec, order=O.ORDER_FCFS, select=select, rp_seed=seed), n, 2048, lv)
+        assert r["status"] == 0
+        check_fcfs_idle_choice(spec, n, 2048, lv, r, select, seed)
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("select", [2, 3])
+@pytest.mark.parametrize("key,n,b", [("cfg0", 3, 1024), ("cfg1a", 3, 2048), ("cfg2", 2, 512), ("cfg2", 3, 1024)])
+def test_fp_rp_replay_with_transfers(order, select, key, n, b):
+    """Replay at the oracle's issue times reproduces every start and finish;
+    the chosen processor was idle at the issue time (its previous task
+    finished by then); under PL a task is issued at its release time when a
+    processor is idle then, else when the first one becomes idle; under
+    FCFS no task is issued before its release and the issue order follows
+    (release, id)."""
+    spec = W.PLATFORMS[key]
+    rng = np.random.default_rng(order * 10 + select + n)
+    for rep_ in range(3):
+        lv = rng.integers(0, 3, O.base_count(n)).astype(np.int8)
+        seed = 77 + rep_
+        pl = O.make_platform(spec, order=order, select=select, rp_seed=seed)
+        r = O.simulate(pl, n, b, lv)
+        assert r["status"] == 0
+        o = r["order"].tolist()
+        s_, f_ = replay(spec, n, b, lv, o, [int(r["proc"][j]) for j in o], issue=r["issue"])
+        assert [s_[j] for j in range(r["n_tasks"])] == r["start"].tolist()
+        assert [f_[j] for j in range(r["n_tasks"])] == r["finish"].tolist()
+        d, po, pv = _dag(n, b, lv)
+        fi = r["finish"]
+        avail = [0] * len(spec.procs)
+        rel_seen = []
+        for j in o:
+            rel = max([int(fi[pv[e]]) for e in range(po[j], po[j + 1])], default=0)
+            t = int(r["issue"][j])
+            p = int(r["proc"][j])
+            idle = [q for q in range(len(spec.procs)) if avail[q] <= t]
+            assert p in idle
+            if order == O.ORDER_PL:
+                assert t == (rel if any(a <= rel for a in avail) else min(avail))
+            else:
+                assert t >= rel
+                rel_seen.append((rel, j, t))
+            if select == O.SELECT_FP:
+                ex = {q: O.exec_ns(pl, int(d["op"][j]), spec.procs[q][1], int(d["bs"][j])) for q in idle}
+                assert p == min(idle, key=lambda q: (ex[q], q))
+            else:
+                assert p == idle[rp_pick(seed, j, len(idle))]
+            avail[p] = int(fi[j])
+        if order == O.ORDER_FCFS:
+            by_queue = sorted(rel_seen)
+            assert [x[2] for x in by_queue] == sorted(x[2] for x in by_queue)

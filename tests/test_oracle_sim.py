@@ -121,10 +121,11 @@ def test_worked_example_with_transfers(key, ncpu):
 # ----------------------------------------------- replay and brute force
 
 
-def replay(spec, n, b, levels, order, procs, atom_level=None):
+def replay(spec, n, b, levels, order, procs, atom_level=None, issue=None):
     """Evaluate a given (task order, assignment) with the write-back caching
     and transfer rules, each task issued at its release time (the latest
-    finish of its predecessors).  Independent of the oracle's event loop."""
+    finish of its predecessors), or at issue[j] when given.  Independent of
+    the oracle's event loop."""
     pl = O.make_platform(spec)
     code = O.levels_to_code(n, levels)
     d = O.expand(n, b, code)
@@ -144,6 +145,9 @@ def replay(spec, n, b, levels, order, procs, atom_level=None):
     fin = {}
     for j, p in zip(order, procs):
         t = max([fin[int(pv[e])] for e in range(po[j], po[j + 1])], default=0)
+        if issue is not None:
+            assert issue[j] >= t
+            t = int(issue[j])
         regs = [tuple(int(v) for v in d["regs"][j][r]) for r in range(int(d["nreg"][j]))]
         m = spec.procs[p][0]
         groups = {}
