@@ -100,21 +100,35 @@ int hesp_platform_create(const hesp_platform_desc *desc, hesp_platform **out);
 /* Override the time of (op, type, block) with `ns` (a measured model,
  * Sec. 2.1 / Sec. 3).  `block` must be a power of two <= 2^20, ns >= 1. */
 int hesp_platform_set_exec_table(hesp_platform *p, int32_t op, int32_t type, int64_t block, int64_t ns);
-/* Scheduling heuristics of Sec. 2.1 used when simulating on this platform:
- * order HESP_ORDER_FCFS (0, default): released tasks in ascending id at each
- * event time; HESP_ORDER_PL (1): a priority list (HEFT-like) -- critical time
- * of a task = its time summed over all processors (the mean times P) plus the
- * largest critical time among its successors; tasks are scheduled in
- * decreasing critical time (ties: lower id), each at its release time (the
- * latest finish among its predecessors).  select HESP_SELECT_EFT (0,
- * default): earliest finish time including transfers; HESP_SELECT_EIT (1):
- * the processor that becomes idle first, max(t, avail).  Ties to the lowest
- * processor id. */
+/* Scheduling heuristics of Sec. 2.1 used when simulating on this platform.
+ * Task order:
+ *   HESP_ORDER_FCFS (0, default): at each event time the released tasks join
+ *   a first-come first-served queue in ascending id and are scheduled from
+ *   its front;
+ *   HESP_ORDER_PL (1): a priority list (HEFT-like) -- critical time of a task
+ *   = its time summed over all processors (the mean times P) plus the largest
+ *   critical time among its successors; tasks are scheduled in decreasing
+ *   critical time (ties: lower id), each at its release time (the latest
+ *   finish among its predecessors).
+ * Processor choice (ties to the lowest processor id):
+ *   HESP_SELECT_EFT (0, default): earliest finish time including transfers;
+ *   HESP_SELECT_EIT (1): the processor that becomes idle first, max(t, avail);
+ *   HESP_SELECT_FP (2): the fastest for the task among the processors idle at
+ *   the scheduling time t (nothing running or queued on them after t);
+ *   HESP_SELECT_RP (3): among the processors idle at t, in id order, the one
+ *   at index ((u >> 32) * n_idle) >> 32, u = SplitMix64 output for counter
+ *   (c = task id, k = 0) under rp_seed (Steele et al. 2014, Lemire's draw).
+ *   Under F-P and R-P a task waits while no processor is idle: in FCFS order
+ *   the queue waits for the next completion; in PL order the task is
+ *   scheduled when the first processor becomes idle.
+ * rp_seed is used by R-P only.  ERR_ARG for an unknown order or choice. */
 #define HESP_ORDER_FCFS 0
 #define HESP_ORDER_PL 1
 #define HESP_SELECT_EFT 0
 #define HESP_SELECT_EIT 1
-int hesp_platform_set_policy(hesp_platform *p, int32_t order, int32_t select);
+#define HESP_SELECT_FP 2
+#define HESP_SELECT_RP 3
+int hesp_platform_set_policy(hesp_platform *p, int32_t order, int32_t select, uint64_t rp_seed);
 /* Host queries of the models, as used by the simulator. */
 int hesp_platform_exec_ns(const hesp_platform *p, int32_t op, int32_t type, int64_t block, int64_t *ns_out);
 int hesp_platform_xfer_ns(const hesp_platform *p, int64_t elems, int64_t *ns_out);

@@ -71,6 +71,7 @@ static DevPlatform dev_platform(const hesp_platform *p) {
     }
     d.order = p->order;
     d.select = p->select;
+    d.rp_seed = p->rp_seed;
     for (int op = 0; op < 4; ++op)
         for (int l = 0; l < HESP_LB; ++l) {
             int64_t s = 0;
@@ -185,10 +186,13 @@ int hesp_platform_set_exec_table(hesp_platform *p, int32_t op, int32_t type, int
     return HESP_OK;
 }
 
-int hesp_platform_set_policy(hesp_platform *p, int32_t order, int32_t select) {
-    if (!p || order < 0 || order > 1 || select < 0 || select > 1) return HESP_ERR_ARG;
+int hesp_platform_set_policy(hesp_platform *p, int32_t order, int32_t select, uint64_t rp_seed) {
+    if (!p || order < HESP_ORDER_FCFS || order > HESP_ORDER_PL || select < HESP_SELECT_EFT ||
+        select > HESP_SELECT_RP)
+        return HESP_ERR_ARG;
     p->order = order;
     p->select = select;
+    p->rp_seed = rp_seed;
     return HESP_OK;
 }
 

@@ -10,19 +10,7 @@
 namespace hesp {
 namespace {
 
-constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
-
-__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ uint64_t sm64_at(uint64_t seed, uint64_t c, uint64_t k) {
-    return sm64_mix(seed + ((c << 32) + k + 1) * kGamma);
-}
-
-__device__ __forceinline__ uint32_t draw(uint64_t u, uint32_t m) { return (uint32_t)(((u >> 32) * m) >> 32); }
+__device__ __forceinline__ uint32_t draw(uint64_t u, uint32_t m) { return lemire_draw(u, m); }
 
 // One block row of threads per candidate tile of the level array.
 __global__ void gen_fixed_kernel(int kind, uint64_t seed, int64_t first, int64_t n_cand, int nb, int n_levels,

@@ -20,8 +20,10 @@ struct hesp_platform {
     // launch shape chosen by hesp_sim_autotune or set by the caller (0 = default)
     int32_t tune_ctas_per_sm;
     int32_t tune_bitmap;  // 0 auto, 1 arena (global memory), 2 shared memory when it fits
-    // scheduling heuristics (Sec. 2.1): task order 0 FCFS / 1 PL, processor choice 0 EFT-P / 1 EIT-P
+    // scheduling heuristics (Sec. 2.1): task order 0 FCFS / 1 PL, processor
+    // choice 0 EFT-P / 1 EIT-P / 2 F-P / 3 R-P, and the seed of R-P's draws
     int32_t order, select;
+    uint64_t rp_seed;
 };
 
 struct hesp_dag {
@@ -32,11 +34,30 @@ struct hesp_dag {
 
 namespace hesp {
 
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) as a counter-based generator:
+// value k of stream c is the published output function applied to
+// seed + ((c << 32) + k + 1) * 0x9E3779B97F4A7C15; a draw in [0, m) is
+// Lemire's multiply-shift ((u >> 32) * m) >> 32.
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t sm64_at(uint64_t seed, uint64_t c, uint64_t k) {
+    return sm64_mix(seed + ((c << 32) + k + 1) * kGamma);
+}
+
+__device__ __forceinline__ uint32_t lemire_draw(uint64_t u, uint32_t m) { return (uint32_t)(((u >> 32) * m) >> 32); }
+
 // Platform image passed by value to the simulation kernel (constant bank),
 // copied to shared memory at kernel start.
 struct DevPlatform {
     int32_t n_mem, n_types, n_procs, pad;
-    int32_t order, select;  // task order (0 FCFS, 1 PL) and processor choice (0 EFT-P, 1 EIT-P)
+    int32_t order, select;  // task order (0 FCFS, 1 PL) and processor choice (0 EFT-P, 1 EIT-P, 2 F-P, 3 R-P)
+    uint64_t rp_seed;       // R-P: seed of the per-task draws
     int64_t exec[4 * HESP_MAX_TYPES * HESP_LB];
     int64_t wsum[4 * HESP_LB];  // task time summed over all processors, per (op, log2 block); -1 if any is -1
     int8_t proc_mem[HESP_MAX_PROCS];

@@ -212,13 +212,15 @@ __device__ __forceinline__ uint64_t warp_max_u64(uint64_t k) {
 // Per-processor FIFO of tasks in flight, threaded through the tasks.  For a
 // task in flight: its successor in the FIFO and that successor's finish time,
 // and the range of its own successor list, all read together when it
-// completes.
+// completes.  Record q also holds slot q of the FCFS wait queue of F-P / R-P
+// (every task joins that queue once).
 struct __align__(16) Link {
     int32_t next;
     int32_t e0, e1;  // successor list succ[e0 .. e1)
     int32_t pad;
     int64_t nfin;
-    int64_t pad2;
+    int32_t rq;  // wait-queue slot
+    int32_t pad2;
 };
 
 struct KArgs {
@@ -296,16 +298,17 @@ struct Counts {
     }
 };
 
-// Schedule task j at time t: data-ready time per memory, EFT over the
-// processors (ties to the lowest id), commit of the coherence state, append
-// to the chosen processor's FIFO.  Clears `ok` on an internal inconsistency.
+// Schedule task j at time t: data-ready time per memory, the processor
+// choice `sel` (ties to the lowest id), commit of the coherence state, append
+// to the chosen processor's FIFO.  Under F-P / R-P the caller guarantees a
+// processor idle at t.  Clears `ok` on an internal inconsistency.
 template <int M, int NS, bool FIFO>
 __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, const KArgs &a, int Lc, int lb_b,
                                                  int lane, const int64_t *s_exec, const int8_t *s_pmem,
                                                  const int8_t *s_ptype, const int pm[NS], const int pt[NS],
                                                  const bool pv[NS], int64_t avail[NS], int head[NS], int tail[NS],
                                                  int64_t hfin[NS], int64_t &mk, bool &ok, int64_t sched_base,
-                                                 bool eit) {
+                                                 int sel, uint64_t rp_seed) {
     const uint64_t d = at<uint64_t>(base, a.ar.off_desc)[j];
     const int32_t *const succoff = at<int32_t>(base, a.ar.off_succoff);
     const int se0 = succoff[j], se1 = succoff[j + 1];  // kept with the task while it is in flight
@@ -376,13 +379,31 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
         }
     }
     // Processor choice, key = value << 6 | proc (ties to the lowest id):
-    // EFT-P by the finish time, EIT-P by the time the processor is idle.
+    // EFT-P by the finish time, EIT-P by the time the processor is idle, F-P
+    // by the task time among the processors idle at t, R-P 0 for the idle
+    // processor whose rank in id order is the draw (1 for the others).
+    int rp_pick = -1;
+    unsigned ib[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) ib[s] = 0;
+    if (sel >= HESP_SELECT_FP) {
+        int n_idle = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            ib[s] = __ballot_sync(FULL, pv[s] && avail[s] <= t);
+            n_idle += __popc(ib[s]);
+        }
+        if (sel == HESP_SELECT_RP && n_idle > 0)
+            rp_pick = (int)lemire_draw(sm64_at(rp_seed, (uint64_t)j, 0), (uint32_t)n_idle);
+    }
     uint64_t key = ~0ull;
     int64_t emine[NS];
+    int before = 0;  // idle processors in lower slots
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         emine[s] = 0;
-        if (pv[s]) {
+        const bool cand = pv[s] && (sel < HESP_SELECT_FP || avail[s] <= t);
+        if (cand) {
             const int64_t ex = s_exec[(op * HESP_MAX_TYPES + pt[s]) * HESP_LB + lb];
             int64_t ready = max(t, avail[s]);
             const int64_t idle = ready;
@@ -396,13 +417,20 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
             const int64_t e = ready + ex;
             emine[s] = e;
             ok &= ex >= 0 && e < (1ll << 57);
-            key = min(key, ((uint64_t)(eit ? idle : e) << 6) | (uint64_t)(lane + 32 * s));
+            int64_t v = e;
+            if (sel == HESP_SELECT_EIT) v = idle;
+            else if (sel == HESP_SELECT_FP) v = ex;
+            else if (sel == HESP_SELECT_RP) v = (before + __popc(ib[s] & ((1u << lane) - 1u))) == rp_pick ? 0 : 1;
+            key = min(key, ((uint64_t)v << 6) | (uint64_t)(lane + 32 * s));
         }
+        if (sel >= HESP_SELECT_FP) before += __popc(ib[s]);
     }
     key = warp_min_u64(key);
-    const int pbest = (int)(key & 63);
+    const bool none = sel >= HESP_SELECT_FP && key == ~0ull;  // no idle processor: the caller's error
+    ok &= !none;
+    const int pbest = none ? 0 : (int)(key & 63);
     int64_t eft = (int64_t)(key >> 6);
-    if (eit) {
+    if (sel != HESP_SELECT_EFT) {
         int64_t mine = emine[0];
 #pragma unroll
         for (int s = 1; s < NS; ++s)
@@ -732,7 +760,9 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
             }
             // GEN = false: the FCFS + EFT-P instantiation; GEN = true: every
             // policy, chosen at run time from the platform.
-            const bool eit = GEN && pl.select == HESP_SELECT_EIT;
+            const int sel = GEN ? pl.select : HESP_SELECT_EFT;
+            const bool waits = GEN && sel >= HESP_SELECT_FP;  // F-P, R-P: idle processors only
+            const uint64_t rp_seed = pl.rp_seed;
             if (GEN && pl.order == HESP_ORDER_PL) {
                 // ---- PL: a priority list by critical time (HEFT-like); each task
                 // is scheduled at its release time, the latest finish among its
@@ -818,9 +848,22 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                 bool ok = true;
                 for (int64_t q = 0; q < T && okp; ++q) {
                     const int j = (int)(src[q] & ((1u << 22) - 1));
-                    const int64_t fj = schedule_task<M, NS, false>(j, rel[j], base, a, Lc, lb_b, lane, s_exec, s_pmem,
+                    int64_t tj = rel[j];
+                    if (waits) {
+                        // no processor idle at the release time: the first one to become idle
+                        bool any = false;
+                        uint64_t mn = ~0ull;
+#pragma unroll
+                        for (int s = 0; s < NS; ++s)
+                            if (pv[s]) {
+                                any |= avail[s] <= tj;
+                                mn = min(mn, (uint64_t)avail[s]);
+                            }
+                        if (!__any_sync(FULL, any)) tj = (int64_t)warp_min_u64(mn);
+                    }
+                    const int64_t fj = schedule_task<M, NS, false>(j, tj, base, a, Lc, lb_b, lane, s_exec, s_pmem,
                                                                    s_ptype, pm, pt, pv, avail, head, tail, hfin, mk,
-                                                                   ok, sched_base, eit);
+                                                                   ok, sched_base, sel, rp_seed);
                     const int e0 = succoff[j], e1 = succoff[j + 1];
                     for (int e = e0 + lane; e < e1; e += 32) {
                         const int sj = succ[e];
@@ -858,7 +901,8 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
             }
             const int64_t sched_base = a.sched_off ? a.sched_off[c] : -1;
             const int32_t *const succ = at<int32_t>(base, a.ar.off_succ);
-            const Link *const link = at<Link>(base, a.ar.off_link);
+            Link *const link = at<Link>(base, a.ar.off_link);
+            int qh = 0, qt = 0;  // F-P / R-P wait queue: link[qh .. qt).rq
             int64_t t = 0;
             int64_t iters = 0;
             const int64_t iter_cap = 4 * T + 64;
@@ -876,8 +920,13 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                         const int j = __reduce_min_sync(FULL, dj);
                         if (j == INT_MAX) break;
                         if (dj == j) dj = INT_MAX;
+                        if (waits) {
+                            if (lane == 0) link[qt].rq = j;
+                            ++qt;
+                            continue;
+                        }
                         schedule_task<M, NS, true>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
-                                                   avail, head, tail, hfin, mk, ok, sched_base, eit);
+                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed);
                         ++scheduled;
                     }
                     direct = false;
@@ -898,15 +947,35 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                             while (wb) {
                                 const int bit = __ffs(wb) - 1;
                                 wb &= wb - 1;
+                                if (waits) {
+                                    if (lane == 0) link[qt].rq = jb + bit;
+                                    ++qt;
+                                    continue;
+                                }
                                 schedule_task<M, NS, true>(jb + bit, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype,
                                                            pm, pt, pv, avail, head, tail, hfin, mk, ok, sched_base,
-                                                           eit);
+                                                           sel, rp_seed);
                                 ++scheduled;
                             }
                         }
                     }
                     wlo = INT_MAX;
                     whi = -1;
+                }
+                if (waits) {
+                    // serve the queue from its front while some processor is idle at t
+                    __syncwarp();
+                    while (qh < qt) {
+                        bool any = false;
+#pragma unroll
+                        for (int s = 0; s < NS; ++s) any |= pv[s] && avail[s] <= t;
+                        if (!__any_sync(FULL, any)) break;
+                        const int j = link[qh].rq;
+                        ++qh;
+                        schedule_task<M, NS, true>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
+                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed);
+                        ++scheduled;
+                    }
                 }
                 // next completion time
                 uint64_t nk = ~0ull;

@@ -49,15 +49,6 @@ struct hesp_surrogate {
 
 namespace {
 
-constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
-__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-__device__ __forceinline__ uint64_t sm64_at(uint64_t seed, uint64_t c, uint64_t k) {
-    return sm64_mix(seed + ((c << 32) + k + 1) * kGamma);
-}
 
 // He-uniform initialisation: w = (2 f - 1) * bound, f = (u >> 40) 2^-24.
 __global__ void init_uniform_kernel(float *w, int64_t rows, int64_t cols, int64_t cols_used, uint64_t seed,

@@ -38,7 +38,8 @@ EXPORTS = (
     "hesp_graph_launch", "hesp_graph_destroy", "hesp_platform_set_tuning", "hesp_platform_get_tuning",
     "hesp_sim_autotune", "hesp_sort_cands_workspace_size", "hesp_sort_cands_by_size", "hesp_platform_set_policy",
 )
-ORDER_FCFS, ORDER_PL, SELECT_EFT, SELECT_EIT = 0, 1, 0, 1
+ORDER_FCFS, ORDER_PL = 0, 1
+SELECT_EFT, SELECT_EIT, SELECT_FP, SELECT_RP = 0, 1, 2, 3
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 CAND_DTYPE = np.dtype([("n_tiles", "<i4"), ("b", "<i4"), ("level_offset", "<i8")])
@@ -128,7 +129,7 @@ def lib():
                                         ctypes.POINTER(i32), ctypes.POINTER(i32), vp, vp]
         L.hesp_sort_cands_workspace_size.argtypes = [i64, ctypes.POINTER(sz)]
         L.hesp_sort_cands_by_size.argtypes = [vp, vp, i64, vp, vp, vp, sz, vp]
-        L.hesp_platform_set_policy.argtypes = [vp, i32, i32]
+        L.hesp_platform_set_policy.argtypes = [vp, i32, i32, u64]
         L.hesp_best_makespan.argtypes = [vp, vp, vp, i64, vp, vp]
         L.hesp_gather_rows.argtypes = [vp, vp, i64, i64, vp, vp]
         L.hesp_generate_mutants.argtypes = [vp, i32, i32, i32, ctypes.c_double, u64, i64, i64, vp, vp]
@@ -158,7 +159,7 @@ class Platform:
     """A simulated platform (hesp_platform handle) built from a
     ``workloads.PlatformSpec``."""
 
-    def __init__(self, spec, order=0, select=0):
+    def __init__(self, spec, order=0, select=0, rp_seed=0):
         self.spec = spec
         L = lib()
         types = (_PType * len(spec.types))()
@@ -176,7 +177,7 @@ class Platform:
         self.h = h
         for (op, ty, bs, ns) in getattr(spec, "exec_overrides", ()):
             check(L.hesp_platform_set_exec_table(h, op, ty, bs, ns), "hesp_platform_set_exec_table")
-        check(L.hesp_platform_set_policy(h, order, select), "hesp_platform_set_policy")
+        check(L.hesp_platform_set_policy(h, order, select, rp_seed & ((1 << 64) - 1)), "hesp_platform_set_policy")
 
     @property
     def n_mem(self):

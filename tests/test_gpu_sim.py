@@ -261,10 +261,11 @@ def test_cfg4_full_size_candidates():
     check_parity(W.PLATFORMS["cfg4"], 32, 2048, lv, g, schedule=False)
 
 
-@pytest.mark.parametrize("order,select", [(0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("order,select", [(0, 1), (1, 0), (1, 1), (0, 2), (0, 3), (1, 2), (1, 3)])
 def test_policies_parity(order, select):
-    """PL task order and EIT-P processor choice (Sec. 2.1) against the oracle:
-    schedules bit-exact on every workload shape."""
+    """PL task order and the EIT-P, F-P and R-P processor choices (Sec. 2.1)
+    against the oracle: schedules bit-exact on every workload shape."""
+    seed = 0x8000000000000000 + 12345 * (order + 1)
     cases = [("cfg0", 3, 1024, W.workload_levels("cfg0")[::8], 1),
              ("cfg1a", 8, 2048, W.workload_levels("cfg1", 300, 48), 2),
              ("cfg1b", 8, 2048, W.workload_levels("cfg1", 900, 48), 2),
@@ -272,7 +273,7 @@ def test_policies_parity(order, select):
              ("cfg4", 5, 2048, np.random.default_rng(2).integers(0, 4, (16, W.base_count(5))).astype(np.int8), 3)]
     for key, n, b, lv, L in cases:
         spec = W.PLATFORMS[key]
-        plat = hesp.Platform(spec, order=order, select=select)
+        plat = hesp.Platform(spec, order=order, select=select, rp_seed=seed)
         C, nb = lv.shape
         d_lv = torch.from_numpy(np.ascontiguousarray(lv).reshape(-1).copy()).cuda()
         cands = hesp.cands_tensor(n, b, np.arange(C, dtype=np.int64) * nb)
@@ -288,7 +289,7 @@ def test_policies_parity(order, select):
         torch.cuda.synchronize()
         ms, st = ms.cpu().numpy(), st.cpu().numpy()
         proc, start, fin = (x.cpu().numpy() for x in sched[1:])
-        pl = O.make_platform(spec, order=order, select=select)
+        pl = O.make_platform(spec, order=order, select=select, rp_seed=seed)
         for c in range(C):
             r = O.simulate(pl, n, b, lv[c])
             assert st[c] == 0 and ms[c] == r["makespan"], (key, c)
