@@ -275,8 +275,8 @@ def run_gpu(args):
 # for the kernel source they were taken on: DRAM bytes per 4,096 candidates on the
 # CPU+GPU platform (scaled to a launch by candidates; traffic grows in proportion)
 # and the share of issue slots busy.
-SIM_NCU = {"source_sha1_12": "3a7171750211", "dram_bytes_per_4096": 1.356322e9 + 1.196373e9,
-           "issue_active_pct": 59.77, "warps_per_sm": 23.5, "alu_pipe_pct": 47.3}
+SIM_NCU = {"source_sha1_12": "73c4d49cbdce", "dram_bytes_per_4096": 1.358183e9 + 1.197208e9,
+           "issue_active_pct": 59.14, "warps_per_sm": 23.5, "alu_pipe_pct": 47.4}
 
 
 def sim_source_matches():
@@ -586,7 +586,7 @@ def main():
     ap.add_argument("--impl", default="hesp", choices=["hesp", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--cpu-sample", type=int, default=16384)
+    ap.add_argument("--cpu-sample", type=int, default=65536)
     ap.add_argument("--ref-sample", type=int, default=256)
     ap.add_argument("--candidates", type=int, default=N_CAND,
                     help="candidates per step (default: the workload's 65,536; smaller only for profiling)")
