@@ -12,7 +12,9 @@ The C file ``hesp_oracle.c`` is the oracle proper (plain, single-threaded, in
 the order the paper describes the method: Fig. 1 base loop, Sec. 2.1
 partitioners, dependences, performance / transfer models, FCFS + EFT-P with
 write-back caching).  This module compiles it with gcc and wraps it with
-ctypes and numpy.  ``mlp_ref`` holds the FP64 reference of the surrogate MLP.
+ctypes and numpy.  ``mlp_ref`` holds the FP64 reference of the surrogate MLP;
+``solver`` the iterative partition solver (Sec. 2.1 "Iterative solver") over
+this simulation.
 
 Every simulator function here is pinned by the tests in
 ``tests/test_oracle_*.py`` (closed forms, numerical execution of the DAG,
