@@ -175,10 +175,11 @@ typedef struct {
 int hesp_sim_workspace_size(const hesp_platform *p, int32_t max_tiles, int32_t max_level, int64_t task_cap,
                             int64_t n_cand, size_t *bytes_out);
 
-/* Simulate n_cand candidates (HeSP Sec. 2.1: FCFS task order at release time,
- * EFT-P processor selection, write-back caching with prefetching transfers).
+/* Simulate n_cand candidates (HeSP Sec. 2.1: the platform's task order and
+ * processor selection, hesp_platform_set_policy -- by default FCFS at release
+ * time and EFT-P -- with write-back caching and prefetching transfers).
  * For each candidate: expand its DAG, derive RaW/WaW/WaR dependences from the
- * overlap of the tasks' data blocks, then run the event loop:
+ * overlap of the tasks' data blocks, then run the event loop (FCFS):
  *   t = 0; released = tasks without predecessors; repeat: schedule every
  *   released task in ascending id at time t; t = earliest finish in flight;
  *   complete every task finishing at t; released = tasks whose predecessors
@@ -211,6 +212,65 @@ int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands_dev, cons
                         int64_t *makespan_dev, int32_t *status_dev, int64_t *ntasks_dev, const int64_t *sched_offsets_dev,
                         int16_t *proc_dev, int64_t *start_dev, int64_t *finish_dev, void *workspace_dev,
                         size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------ iterative partition solver
+ * HeSP's iterative solver (Sec. 2.1 "Iterative solver"): each iteration is a
+ * schedule stage (simulate the partition) and a partition stage (list
+ * candidate moves, score them, pick one).  A partition is one split level per
+ * base task; move k = 2 t + d changes base task t by +1 (d = 0, partition) or
+ * -1 (d = 1, merge back).  Candidate moves, in increasing k: a partition move
+ * for each base task chosen by the selection policy and below the deepest
+ * level, and a merge move for every split base task (an existing task
+ * cluster).  Selection: HESP_SOLVER_ALL every base task; HESP_SOLVER_CP the
+ * base tasks flagged by hesp_simulate_critical; HESP_SOLVER_SHALLOW the base
+ * tasks at the minimal level (depth).  A move's score is the current
+ * makespan minus its simulated makespan (the paper estimates it; here the
+ * whole neighbourhood is simulated in one hesp_simulate_batch call); moves
+ * with a score <= 0 or a failed simulation are dropped.  Sampling:
+ * HESP_PICK_HARD the largest score, ties to the lower index; HESP_PICK_SOFT
+ * r = floor(u * S / 2^64) with S the sum of the kept scores and u the
+ * SplitMix64 output for counter (c = iteration, k = 0) under `seed`, then the
+ * first kept move whose running score sum exceeds r (probability score / S). */
+#define HESP_SOLVER_ALL 0
+#define HESP_SOLVER_CP 1
+#define HESP_SOLVER_SHALLOW 2
+#define HESP_PICK_HARD 0
+#define HESP_PICK_SOFT 1
+
+/* hesp_simulate_batch (no schedule output) that also flags, per base task,
+ * whether one of its tasks lies on the critical path of the candidate's
+ * schedule: the longest path of the DAG weighted by the scheduled task
+ * times; a task is on it when the longest path through it is as long as the
+ * longest path overall.  crit_dev (int8, device) is laid out like the levels:
+ * crit_dev[level_offset + t] = 1 or 0 for base task t.  Always runs the
+ * general-policy kernel.  Errors as hesp_simulate_batch. */
+int hesp_simulate_critical(const hesp_platform *p, const hesp_cand *cands_dev, const int8_t *levels_dev,
+                           int64_t n_cand, int32_t max_tiles, int32_t max_level, int64_t task_cap,
+                           int64_t *makespan_dev, int32_t *status_dev, int8_t *crit_dev, void *workspace_dev,
+                           size_t workspace_bytes, void *stream);
+
+/* Partition stage, step (1): the candidate moves of the partition levels_dev
+ * (int8[n_base], device, levels 0 .. n_levels - 1).  Writes the move codes in
+ * increasing k to moves_dev (int32, capacity 2 n_base), their number to
+ * *count_dev (int64, device), and, when rows_dev is not NULL, the moved
+ * partitions to rows_dev (int8, row r = levels with move r applied, capacity
+ * 2 n_base x n_base; rows past the count are left untouched).  crit_dev
+ * (int8[n_base]) is read for HESP_SOLVER_CP only.  ERR_ARG on a bad argument,
+ * ERR_UNSUPPORTED for n_base > 32767.  Asynchronous on `stream`. */
+int hesp_solver_moves(const int8_t *levels_dev, int32_t n_base, int32_t n_levels, int32_t mode,
+                      const int8_t *crit_dev, int32_t *moves_dev, int64_t *count_dev, int8_t *rows_dev, void *stream);
+
+/* Partition stage, step (2): score the *count_dev moves from their simulated
+ * makespan_dev / status_dev (index r = row r of hesp_solver_moves) against
+ * *cur_makespan_dev, pick one (pick = HESP_PICK_HARD / HESP_PICK_SOFT; seed
+ * and iteration drive Soft's draw), and apply it: levels_dev (the current
+ * partition) and *cur_makespan_dev are updated in place and *chosen_dev is
+ * the move code, or -1 when no move has a positive score (a local optimum;
+ * nothing changes), or -2 when the score sum is 2^64 or more (nothing
+ * changes).  All device pointers; asynchronous on `stream`. */
+int hesp_solver_pick(const int64_t *makespan_dev, const int32_t *status_dev, const int32_t *moves_dev,
+                     const int64_t *count_dev, int32_t pick, uint64_t seed, int64_t iteration,
+                     int64_t *cur_makespan_dev, int8_t *levels_dev, int64_t *chosen_dev, void *stream);
 
 /* Allocation-free variant of hesp_simulate_batch.  The paper has no
  * counterpart: it exists for callers that cannot allocate device memory when

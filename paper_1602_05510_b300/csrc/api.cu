@@ -326,11 +326,12 @@ int hesp_sim_workspace_size(const hesp_platform *p, int32_t max_tiles, int32_t m
     return HESP_OK;
 }
 
-int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands, const int8_t *levels, int64_t n_cand,
-                        int32_t max_tiles, int32_t max_level, int64_t task_cap, int64_t *makespan, int32_t *status,
-                        int64_t *ntasks,
-                        const int64_t *sched_off, int16_t *sproc, int64_t *sstart, int64_t *sfinish, void *ws,
-                        size_t ws_bytes, void *stream) {
+namespace {
+
+int simulate_common(const hesp_platform *p, const hesp_cand *cands, const int8_t *levels, int64_t n_cand,
+                    int32_t max_tiles, int32_t max_level, int64_t task_cap, int64_t *makespan, int32_t *status,
+                    int64_t *ntasks, const int64_t *sched_off, int16_t *sproc, int64_t *sstart, int64_t *sfinish,
+                    int8_t *crit, void *ws, size_t ws_bytes, void *stream) {
     if (!p || n_cand < 0 || task_cap < 0) return HESP_ERR_ARG;
     if (n_cand == 0) return HESP_OK;
     if (!cands || !levels || !makespan || !status || !ws) return HESP_ERR_ARG;
@@ -350,7 +351,26 @@ int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands, const in
     if (slots > n_cand) slots = n_cand;
     const DevPlatform dp = dev_platform(p);
     return launch_sim(p, dp, ar, slots, cands, levels, n_cand, max_tiles, max_level, makespan, status, ntasks,
-                      sched_off, sproc, sstart, sfinish, (char *)ws, (cudaStream_t)stream);
+                      sched_off, sproc, sstart, sfinish, crit, (char *)ws, (cudaStream_t)stream);
+}
+
+}  // namespace
+
+int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands, const int8_t *levels, int64_t n_cand,
+                        int32_t max_tiles, int32_t max_level, int64_t task_cap, int64_t *makespan, int32_t *status,
+                        int64_t *ntasks,
+                        const int64_t *sched_off, int16_t *sproc, int64_t *sstart, int64_t *sfinish, void *ws,
+                        size_t ws_bytes, void *stream) {
+    return simulate_common(p, cands, levels, n_cand, max_tiles, max_level, task_cap, makespan, status, ntasks,
+                           sched_off, sproc, sstart, sfinish, nullptr, ws, ws_bytes, stream);
+}
+
+int hesp_simulate_critical(const hesp_platform *p, const hesp_cand *cands, const int8_t *levels, int64_t n_cand,
+                           int32_t max_tiles, int32_t max_level, int64_t task_cap, int64_t *makespan,
+                           int32_t *status, int8_t *crit, void *ws, size_t ws_bytes, void *stream) {
+    if (n_cand > 0 && !crit) return HESP_ERR_ARG;
+    return simulate_common(p, cands, levels, n_cand, max_tiles, max_level, task_cap, makespan, status, nullptr,
+                           nullptr, nullptr, nullptr, nullptr, crit, ws, ws_bytes, stream);
 }
 
 int hesp_generate_candidates(int32_t kind, uint64_t seed, int64_t first, int64_t n_cand, int32_t n_tiles, int32_t b,

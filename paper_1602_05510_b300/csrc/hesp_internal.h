@@ -97,7 +97,7 @@ int sim_slots_for(const hesp_platform *p, const Arena &ar, int64_t *resident_war
 int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, int64_t n_slots,
                const hesp_cand *cands, const int8_t *levels, int64_t n_cand, int32_t max_tiles, int32_t max_level,
                int64_t *makespan, int32_t *status, int64_t *ntasks, const int64_t *sched_off, int16_t *sproc,
-               int64_t *sstart, int64_t *sfinish, char *ws, cudaStream_t stream);
+               int64_t *sstart, int64_t *sfinish, int8_t *crit, char *ws, cudaStream_t stream);
 int sim_kernel_occupancy(int n_mem, int n_procs, int64_t Tcap, int *blocks_per_sm, int *threads_per_block);
 int sim_bitmap_smem_words(int64_t Tcap);
 

@@ -235,6 +235,7 @@ struct KArgs {
     int16_t *sproc;
     int64_t *sstart, *sfinish;
     char *ws;
+    int8_t *crit;  // optional: per base task, 1 if one of its tasks is on the critical path
     Arena ar;
     int64_t n_slots;
     int32_t bm_smem_words;  // > 0: the released-task bitmap lives in shared memory
@@ -302,7 +303,7 @@ struct Counts {
 // choice `sel` (ties to the lowest id), commit of the coherence state, append
 // to the chosen processor's FIFO.  Under F-P / R-P the caller guarantees a
 // processor idle at t.  Clears `ok` on an internal inconsistency.
-template <int M, int NS, bool FIFO>
+template <int M, int NS, bool FIFO, bool REC>
 __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, const KArgs &a, int Lc, int lb_b,
                                                  int lane, const int64_t *s_exec, const int8_t *s_pmem,
                                                  const int8_t *s_ptype, const int pm[NS], const int pt[NS],
@@ -504,6 +505,9 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
             }
         }
     }
+    // REC: keep the chosen processor in the task's (spent) pending count for
+    // the critical-path pass; a scheduled task's count is never read again
+    if (REC && lane == 0) at<uint16_t>(base, a.ar.off_pending)[j] = (uint16_t)pbest;
     if (lane == 0 && sched_base >= 0) {
         a.sproc[sched_base + j] = (int16_t)pbest;
         a.sstart[sched_base + j] = eft - s_exec[(op * HESP_MAX_TYPES + s_ptype[pbest]) * HESP_LB + lb];
@@ -861,7 +865,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                             }
                         if (!__any_sync(FULL, any)) tj = (int64_t)warp_min_u64(mn);
                     }
-                    const int64_t fj = schedule_task<M, NS, false>(j, tj, base, a, Lc, lb_b, lane, s_exec, s_pmem,
+                    const int64_t fj = schedule_task<M, NS, false, GEN>(j, tj, base, a, Lc, lb_b, lane, s_exec, s_pmem,
                                                                    s_ptype, pm, pt, pv, avail, head, tail, hfin, mk,
                                                                    ok, sched_base, sel, rp_seed);
                     const int e0 = succoff[j], e1 = succoff[j + 1];
@@ -925,7 +929,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                             ++qt;
                             continue;
                         }
-                        schedule_task<M, NS, true>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
+                        schedule_task<M, NS, true, GEN>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
                                                    avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed);
                         ++scheduled;
                     }
@@ -952,7 +956,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                                     ++qt;
                                     continue;
                                 }
-                                schedule_task<M, NS, true>(jb + bit, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype,
+                                schedule_task<M, NS, true, GEN>(jb + bit, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype,
                                                            pm, pt, pv, avail, head, tail, hfin, mk, ok, sched_base,
                                                            sel, rp_seed);
                                 ++scheduled;
@@ -972,7 +976,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                         if (!__any_sync(FULL, any)) break;
                         const int j = link[qh].rq;
                         ++qh;
-                        schedule_task<M, NS, true>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
+                        schedule_task<M, NS, true, GEN>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
                                                    avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed);
                         ++scheduled;
                     }
@@ -1048,6 +1052,64 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
             }
         }
 
+        // ---- 5. critical-path flags per base task: a task is critical when the
+        // longest path through it, weighted by the scheduled task times, is as
+        // long as the longest path of the DAG (the iterative solver's CP choice)
+        if (GEN && a.crit && status == HESP_OK) {
+            const uint16_t *const prc = at<uint16_t>(base, a.ar.off_pending);
+            const int32_t *const succoff = at<int32_t>(base, a.ar.off_succoff);
+            const int32_t *const succ = at<int32_t>(base, a.ar.off_succ);
+            int64_t *const down = at<int64_t>(base, a.ar.off_link);  // the link area is free now
+            int64_t *const up = down + T;
+            auto dur = [&](int64_t j) -> int64_t {
+                const uint64_t d = desc[j];
+                return s_exec[((int)(d & 3) * HESP_MAX_TYPES + s_ptype[prc[j]]) * HESP_LB + lb_b -
+                              (int)((d >> 2) & 7)];
+            };
+            // longest path from each task to a sink (creation order is topological)
+            for (int64_t j = T - 1; j >= 0; --j) {
+                uint64_t mx = 0;
+                for (int e = succoff[j] + lane; e < succoff[j + 1]; e += 32) mx = max(mx, (uint64_t)down[succ[e]]);
+                mx = warp_max_u64(mx);
+                if (lane == 0) down[j] = dur(j) + (int64_t)mx;
+                __syncwarp();
+            }
+            // longest path from a source to each task, pushed along the successor lists
+            for (int64_t j = lane; j < T; j += 32) up[j] = dur(j);
+            __syncwarp();
+            uint64_t lmax = 0;
+            for (int64_t j = 0; j < T; ++j) {
+                const int64_t uj = up[j];
+                for (int e = succoff[j] + lane; e < succoff[j + 1]; e += 32) {
+                    const int s = succ[e];
+                    up[s] = max(up[s], uj + dur(s));
+                }
+                __syncwarp();
+            }
+            for (int64_t j = lane; j < T; j += 32) lmax = max(lmax, (uint64_t)down[j]);
+            const int64_t longest = (int64_t)warp_max_u64(lmax);
+            // base tasks own consecutive task ranges in creation order
+            int64_t run = 0;
+            for (int64_t t0 = 0; t0 < nb; t0 += 32) {
+                const int64_t t = t0 + lane;
+                int cnt = 0;
+                if (t < nb) {
+                    int op, K, I, J;
+                    decode_base(n, t, op, K, I, J);
+                    cnt = c_cnt[op][a.levels[loff + t]];
+                }
+                const int incl = warp_incl_scan(cnt, lane);
+                if (t < nb) {
+                    int8_t f = 0;
+                    for (int64_t j = run + incl - cnt; j < run + incl && !f; ++j)
+                        f = (up[j] + down[j] - dur(j) == longest) ? 1 : 0;
+                    a.crit[loff + t] = f;
+                }
+                run += __shfl_sync(FULL, incl, 31);
+            }
+            __syncwarp();
+        }
+
         if (lane == 0) {
             a.status[c] = status;
             a.makespan[c] = status == HESP_OK ? mk : -1;
@@ -1107,7 +1169,7 @@ int sim_kernel_occupancy(int n_mem, int n_procs, int64_t Tcap, int *blocks_per_s
 int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, int64_t n_slots,
                const hesp_cand *cands, const int8_t *levels, int64_t n_cand, int32_t max_tiles, int32_t max_level,
                int64_t *makespan, int32_t *status, int64_t *ntasks, const int64_t *sched_off, int16_t *sproc,
-               int64_t *sstart, int64_t *sfinish, char *ws, cudaStream_t stream) {
+               int64_t *sstart, int64_t *sfinish, int8_t *crit, char *ws, cudaStream_t stream) {
     KArgs a;
     a.cands = cands;
     a.levels = levels;
@@ -1121,6 +1183,7 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
     a.sproc = sproc;
     a.sstart = sstart;
     a.sfinish = sfinish;
+    a.crit = crit;
     a.ar = ar;
     a.n_slots = n_slots;
     a.ws = ws + kWsHeaderBytes;
@@ -1132,7 +1195,7 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
     const int64_t blocks = (n_slots * 32 + threads - 1) / threads;
     const bool two = p->n_procs > 32;
     const unsigned ub = (unsigned)blocks;
-    const bool gen = p->order != HESP_ORDER_FCFS || p->select != HESP_SELECT_EFT;
+    const bool gen = p->order != HESP_ORDER_FCFS || p->select != HESP_SELECT_EFT || crit != nullptr;
     switch (p->n_mem) {
     case 1: two ? launch_one<1, 2>(gen, ub, threads, smem, stream, dp, a, ctr)
                 : launch_one<1, 1>(gen, ub, threads, smem, stream, dp, a, ctr); break;

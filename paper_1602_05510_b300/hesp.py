@@ -37,7 +37,10 @@ EXPORTS = (
     "hesp_generate_mutants", "hesp_gather_rows", "hesp_best_makespan", "hesp_graph_begin", "hesp_graph_end",
     "hesp_graph_launch", "hesp_graph_destroy", "hesp_platform_set_tuning", "hesp_platform_get_tuning",
     "hesp_sim_autotune", "hesp_sort_cands_workspace_size", "hesp_sort_cands_by_size", "hesp_platform_set_policy",
+    "hesp_simulate_critical", "hesp_solver_moves", "hesp_solver_pick",
 )
+SOLVER_ALL, SOLVER_CP, SOLVER_SHALLOW = 0, 1, 2
+PICK_HARD, PICK_SOFT = 0, 1
 ORDER_FCFS, ORDER_PL = 0, 1
 SELECT_EFT, SELECT_EIT, SELECT_FP, SELECT_RP = 0, 1, 2, 3
 NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -95,6 +98,9 @@ def lib():
         L.hesp_sim_workspace_size.argtypes = [vp, i32, i32, i64, i64, ctypes.POINTER(sz)]
         L.hesp_simulate_batch.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         L.hesp_simulate_batch_noalloc.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.hesp_simulate_critical.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, sz, vp]
+        L.hesp_solver_moves.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp]
+        L.hesp_solver_pick.argtypes = [vp, vp, vp, vp, i32, u64, i64, vp, vp, vp, vp]
         L.hesp_gemm_bf16.argtypes = [i32, i32, i32, vp, i64, vp, i64, i32, vp, i64, vp, vp, i64, vp, i64, vp, i64,
                                      vp, vp]
         f32, f64 = ctypes.c_float, ctypes.c_double
@@ -300,6 +306,35 @@ def simulate_batch_noalloc(platform: Platform, cands, levels, n_cand, max_tiles,
                                             _ptr(ss), _ptr(sf), _stream(stream)),
           "hesp_simulate_batch_noalloc")
     return makespan, status, ntasks
+
+
+def simulate_critical(platform: Platform, cands, levels, n_cand, max_tiles, max_level, workspace, crit,
+                      makespan=None, status=None, stream=None, task_cap=0):
+    """hesp_simulate_critical: makespans plus, per base task, a critical-path
+    flag written to `crit` (int8, laid out like `levels`)."""
+    import torch
+    dev = levels.device
+    if makespan is None:
+        makespan = torch.empty(n_cand, dtype=torch.int64, device=dev)
+    if status is None:
+        status = torch.empty(n_cand, dtype=torch.int32, device=dev)
+    check(lib().hesp_simulate_critical(platform.h, _ptr(cands), _ptr(levels), n_cand, max_tiles, max_level, task_cap,
+                                       _ptr(makespan), _ptr(status), _ptr(crit), _ptr(workspace), workspace.numel(),
+                                       _stream(stream)), "hesp_simulate_critical")
+    return makespan, status
+
+
+def solver_moves(levels, n_base, n_levels, mode, crit, moves, count, rows=None, stream=None):
+    """hesp_solver_moves: candidate moves of the partition `levels`."""
+    check(lib().hesp_solver_moves(_ptr(levels), n_base, n_levels, mode, _ptr(crit), _ptr(moves), _ptr(count),
+                                  _ptr(rows), _stream(stream)), "hesp_solver_moves")
+
+
+def solver_pick(makespan, status, moves, count, pick, seed, iteration, cur_makespan, levels, chosen, stream=None):
+    """hesp_solver_pick: score, pick and apply one move (in place)."""
+    check(lib().hesp_solver_pick(_ptr(makespan), _ptr(status), _ptr(moves), _ptr(count), pick,
+                                 seed & ((1 << 64) - 1), iteration, _ptr(cur_makespan), _ptr(levels), _ptr(chosen),
+                                 _stream(stream)), "hesp_solver_pick")
 
 
 def generate_candidates(kind, seed, first, n_cand, n_tiles, b, n_levels, levels, cands=None, stream=None):

@@ -204,3 +204,136 @@ def surrogate_search(spec, n_tiles, b, n_levels, seed, budget_s, per_launch=4096
             sur.train(lab_lv, lab_ms, n_lab, cfg.batch, cfg.steps_per_round, cfg.lr, seed=seed + 100 + rnd)
         rnd += 1
     return log
+
+
+@dataclass
+class SolverStep:
+    levels: np.ndarray        # partition at the start of the iteration
+    makespan: int
+    moves: List[int]          # candidate move codes (2 t + d)
+    makespans: List[int]      # simulated makespan of each moved partition
+    chosen: Optional[int]     # applied move code, None at a local optimum
+
+
+class IterativeSolver:
+    """HeSP's iterative partition solver (Sec. 2.1 "Iterative solver") on one
+    GPU.  Each iteration: the schedule stage simulates the current partition
+    (with critical-path flags), the partition stage lists the candidate moves
+    (selection All / CP / Shallow), simulates every moved partition in one
+    batched launch, and applies the best (Hard) or a score-proportional draw
+    (Soft).  Per iteration the host reads back two numbers (the move count
+    and the chosen move)."""
+
+    def __init__(self, spec, n_tiles, b, n_levels, mode, pick, task_cap=0, ws_bytes=None, order=0, select=0,
+                 rp_seed=0):
+        import torch
+        self.plat = hesp.Platform(spec, order=order, select=select, rp_seed=rp_seed)
+        self.n, self.b, self.NL, self.mode, self.pick, self.task_cap = n_tiles, b, n_levels, mode, pick, task_cap
+        nb = self.nb = W.base_count(n_tiles)
+        self.max_moves = 2 * nb
+        self.ws = hesp.alloc_workspace(self.plat, n_tiles, n_levels - 1, self.max_moves, task_cap, max_bytes=ws_bytes)
+        dev = "cuda"
+        self.cur = torch.zeros(nb, dtype=torch.int8, device=dev)
+        self.rows = torch.empty(self.max_moves * nb, dtype=torch.int8, device=dev)
+        self.moves = torch.empty(self.max_moves, dtype=torch.int32, device=dev)
+        self.count = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.crit = torch.zeros(nb, dtype=torch.int8, device=dev)
+        self.cur_ms = torch.empty(1, dtype=torch.int64, device=dev)
+        self.cur_st = torch.empty(1, dtype=torch.int32, device=dev)
+        self.ms = torch.empty(self.max_moves, dtype=torch.int64, device=dev)
+        self.st = torch.empty(self.max_moves, dtype=torch.int32, device=dev)
+        self.nt = torch.empty(self.max_moves, dtype=torch.int64, device=dev)
+        self.chosen = torch.empty(1, dtype=torch.int64, device=dev)
+        self.cands_rows = hesp.cands_tensor(n_tiles, b, np.arange(self.max_moves, dtype=np.int64) * nb)
+        self.cand_cur = hesp.cands_tensor(n_tiles, b, np.zeros(1, np.int64))
+
+    def start(self, levels=None, seed=0, draw=0):
+        """Set the current partition: `levels` (host), or the uniform draw
+        `draw` of the SplitMix64 stream `seed`."""
+        import torch
+        if levels is not None:
+            self.cur.copy_(torch.from_numpy(np.ascontiguousarray(levels, np.int8)))
+        else:
+            hesp.generate_candidates(hesp.GEN_UNIFORM, seed, draw, 1, self.n, self.b, self.NL, self.cur)
+
+    def schedule_stage(self):
+        hesp.simulate_critical(self.plat, self.cand_cur, self.cur, 1, self.n, self.NL - 1, self.ws, self.crit,
+                               makespan=self.cur_ms, status=self.cur_st, task_cap=self.task_cap)
+
+    def iterate(self, seed, iteration, trace=False):
+        """One iteration from the current partition.  Returns (chosen move or
+        None, moves simulated, task-events simulated, SolverStep if trace)."""
+        import torch
+        if trace:
+            lv0 = self.cur.cpu().numpy().copy()
+        self.schedule_stage()
+        hesp.solver_moves(self.cur, self.nb, self.NL, self.mode, self.crit, self.moves, self.count, self.rows)
+        k = int(self.count.item())
+        step = None
+        if trace:
+            m0 = int(self.cur_ms.item())
+        if k == 0:
+            if trace:
+                step = SolverStep(lv0, m0, [], [], None)
+            return None, 0, 0, step
+        hesp.simulate_batch(self.plat, self.cands_rows, self.rows, k, self.n, self.NL - 1, self.ws,
+                            makespan=self.ms, status=self.st, ntasks=self.nt, task_cap=self.task_cap)
+        if trace:
+            mv = self.moves[:k].cpu().numpy().tolist()
+            mss = self.ms[:k].cpu().numpy().tolist()
+        hesp.solver_pick(self.ms, self.st, self.moves, self.count, self.pick, seed, iteration, self.cur_ms, self.cur,
+                         self.chosen)
+        _, ev = hesp.best_makespan(self.ms[:k], self.st[:k], self.nt[:k])
+        vals = torch.stack([self.chosen[0], ev]).cpu().numpy()
+        ch = int(vals[0])
+        if ch == -2:
+            raise hesp.HespError(-6, "hesp_solver_pick (score sum >= 2^64)")
+        chosen = None if ch < 0 else ch
+        if trace:
+            step = SolverStep(lv0, m0, mv, mss, chosen)
+        return chosen, k, int(vals[1]), step
+
+    def solve(self, levels0, seed, iterations):
+        """Up to `iterations` iterations from levels0; the trace of each."""
+        self.start(levels0)
+        steps = []
+        for it in range(iterations):
+            chosen, _, _, step = self.iterate(seed, it, trace=True)
+            steps.append(step)
+            if chosen is None:
+                break
+        return steps
+
+
+def iterative_search(spec, n_tiles, b, n_levels, mode, pick, seed, budget_s, task_cap=0, ws_bytes=None,
+                     solver: Optional[IterativeSolver] = None) -> SearchLog:
+    """The iterative solver as a search arm: from uniform random partitions
+    (draw r of stream `seed` for restart r), iterate to a local optimum, then
+    restart, until budget_s of wall time have passed.  Soft draws use
+    (seed + r, iteration)."""
+    import torch
+    sv = solver or IterativeSolver(spec, n_tiles, b, n_levels, mode, pick, task_cap, ws_bytes)
+    names = {hesp.SOLVER_ALL: "all", hesp.SOLVER_CP: "cp", hesp.SOLVER_SHALLOW: "shallow"}
+    log = SearchLog("iterative-%s-%s" % (names[mode], "hard" if pick == hesp.PICK_HARD else "soft"))
+    best, events, done, r = None, 0, 0, 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        sv.start(seed=seed, draw=r)
+        it = 0
+        while time.perf_counter() - t0 < budget_s:
+            chosen, k, ev, _ = sv.iterate(seed + r, it)
+            events += ev
+            done += k
+            m = int(sv.cur_ms.item())
+            best = m if best is None else min(best, m)
+            log.times.append(time.perf_counter() - t0)
+            log.best.append(best)
+            log.events.append(events)
+            log.simulated.append(done)
+            it += 1
+            if chosen is None:
+                break
+        log.metrics.append({"restart": r, "iterations": it, "makespan": int(sv.cur_ms.item())})
+        r += 1
+    return log
