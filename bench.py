@@ -541,7 +541,7 @@ def run_search(args):
     each for the same wall-time budget on one GPU."""
     import torch
 
-    from paper_1602_05510_b300 import build
+    from paper_1602_05510_b300 import build, hesp
     from paper_1602_05510_b300 import search as S
 
     build.build()
@@ -560,6 +560,10 @@ def run_search(args):
     cfg_m = S.SurrogateConfig(**dict(cfg.__dict__, use_surrogate=False))
     mlog = S.surrogate_search(spec, n, b, NL, seed=5, budget_s=args.budget, per_launch=args.round_sims, cfg=cfg_m,
                               sim=sim2)
+    del sim, sim2
+    # the paper's own iterative solver (CP selection, Hard sampling) from the unsplit partition
+    ilog = S.iterative_search(spec, n, b, NL, hesp.SOLVER_CP, hesp.PICK_HARD, seed=6, budget_s=args.budget,
+                              task_cap=cap, ws_bytes=ws, first=np.zeros(W.base_count(n), np.int8))
     target = rlog.best[-1]
     t_reach = slog.time_to_reach(target)
     line = {"metric": "best makespan in %.0f s, surrogate vs plain search" % args.budget, "unit": "ns",
@@ -573,8 +577,48 @@ def run_search(args):
             "mutation_without_surrogate": {"best": mlog.best[-1], "candidates_simulated": mlog.simulated[-1],
                                            "trace": list(zip(mlog.times, mlog.best)),
                                            "time_to_random_best_s": mlog.time_to_reach(target)},
+            "iterative_cp_hard": {"best": ilog.best[-1], "candidates_simulated": ilog.simulated[-1],
+                                  "iterations": len(ilog.best), "task_events": ilog.events[-1],
+                                  "trace": list(zip(ilog.times, ilog.best)), "restarts": ilog.metrics,
+                                  "time_to_random_best_s": ilog.time_to_reach(target)},
             "surrogate_time_to_random_best_s": t_reach,
             "time_ratio": (t_reach / rlog.times[-1]) if t_reach is not None else None}
+    print(json.dumps(line))
+
+
+def run_solver(args):
+    """HeSP's iterative solver (Sec. 2.1) with each selection policy (All, CP,
+    Shallow) and sampling type (Hard, Soft) on 8 x 8 tiles (120 base tasks,
+    levels 0..2, 12 CPU + 1 GPU-type processors), starting from the unsplit
+    partition and restarting from uniform random ones at each local optimum,
+    next to plain batched random search, each for the same wall time."""
+    import torch
+
+    from paper_1602_05510_b300 import build, hesp
+    from paper_1602_05510_b300 import search as S
+
+    build.build()
+    n, b, NL = 8, 2048, 3
+    spec = W.PLATFORMS["cfg1a"]
+    B = args.solver_budget
+    arms = {}
+    rlog = S.random_search(spec, n, b, NL, seed=4, budget_s=B, per_launch=4096)
+    arms["random"] = {"best": rlog.best[-1], "candidates_simulated": rlog.simulated[-1],
+                      "task_events": rlog.events[-1]}
+    for mode, mname in ((hesp.SOLVER_ALL, "all"), (hesp.SOLVER_CP, "cp"), (hesp.SOLVER_SHALLOW, "shallow")):
+        for pick, pname in ((hesp.PICK_HARD, "hard"), (hesp.PICK_SOFT, "soft")):
+            lg = S.iterative_search(spec, n, b, NL, mode, pick, seed=6, budget_s=B, first=np.zeros(120, np.int8))
+            first_opt = lg.metrics[0] if lg.metrics else None
+            arms["%s_%s" % (mname, pname)] = {
+                "best": lg.best[-1], "candidates_simulated": lg.simulated[-1], "task_events": lg.events[-1],
+                "iterations": len(lg.best), "restarts": len(lg.metrics),
+                "first_local_optimum": first_opt,
+                "time_to_random_best_s": lg.time_to_reach(rlog.best[-1])}
+            torch.cuda.synchronize()
+    line = {"metric": "best makespan in %.0f s per arm, iterative solver policies vs plain search" % B,
+            "unit": "ns", "higher_is_better": False, "n_gpus": 1,
+            "workload": "8x8 tiles, b=2048, levels 0..2, 12 CPU + 1 GPU-type processors; solver arms start "
+                        "from the unsplit partition", "arms": arms}
     print(json.dumps(line))
 
 
@@ -590,13 +634,14 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=256)
     ap.add_argument("--candidates", type=int, default=N_CAND,
                     help="candidates per step (default: the workload's 65,536; smaller only for profiling)")
-    ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search", "uneven"],
+    ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search", "uneven", "solver"],
                     help="random: the default benchmark line; surrogate: label/train/rank/re-score "
                          "pipeline; search: surrogate-guided vs random search")
     ap.add_argument("--labels", type=int, default=1 << 20)
     ap.add_argument("--proposals", type=int, default=1 << 22)
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--budget", type=float, default=60.0)
+    ap.add_argument("--solver-budget", type=float, default=10.0)
     ap.add_argument("--per-launch", type=int, default=4096)
     ap.add_argument("--round-sims", type=int, default=1024)
     ap.add_argument("--round-proposals", type=int, default=65536)
@@ -611,6 +656,8 @@ def main():
         return run_search(args)
     if args.workload == "uneven":
         return run_uneven(args)
+    if args.workload == "solver":
+        return run_solver(args)
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -306,11 +306,12 @@ class IterativeSolver:
 
 
 def iterative_search(spec, n_tiles, b, n_levels, mode, pick, seed, budget_s, task_cap=0, ws_bytes=None,
-                     solver: Optional[IterativeSolver] = None) -> SearchLog:
-    """The iterative solver as a search arm: from uniform random partitions
-    (draw r of stream `seed` for restart r), iterate to a local optimum, then
-    restart, until budget_s of wall time have passed.  Soft draws use
-    (seed + r, iteration)."""
+                     solver: Optional[IterativeSolver] = None, first=None) -> SearchLog:
+    """The iterative solver as a search arm: from a start partition, iterate
+    to a local optimum, then restart, until budget_s of wall time have
+    passed.  Restart 0 starts from `first` (host levels) when given, every
+    other restart r from draw r of the uniform SplitMix64 stream `seed`.
+    Soft draws use (seed + r, iteration)."""
     import torch
     sv = solver or IterativeSolver(spec, n_tiles, b, n_levels, mode, pick, task_cap, ws_bytes)
     names = {hesp.SOLVER_ALL: "all", hesp.SOLVER_CP: "cp", hesp.SOLVER_SHALLOW: "shallow"}
@@ -319,7 +320,10 @@ def iterative_search(spec, n_tiles, b, n_levels, mode, pick, seed, budget_s, tas
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < budget_s:
-        sv.start(seed=seed, draw=r)
+        if r == 0 and first is not None:
+            sv.start(levels=first)
+        else:
+            sv.start(seed=seed, draw=r)
         it = 0
         while time.perf_counter() - t0 < budget_s:
             chosen, k, ev, _ = sv.iterate(seed + r, it)
