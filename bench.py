@@ -622,6 +622,40 @@ def run_solver(args):
     print(json.dumps(line))
 
 
+def run_table1(args):
+    """The paper's Table 1 procedure on the synthetic cost model, for a
+    CPU-GPU machine shaped like its 28-core + 3-GPU one (N = 32768, single
+    precision transfers) and a 4 big + 4 LITTLE one (N = 8192): per
+    scheduling policy, the best homogeneous tile size and the heterogeneous
+    partition the All/Soft iterative solver reaches from it."""
+    import dataclasses
+
+    from paper_1602_05510_b300 import build
+    from paper_1602_05510_b300 import table1 as TB
+
+    build.build()
+    plats = [("cpu28_gpu3 (N=32768, fp32)",
+              dataclasses.replace(W.cpu_gpu_platform(28, 3), bytes_per_elem=4), 32768, (512, 1024, 2048, 4096)),
+             ("big4_little4 (N=8192, fp64)", W.big_little_platform(), 8192, (128, 256, 512, 1024, 2048))]
+    out = {}
+    for pname, spec, N, sizes in plats:
+        rows = []
+        for name, order, select in TB.POLICIES:
+            t0 = time.perf_counter()
+            r = TB.table_row(spec, N, sizes, order, select, rp_seed=1, max_level=3, iterations=args.table_iters,
+                             seed=2, task_cap=1 << 20, ws_bytes=48 << 30)
+            rows.append({"policy": name, "homog_gflops": r["homog"]["gflops"],
+                         "homog_load_pct": 100 * r["homog"]["load"], "homog_block": r["homog_block"],
+                         "het_gflops": r["het"]["gflops"], "improvement_pct": r["improvement"],
+                         "het_load_pct": 100 * r["het"]["load"], "avg_block": r["het"]["avg_block"],
+                         "dag_depth": r["het"]["depth"], "solver_iterations": r["iterations"],
+                         "sweep_makespans": r["sweep"], "s": time.perf_counter() - t0})
+        out[pname] = rows
+    print(json.dumps({"metric": "Table 1 procedure (homogeneous sweep + All/Soft iterative solver)", "n_gpus": 1,
+                      "cost_model": "synthetic (CPU 30 GFLOP/s h=96, GPU 2500 GFLOP/s h=768, big 12, LITTLE 3)",
+                      "tables": out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -634,7 +668,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=256)
     ap.add_argument("--candidates", type=int, default=N_CAND,
                     help="candidates per step (default: the workload's 65,536; smaller only for profiling)")
-    ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search", "uneven", "solver"],
+    ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search", "uneven", "solver", "table1"],
                     help="random: the default benchmark line; surrogate: label/train/rank/re-score "
                          "pipeline; search: surrogate-guided vs random search")
     ap.add_argument("--labels", type=int, default=1 << 20)
@@ -642,6 +676,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--budget", type=float, default=60.0)
     ap.add_argument("--solver-budget", type=float, default=10.0)
+    ap.add_argument("--table-iters", type=int, default=40)
     ap.add_argument("--per-launch", type=int, default=4096)
     ap.add_argument("--round-sims", type=int, default=1024)
     ap.add_argument("--round-proposals", type=int, default=65536)
@@ -658,6 +693,8 @@ def main():
         return run_uneven(args)
     if args.workload == "solver":
         return run_solver(args)
+    if args.workload == "table1":
+        return run_table1(args)
     if args.impl == "reference":
         run_reference(args)
     else:

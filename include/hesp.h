@@ -213,6 +213,24 @@ int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands_dev, cons
                         int16_t *proc_dev, int64_t *start_dev, int64_t *finish_dev, void *workspace_dev,
                         size_t workspace_bytes, void *stream);
 
+/* Table 1 metrics (Sec. 3) of simulated candidates, one value per candidate:
+ *   busy_dev[c]      = sum over its tasks of finish - start (the processors'
+ *                      total busy time; average load = busy / (P * makespan));
+ *                      -1 when no schedule is given;
+ *   ntasks_dev[c]    = its task count;
+ *   sum_block_dev[c] = sum over its tasks of the block size (average block
+ *                      size = sum_block / ntasks);
+ *   depth_dev[c]     = 1 + its deepest split level (the levels of its task
+ *                      hierarchy).
+ * GFLOPS = (n b)^3 / 3 / makespan.  Inputs as for hesp_simulate_batch; the
+ * schedule (sched_offsets_dev, start_dev, finish_dev: all three or none) is
+ * the one hesp_simulate_batch wrote.  Any output pointer may be NULL.  All
+ * device pointers; asynchronous on `stream`. */
+int hesp_schedule_metrics(const hesp_cand *cands_dev, const int8_t *levels_dev, int64_t n_cand,
+                          const int64_t *sched_offsets_dev, const int64_t *start_dev, const int64_t *finish_dev,
+                          int64_t *busy_dev, int64_t *ntasks_dev, int64_t *sum_block_dev, int32_t *depth_dev,
+                          void *stream);
+
 /* ------------------------------------------------ iterative partition solver
  * HeSP's iterative solver (Sec. 2.1 "Iterative solver"): each iteration is a
  * schedule stage (simulate the partition) and a partition stage (list

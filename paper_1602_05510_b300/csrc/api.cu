@@ -365,6 +365,18 @@ int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands, const in
                            sched_off, sproc, sstart, sfinish, nullptr, ws, ws_bytes, stream);
 }
 
+int hesp_schedule_metrics(const hesp_cand *cands, const int8_t *levels, int64_t n_cand, const int64_t *sched_off,
+                          const int64_t *start, const int64_t *finish, int64_t *busy, int64_t *ntasks,
+                          int64_t *sum_block, int32_t *depth, void *stream) {
+    if (n_cand < 0) return HESP_ERR_ARG;
+    if (n_cand == 0) return HESP_OK;
+    if (!cands || !levels) return HESP_ERR_ARG;
+    const bool any_s = sched_off || start || finish;
+    if (any_s && !(sched_off && start && finish)) return HESP_ERR_ARG;
+    return launch_metrics(cands, levels, n_cand, sched_off, start, finish, busy, ntasks, sum_block, depth,
+                          (cudaStream_t)stream);
+}
+
 int hesp_simulate_critical(const hesp_platform *p, const hesp_cand *cands, const int8_t *levels, int64_t n_cand,
                            int32_t max_tiles, int32_t max_level, int64_t task_cap, int64_t *makespan,
                            int32_t *status, int8_t *crit, void *ws, size_t ws_bytes, void *stream) {

@@ -99,6 +99,9 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
                int64_t *makespan, int32_t *status, int64_t *ntasks, const int64_t *sched_off, int16_t *sproc,
                int64_t *sstart, int64_t *sfinish, int8_t *crit, char *ws, cudaStream_t stream);
 int sim_kernel_occupancy(int n_mem, int n_procs, int64_t Tcap, int *blocks_per_sm, int *threads_per_block);
+int launch_metrics(const hesp_cand *cands, const int8_t *levels, int64_t n_cand, const int64_t *sched_off,
+                   const int64_t *start, const int64_t *finish, int64_t *busy, int64_t *ntasks, int64_t *sum_block,
+                   int32_t *depth, cudaStream_t stream);
 int sim_bitmap_smem_words(int64_t Tcap);
 
 int launch_generate(int32_t kind, uint64_t seed, int64_t first, int64_t n_cand, int32_t n_tiles, int32_t b,

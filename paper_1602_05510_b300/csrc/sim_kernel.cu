@@ -1137,7 +1137,61 @@ void launch_one(bool gen, unsigned blocks, int threads, size_t smem, cudaStream_
     else sim_kernel<M, NS, false><<<blocks, threads, smem, stream>>>(dp, a, ctr);
 }
 
+// Table-1 metrics of simulated schedules, one warp per candidate: the tasks'
+// summed execution time (finish - start), the task count, the summed block
+// size of the tasks (each base task at level l holds c_cnt[op][l] tasks of
+// block b >> l), and the hierarchy depth 1 + max level.
+__global__ void metrics_kernel(const hesp_cand *cands, const int8_t *levels, int64_t n_cand, const int64_t *sched_off,
+                               const int64_t *start, const int64_t *finish, int64_t *busy, int64_t *ntasks,
+                               int64_t *sum_block, int32_t *depth) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c >= n_cand) return;
+    const hesp_cand cd = cands[c];
+    const int n = cd.n_tiles, b = cd.b;
+    const int64_t nb = (int64_t)n * (n + 1) * (n + 2) / 6;
+    int64_t cnt = 0, sb = 0;
+    int lmax = 0;
+    for (int64_t t = lane; t < nb; t += 32) {
+        int op, K, I, J;
+        decode_base(n, t, op, K, I, J);
+        const int l = levels[cd.level_offset + t];
+        cnt += c_cnt[op][l];
+        sb += (int64_t)c_cnt[op][l] * (b >> l);
+        lmax = max(lmax, l);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        cnt += __shfl_xor_sync(FULL, cnt, o);
+        sb += __shfl_xor_sync(FULL, sb, o);
+    }
+    lmax = __reduce_max_sync(FULL, lmax);
+    int64_t bz = 0;
+    if (sched_off) {
+        const int64_t o0 = sched_off[c];
+        for (int64_t j = lane; j < cnt; j += 32) bz += finish[o0 + j] - start[o0 + j];
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) bz += __shfl_xor_sync(FULL, bz, o);
+    }
+    if (lane == 0) {
+        if (busy) busy[c] = sched_off ? bz : -1;
+        if (ntasks) ntasks[c] = cnt;
+        if (sum_block) sum_block[c] = sb;
+        if (depth) depth[c] = 1 + lmax;
+    }
+}
+
 }  // namespace
+
+int launch_metrics(const hesp_cand *cands, const int8_t *levels, int64_t n_cand, const int64_t *sched_off,
+                   const int64_t *start, const int64_t *finish, int64_t *busy, int64_t *ntasks, int64_t *sum_block,
+                   int32_t *depth, cudaStream_t stream) {
+    if (n_cand == 0) return HESP_OK;
+    const int64_t blocks = (n_cand * 32 + 255) / 256;
+    metrics_kernel<<<(unsigned)blocks, 256, 0, stream>>>(cands, levels, n_cand, sched_off, start, finish, busy, ntasks,
+                                                        sum_block, depth);
+    return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
+}
 
 // Shared-memory bitmap words per warp for a workspace sized for Tcap tasks
 // (0 = the bitmap stays in the arena): up to 2048 words (64 Ki tasks).

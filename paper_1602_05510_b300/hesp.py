@@ -37,7 +37,7 @@ EXPORTS = (
     "hesp_generate_mutants", "hesp_gather_rows", "hesp_best_makespan", "hesp_graph_begin", "hesp_graph_end",
     "hesp_graph_launch", "hesp_graph_destroy", "hesp_platform_set_tuning", "hesp_platform_get_tuning",
     "hesp_sim_autotune", "hesp_sort_cands_workspace_size", "hesp_sort_cands_by_size", "hesp_platform_set_policy",
-    "hesp_simulate_critical", "hesp_solver_moves", "hesp_solver_pick",
+    "hesp_simulate_critical", "hesp_solver_moves", "hesp_solver_pick", "hesp_schedule_metrics",
 )
 SOLVER_ALL, SOLVER_CP, SOLVER_SHALLOW = 0, 1, 2
 PICK_HARD, PICK_SOFT = 0, 1
@@ -101,6 +101,7 @@ def lib():
         L.hesp_simulate_critical.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, sz, vp]
         L.hesp_solver_moves.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp]
         L.hesp_solver_pick.argtypes = [vp, vp, vp, vp, i32, u64, i64, vp, vp, vp, vp]
+        L.hesp_schedule_metrics.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
         L.hesp_gemm_bf16.argtypes = [i32, i32, i32, vp, i64, vp, i64, i32, vp, i64, vp, vp, i64, vp, i64, vp, i64,
                                      vp, vp]
         f32, f64 = ctypes.c_float, ctypes.c_double
@@ -322,6 +323,24 @@ def simulate_critical(platform: Platform, cands, levels, n_cand, max_tiles, max_
                                        _ptr(makespan), _ptr(status), _ptr(crit), _ptr(workspace), workspace.numel(),
                                        _stream(stream)), "hesp_simulate_critical")
     return makespan, status
+
+
+def schedule_metrics(cands, levels, n_cand, schedule=None, stream=None):
+    """hesp_schedule_metrics: (busy, ntasks, sum_block, depth) device tensors
+    per candidate; `schedule` = the (offsets, proc, start, finish) tensors
+    given to simulate_batch, or None (busy is then -1)."""
+    import torch
+    dev = levels.device
+    busy = torch.empty(n_cand, dtype=torch.int64, device=dev)
+    nt = torch.empty(n_cand, dtype=torch.int64, device=dev)
+    sb = torch.empty(n_cand, dtype=torch.int64, device=dev)
+    dp = torch.empty(n_cand, dtype=torch.int32, device=dev)
+    so = ss = sf = None
+    if schedule is not None:
+        so, _, ss, sf = schedule
+    check(lib().hesp_schedule_metrics(_ptr(cands), _ptr(levels), n_cand, _ptr(so), _ptr(ss), _ptr(sf), _ptr(busy),
+                                      _ptr(nt), _ptr(sb), _ptr(dp), _stream(stream)), "hesp_schedule_metrics")
+    return busy, nt, sb, dp
 
 
 def solver_moves(levels, n_base, n_levels, mode, crit, moves, count, rows=None, stream=None):
