@@ -418,7 +418,9 @@ int hesp_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *a_dev, int64_t l
  * activations for max_batch rows). */
 typedef struct hesp_surrogate hesp_surrogate;
 
-/* hidden and max_batch: multiples of 64.  Synchronous. */
+/* hidden and max_batch: multiples of 64; n_levels 1 .. HESP_MAX_LEVEL + 1
+ * (the first layer builds its one-hot operand inside the GEMM from a table
+ * sized for at most 5 levels).  Synchronous. */
 int hesp_surrogate_create(int32_t n_base, int32_t n_levels, int32_t hidden, int32_t max_batch, uint64_t seed,
                           hesp_surrogate **out);
 void hesp_surrogate_destroy(hesp_surrogate *s);

@@ -2,17 +2,28 @@
 //     C[M, N] = A[M, K] . B[N, K]^T      (A, B bf16, K contiguous; FP32 accumulate)
 // with fused epilogues for the surrogate MLP's layers.
 //
-// One CTA computes a 128 x 128 tile of C.  Warp 0 (one elected lane) streams
-// 128 x 64 tiles of A and B into a 3-stage shared-memory ring with TMA
-// (cp.async.bulk.tensor, 128-byte swizzle); warp 1 (one lane) issues
-// tcgen05.mma (M = 128, N = 128, K = 16 per instruction) into a TMEM
-// accumulator and releases each stage with tcgen05.commit on its "empty"
-// mbarrier; warp 2 owns the TMEM allocation; all four warps then drain the
-// accumulator with tcgen05.ld (warp w reads TMEM lanes 32w .. 32w+31 = rows)
-// and apply the epilogue.  Two CTAs fit one SM (~100 KB of shared memory and
-// 128 TMEM columns each), so one CTA's epilogue overlaps the other's main
-// loop.  Every mbarrier wait is bounded: on expiry the CTA
-// raises the caller's error flag, frees its TMEM and returns.
+// Persistent and warp-specialised, one CTA per SM: each CTA walks 128 x 256
+// output tiles (blockIdx.x, + gridDim.x, ...; the N-tiles of one row block
+// are consecutive).  Warp 0 (one lane) streams 64-column k-blocks of B (256
+// rows) -- and of A (128 rows), unless A is built in place -- into a 4-stage
+// shared-memory ring with TMA (cp.async.bulk.tensor, 128-byte swizzle); warp 1
+// (one lane) issues tcgen05.mma (M = 128, N = 256, K = 16 per instruction)
+// into one of two TMEM accumulators (2 x 256 columns, all of TMEM) and frees
+// each stage with tcgen05.commit; warps 2-9 drain the other accumulator
+// (tcgen05.ld; warp w reads TMEM lanes 32 (w % 4) .. + 31, warps 2-5 the first
+// 128 columns and 6-9 the last) and apply the epilogue, so a tile's epilogue
+// runs under the next tile's main loop.
+//
+// With NL > 0 the A operand is the one-hot encoding of int8 levels,
+// X[r, f] = (levels[r, f / NL] == f % NL) for f < n_base NL (else 0), and
+// warps 10-13 build its tiles in shared memory (thread r writes row r, eight
+// 16-byte chunks per k-block, in the same swizzled layout), so the one-hot
+// matrix never exists in memory.  A chunk of 8 features starting at phase
+// v0 = f % NL spans at most S tasks; its 16 bytes are read from a table,
+// built once per CTA, indexed by (v0, the S levels).
+//
+// Every mbarrier wait is bounded: on expiry the role stops, the caller's error
+// flag is raised, and the CTA frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -28,11 +39,28 @@ namespace hesp {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 3;
-constexpr int TILE_BYTES = BM * BK * 2;  // 16 KiB per operand per stage
-constexpr int STAGE_BYTES = 2 * TILE_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int A_BYTES = BM * BK * 2;  // 16 KiB
+constexpr int B_BYTES = BN * BK * 2;  // 32 KiB
+constexpr int LV_COLS = 80;           // level window box: 80 bytes x 128 rows (inner start rounded down to 16)
+constexpr int LV_BYTES = BM * LV_COLS;
+constexpr int TABLE_BYTES = 10240;    // one-hot chunk table: NL * NL^S entries of 16 bytes (<= 625 for NL <= 5)
+// per instantiation: TMA A operand (NL = 0), or A built from levels (NL > 0)
+__host__ __device__ constexpr int stages_of(int nl) { return nl > 0 ? 3 : 4; }
+__host__ __device__ constexpr int stage_bytes_of(int nl) { return A_BYTES + B_BYTES + (nl > 0 ? LV_BYTES : 0); }
+__host__ __device__ constexpr int smem_bytes_of(int nl) {
+    return 1024 + stages_of(nl) * stage_bytes_of(nl) + (nl > 0 ? TABLE_BYTES : 0) + 512;
+}
+constexpr int TMEM_COLS = 2 * BN;  // two accumulators: all of TMEM, one CTA per SM
+constexpr int N_EPI_WARPS = 8;
 constexpr uint32_t kWaitLimit = 1u << 22;
+
+// tasks spanned by 8 consecutive features, at most, for NL levels per task
+__host__ __device__ constexpr int span_of(int nl) { return nl <= 0 ? 1 : (nl - 1 + 8 + nl - 1) / nl; }
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+// level bytes a 64-feature k-block reads (the S tasks from each chunk's first
+// task), in 32-bit words
+__host__ __device__ constexpr int window_words(int nl) { return ((nl - 1 + 56) / nl + span_of(nl) + 3) / 4; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -41,6 +69,9 @@ __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
     uint32_t ok;
@@ -96,28 +127,131 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(128, 2)
-    gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
+// Epilogue of 16 accumulator columns of one output row.
+__device__ __forceinline__ void epilogue16(const GemmArgs &g, int row, int col0, const uint32_t (&r)[16]) {
+    float v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+    const bool full = col0 + 16 <= g.N;
+    if (g.epi == 0) {
+        float *dst = g.C + (int64_t)row * g.ldc + col0;
+        if (full && (((uintptr_t)dst) & 15) == 0) {
+#pragma unroll
+            for (int q = 0; q < 16; q += 4)
+                *reinterpret_cast<float4 *>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        } else {
+            for (int q = 0; q < 16 && col0 + q < g.N; ++q) dst[q] = v[q];
+        }
+        return;
+    }
+    if (g.epi == 1) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const float bq = (col0 + q < g.N) ? g.bias[col0 + q] : 0.f;
+            v[q] = fmaxf(v[q] + bq, 0.f);
+        }
+    } else {
+        const __nv_bfloat16 *mk = g.mask + (int64_t)row * g.ldm + col0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (col0 + q < g.N && !(__bfloat162float(mk[q]) > 0.f)) v[q] = 0.f;
+    }
+    __nv_bfloat16 h[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) h[q] = __float2bfloat16_rn(v[q]);
+    __nv_bfloat16 *dst = g.out + (int64_t)row * g.ldo + col0;
+    if (full && (((uintptr_t)dst) & 15) == 0) {
+        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(h);
+        *reinterpret_cast<uint4 *>(dst + 8) = *reinterpret_cast<const uint4 *>(h + 8);
+    } else {
+        for (int q = 0; q < 16 && col0 + q < g.N; ++q) dst[q] = h[q];
+    }
+    if (g.out_t) {
+        for (int q = 0; q < 16 && col0 + q < g.N; ++q) g.out_t[(int64_t)(col0 + q) * g.ldt + row] = h[q];
+    }
+}
+
+// One 64-feature k-block of one one-hot row, whose first feature has phase V
+// (= f % NL) and whose tasks start at window byte 0 (n_valid of the window's
+// bytes are tasks of the row).  Chunk c covers features V + 8c .. + 7 of the
+// window: tasks i0 = (V + 8c) / NL .. i0 + S - 1, phase v0 = (V + 8c) % NL.
+// With the whole window valid (tasks of the row, levels < NL) a chunk is one
+// table entry; otherwise each feature is compared on its own (bf16 1.0 where
+// the level matches, 0 past the row or for an invalid level).
+template <int NL, int V, int WW>
+__device__ __forceinline__ void onehot_kblock(const uint32_t (&w)[WW], const uint4 *table, uint8_t *arow, int r,
+                                              int n_valid) {
+    constexpr int S = span_of(NL);
+    uint32_t bad = n_valid < 4 * WW ? 1u : 0u;  // the window runs past the row's last task
+#pragma unroll
+    for (int i = 0; i < WW; ++i)  // a byte >= NL: bit 7 set, or bit 7 after adding 128 - NL to its low 7 bits
+        bad |= (w[i] | ((w[i] & 0x7F7F7F7Fu) + (uint32_t)(128 - NL) * 0x01010101u)) & 0x80808080u;
+    if (bad == 0) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int p = V + 8 * c;
+            const int i0 = p / NL, v0 = p % NL;
+            int idx = v0;
+#pragma unroll
+            for (int i = 0; i < S; ++i) {
+                const int bi = i0 + i;
+                idx = idx * NL + (int)((w[bi >> 2] >> (8 * (bi & 3))) & 0xFFu);
+            }
+            *reinterpret_cast<uint4 *>(arow + ((c ^ (r & 7)) << 4)) = table[idx];
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            uint32_t o[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int p0 = V + 8 * c + 2 * h, p1 = p0 + 1;
+                const int b0 = p0 / NL, b1 = p1 / NL;
+                const uint32_t l0 = b0 < n_valid ? (w[b0 >> 2] >> (8 * (b0 & 3))) & 0xFFu : 0xFFu;
+                const uint32_t l1 = b1 < n_valid ? (w[b1 >> 2] >> (8 * (b1 & 3))) & 0xFFu : 0xFFu;
+                o[h] = (l0 == (uint32_t)(p0 % NL) ? 0x3F80u : 0u) | ((l1 == (uint32_t)(p1 % NL) ? 0x3F80u : 0u) << 16);
+            }
+            *reinterpret_cast<uint4 *>(arow + ((c ^ (r & 7)) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
+        }
+    }
+}
+
+template <int NL>
+__global__ void __launch_bounds__(NL > 0 ? 448 : 320, 1)
+    gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmL, GemmArgs g) {
+    constexpr int STAGES = stages_of(NL), STAGE_BYTES = stage_bytes_of(NL);
+    constexpr int NBARS = 3 * STAGES + 4;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES);
-    uint32_t *holder = (uint32_t *)(bars + 2 * STAGES + 1);
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+    uint4 *table = (uint4 *)(smem + STAGES * STAGE_BYTES);
+    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES + (NL > 0 ? TABLE_BYTES : 0));
+    uint32_t *holder = (uint32_t *)(bars + NBARS);
+    // full: the stage is ready for the MMA; empty: the MMA is done with it;
+    // lfull (NL > 0): B and the level window have landed; tfull / tempty: an
+    // accumulator is complete / drained
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), lfull0 = smem_u32(bars + 2 * STAGES);
+    const uint32_t tfull0 = smem_u32(bars + 3 * STAGES), tempty0 = smem_u32(bars + 3 * STAGES + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int KT = g.K / BK;
+    const int nN = (g.N + BN - 1) / BN;
+    const int n_tiles = ((g.M + BM - 1) / BM) * nN;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full0 + 8 * s, 1);
+            mbar_init(full0 + 8 * s, NL > 0 ? 4 : 1);  // one lane per A-producer warp, or the TMA thread
             mbar_init(empty0 + 8 * s, 1);
+            mbar_init(lfull0 + 8 * s, 1);
         }
-        mbar_init(done, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull0 + 8 * a, 1);
+            mbar_init(tempty0 + 8 * a, N_EPI_WARPS);  // one lane per epilogue warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)),
-                     "r"(BN)
+                     "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -127,107 +261,175 @@ __global__ void __launch_bounds__(128, 2)
     const uint32_t tmem = *holder;
 
     bool fail = false;
-    if (warp == 0 && lane == 0) {
-        // TMA producer
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % STAGES;
-            if (kt >= STAGES && !mbar_wait(empty0 + 8 * s, ((kt / STAGES) - 1) & 1)) {
-                fail = true;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer: A and B (NL = 0), or B and the level window (NL > 0)
+            int it = 0;
+            for (int tile = blockIdx.x; tile < n_tiles && !fail; tile += gridDim.x) {
+                const int m0 = (tile / nN) * BM, n0 = (tile % nN) * BN;
+                for (int kt = 0; kt < KT; ++kt, ++it) {
+                    const int s = it % STAGES, q = it / STAGES;
+                    if (q > 0 && !mbar_wait(empty0 + 8 * s, (q - 1) & 1)) {
+                        fail = true;
+                        break;
+                    }
+                    const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+                    if constexpr (NL == 0) {
+                        mbar_expect_tx(full0 + 8 * s, A_BYTES + B_BYTES);
+                        tma_load_2d(sa, &tmA, full0 + 8 * s, kt * BK, m0);
+                        tma_load_2d(sa + A_BYTES, &tmB, full0 + 8 * s, kt * BK, n0);
+                    } else {
+                        // tasks from t_kb on; the box starts at t_kb rounded down to 16 bytes
+                        const int t_kb = (kt * BK) / NL;
+                        mbar_expect_tx(lfull0 + 8 * s, B_BYTES + LV_BYTES);
+                        tma_load_2d(sa + A_BYTES, &tmB, lfull0 + 8 * s, kt * BK, n0);
+                        tma_load_2d(sa + A_BYTES + B_BYTES, &tmL, lfull0 + 8 * s, t_kb & ~15, m0);
+                    }
+                }
             }
-            mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-            tma_load_2d(sa, &tmA, full0 + 8 * s, kt * BK, m0);
-            tma_load_2d(sa + TILE_BYTES, &tmB, full0 + 8 * s, kt * BK, n0);
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        constexpr uint32_t idesc = idesc_bf16(BM, BN);
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % STAGES;
-            if (!mbar_wait(full0 + 8 * s, (kt / STAGES) & 1)) {
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            int it = 0, i = 0;
+            for (int tile = blockIdx.x; tile < n_tiles && !fail; tile += gridDim.x, ++i) {
+                const int acc_i = i & 1, use = i >> 1;
+                if (use > 0 && !mbar_wait(tempty0 + 8 * acc_i, (use - 1) & 1)) {
+                    fail = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(acc_i * BN);
+                for (int kt = 0; kt < KT; ++kt, ++it) {
+                    const int s = it % STAGES, q = it / STAGES;
+                    if (!mbar_wait(full0 + 8 * s, q & 1)) {
+                        fail = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint64_t da = sw128_desc(sa + kk * 32);
+                        const uint64_t db = sw128_desc(sa + A_BYTES + kk * 32);
+                        const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\t"
+                            "setp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                            "l"(da), "l"(db), "r"(idesc), "r"(accum)
+                            : "memory");
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 +
+                                                                                                            8 * s)
+                        : "memory");
+                }
+                if (fail) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 tfull0 + 8 * acc_i)
+                             : "memory");
+            }
+        }
+    } else if (warp < 2 + N_EPI_WARPS) {
+        // epilogue: rows 32 (warp % 4) .. + 31 of each tile, columns
+        // 128 h .. + 127 with h = (warp - 2) / 4
+        const int wq = warp & 3, h = (warp - 2) >> 2;
+        int i = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+            const int acc_i = i & 1, use = i >> 1;
+            const bool ok = __all_sync(0xFFFFFFFFu, mbar_wait(tfull0 + 8 * acc_i, use & 1));
+            if (!ok) {
                 fail = true;
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint64_t da = sw128_desc(sa + kk * 32);
-                const uint64_t db = sw128_desc(sa + TILE_BYTES + kk * 32);
-                const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\t"
-                    "setp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                    "l"(da), "l"(db), "r"(idesc), "r"(acc)
-                    : "memory");
+            const int m0 = (tile / nN) * BM, n0 = (tile % nN) * BN;
+            const int row = m0 + wq * 32 + lane;
+            const bool rok = row < g.M;
+            for (int c0 = h * 128; c0 < h * 128 + 128; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(acc_i * BN + c0), r);
+                if (rok && n0 + c0 < g.N) epilogue16(g, row, n0 + c0, r);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 +
-                                                                                                           8 * s)
-                         : "memory");
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty0 + 8 * acc_i);
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done)
-                     : "memory");
-    }
-    __syncwarp();
-    const bool ready = __all_sync(0xFFFFFFFFu, !fail && mbar_wait(done, 0));
-    tc_fence_after();
-    if (ready) {
-        const int row = m0 + warp * 32 + lane;
-        const bool rok = row < g.M;
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            uint32_t r[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-            const int col0 = n0 + c0;
-            if (!rok || col0 >= g.N) continue;
-            float v[16];
+    } else if constexpr (NL > 0) {
+        // A producers (warps 10-13): the chunk table, then for each k-block,
+        // once B and the level window have landed, thread r builds row r of
+        // the A tile from its window, with byte positions fixed by the
+        // k-block's phase.  The only barrier across the four warps is the one
+        // after the table is built, before any wait that can time out.
+        constexpr int S = span_of(NL);
+        constexpr int NE = NL * ipow(NL, S);
+        constexpr int WW = window_words(NL);
+        const int tid = threadIdx.x - 32 * (2 + N_EPI_WARPS);
+        for (int e = tid; e < NE; e += 128) {
+            int rem = e, lv_[S];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
-            const bool full = col0 + 16 <= g.N;
-            if (g.epi == 0) {
-                float *dst = g.C + (int64_t)row * g.ldc + col0;
-                if (full && (((uintptr_t)dst) & 15) == 0) {
+            for (int i = S - 1; i >= 0; --i) {
+                lv_[i] = rem % NL;
+                rem /= NL;
+            }
+            const int v0 = rem;
+            uint32_t w[4];
 #pragma unroll
-                    for (int q = 0; q < 16; q += 4) *reinterpret_cast<float4 *>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-                } else {
-                    for (int q = 0; q < 16 && col0 + q < g.N; ++q) dst[q] = v[q];
+            for (int q = 0; q < 8; q += 2) {
+                const int p0 = v0 + q, p1 = v0 + q + 1;
+                const uint32_t lo = lv_[p0 / NL] == p0 % NL ? 0x3F80u : 0u;
+                const uint32_t hi = lv_[p1 / NL] == p1 % NL ? 0x3F80u : 0u;
+                w[q >> 1] = lo | (hi << 16);
+            }
+            table[e] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");  // the four producer warps
+        const int r = tid;
+        const int nb = g.oh_base;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < n_tiles && !fail; tile += gridDim.x) {
+            for (int kt = 0; kt < KT; ++kt, ++it) {
+                const int s = it % STAGES, q = it / STAGES;
+                if (!__all_sync(0xFFFFFFFFu, mbar_wait(lfull0 + 8 * s, q & 1))) {
+                    fail = true;
+                    break;
                 }
-                continue;
-            }
-            if (g.epi == 1) {
+                const int t_kb = (kt * BK) / NL, v_kb = kt * BK - t_kb * NL;
+                const int o = t_kb & 15;  // window start inside the 16-byte aligned box
+                const uint32_t *lrow =
+                    (const uint32_t *)(smem + s * STAGE_BYTES + A_BYTES + B_BYTES + r * LV_COLS) + (o >> 2);
+                uint32_t win[WW];
+                uint32_t prev = lrow[0];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float bq = (col0 + q < g.N) ? g.bias[col0 + q] : 0.f;
-                    v[q] = fmaxf(v[q] + bq, 0.f);
+                for (int i = 0; i < WW; ++i) {
+                    const uint32_t next = lrow[i + 1];
+                    win[i] = __funnelshift_r(prev, next, 8 * (o & 3));
+                    prev = next;
                 }
-            } else {
-                const __nv_bfloat16 *mk = g.mask + (int64_t)row * g.ldm + col0;
-#pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (col0 + q < g.N && !(__bfloat162float(mk[q]) > 0.f)) v[q] = 0.f;
-            }
-            __nv_bfloat16 h[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) h[q] = __float2bfloat16_rn(v[q]);
-            __nv_bfloat16 *dst = g.out + (int64_t)row * g.ldo + col0;
-            if (full && (((uintptr_t)dst) & 15) == 0) {
-                *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(h);
-                *reinterpret_cast<uint4 *>(dst + 8) = *reinterpret_cast<const uint4 *>(h + 8);
-            } else {
-                for (int q = 0; q < 16 && col0 + q < g.N; ++q) dst[q] = h[q];
-            }
-            if (g.out_t) {
-                for (int q = 0; q < 16 && col0 + q < g.N; ++q) g.out_t[(int64_t)(col0 + q) * g.ldt + row] = h[q];
+                uint8_t *arow = smem + s * STAGE_BYTES + r * 128;
+                const int n_valid = nb - t_kb;
+                switch (v_kb) {
+                case 0: onehot_kblock<NL, 0>(win, table, arow, r, n_valid); break;
+                case 1: if constexpr (NL > 1) onehot_kblock<NL, 1>(win, table, arow, r, n_valid); break;
+                case 2: if constexpr (NL > 2) onehot_kblock<NL, 2>(win, table, arow, r, n_valid); break;
+                case 3: if constexpr (NL > 3) onehot_kblock<NL, 3>(win, table, arow, r, n_valid); break;
+                default: if constexpr (NL > 4) onehot_kblock<NL, 4>(win, table, arow, r, n_valid); break;
+                }
+                // make the generic-proxy writes visible to the tensor core
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(full0 + 8 * s);
             }
         }
     }
-    if ((fail || !ready) && g.err && lane == 0) atomicExch(g.err, 1);
+    if (fail && g.err) atomicExch(g.err, 1);
     tc_fence_before();
     __syncthreads();
     if (warp == 2) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
 }
 
@@ -247,16 +449,57 @@ int get_encode() {
     return HESP_OK;
 }
 
-// Tensor map of a row-major bf16 matrix [rows, ld] read in 128 x 64 boxes.
-int make_map(CUtensorMap *tm, const void *ptr, int64_t rows, int64_t cols, int64_t ld) {
+// Tensor map of a row-major bf16 matrix [rows, ld] read in box_rows x 64 boxes.
+int make_map(CUtensorMap *tm, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-    cuuint32_t box[2] = {BK, BM};
+    cuuint32_t box[2] = {BK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     const CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box,
                                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? HESP_OK : HESP_ERR_ARG;
+}
+
+// Tensor map of int8 levels [rows, ld bytes] read in 128-row x LV_COLS-byte
+// boxes (ld a multiple of 16; bytes past n_base read as 0).
+int make_level_map(CUtensorMap *tm, const int8_t *ptr, int64_t rows, int64_t n_base, int64_t ld) {
+    cuuint64_t dims[2] = {(cuuint64_t)n_base, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld};
+    cuuint32_t box[2] = {LV_COLS, BM};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<int8_t *>(ptr), dims, strides, box,
+                                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? HESP_OK : HESP_ERR_ARG;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess)
+            n = 148;
+    }
+    return n;
+}
+
+template <int NL>
+int launch_persistent(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap &tl, const GemmArgs &g,
+                      cudaStream_t st) {
+    constexpr int SMEM = smem_bytes_of(NL);
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaFuncSetAttribute(gemm_bf16_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) !=
+            cudaSuccess)
+            return HESP_ERR_CUDA;
+        attr_set = true;
+    }
+    const int64_t tiles = (int64_t)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
+    const int64_t grid = tiles < sm_count() ? tiles : sm_count();
+    gemm_bf16_kernel<NL><<<(unsigned)grid, NL > 0 ? 448 : 320, SMEM, st>>>(ta, tb, tl, g);
+    return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
 }
 
 }  // namespace
@@ -270,18 +513,38 @@ int launch_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, con
     int rc = get_encode();
     if (rc) return rc;
     CUtensorMap ta, tb;
-    if ((rc = make_map(&ta, A, g.M, g.K, lda))) return rc;
-    if ((rc = make_map(&tb, B, g.N, g.K, ldb))) return rc;
-    static bool attr_set = false;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
-            cudaSuccess)
-            return HESP_ERR_CUDA;
-        attr_set = true;
+    if ((rc = make_map(&ta, A, g.M, g.K, lda, BM))) return rc;
+    if ((rc = make_map(&tb, B, g.N, g.K, ldb, BN))) return rc;
+    return launch_persistent<0>(ta, tb, tb, g, st);
+}
+
+// C = onehot(levels) . B^T with the one-hot A built in shared memory:
+// A[r, f] = (levels[r * stride + f / NL] == f % NL) for f < n_base * NL, else 0;
+// K = g.K (a multiple of 64, >= n_base * NL); levels 16-byte aligned with a
+// row stride that is a multiple of 16 bytes (TMA reads the level windows).
+int launch_gemm_onehot(const int8_t *levels, int64_t stride, int n_base, int NL, const void *B, int64_t ldb,
+                       const GemmArgs &g0, cudaStream_t st) {
+    if (g0.M < 1 || g0.N < 1 || g0.K < BK || g0.K % BK || (ldb & 7) || ldb < g0.K || !levels || NL < 1 ||
+        NL > 5 || n_base < 1 || (int64_t)n_base * NL > g0.K || stride < n_base || (stride & 15))
+        return HESP_ERR_ARG;
+    if (((uintptr_t)B & 15) || ((uintptr_t)levels & 15)) return HESP_ERR_ARG;
+    int rc = get_encode();
+    if (rc) return rc;
+    CUtensorMap tb, tl;
+    if ((rc = make_map(&tb, B, g0.N, g0.K, ldb, BN))) return rc;
+    if ((rc = make_level_map(&tl, levels, g0.M, n_base, stride))) return rc;
+    GemmArgs g = g0;
+    g.oh_lv = levels;
+    g.oh_stride = stride;
+    g.oh_base = n_base;
+    g.oh_levels = NL;
+    switch (NL) {
+    case 1: return launch_persistent<1>(tb, tb, tl, g, st);
+    case 2: return launch_persistent<2>(tb, tb, tl, g, st);
+    case 3: return launch_persistent<3>(tb, tb, tl, g, st);
+    case 4: return launch_persistent<4>(tb, tb, tl, g, st);
+    default: return launch_persistent<5>(tb, tb, tl, g, st);
     }
-    dim3 grid((unsigned)((g.N + BN - 1) / BN), (unsigned)((g.M + BM - 1) / BM));
-    gemm_bf16_kernel<<<grid, 128, SMEM_BYTES, st>>>(ta, tb, g);
-    return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
 }
 
 }  // namespace hesp

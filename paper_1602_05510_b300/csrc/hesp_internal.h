@@ -128,7 +128,13 @@ struct GemmArgs {
     const __nv_bfloat16 *mask;
     int ldm;
     int *err;
+    // one-hot A operand (launch_gemm_onehot only)
+    const int8_t *oh_lv = nullptr;
+    int64_t oh_stride = 0;
+    int oh_base = 0, oh_levels = 0;
 };
 int launch_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, const GemmArgs &g, cudaStream_t st);
+int launch_gemm_onehot(const int8_t *levels, int64_t stride, int n_base, int NL, const void *B, int64_t ldb,
+                       const GemmArgs &g, cudaStream_t st);
 
 }  // namespace hesp

@@ -5,7 +5,8 @@
 // large proposal sets, whose best slice is re-simulated exactly.
 //
 // Layer math (one batch of B rows):
-//   X   = one_hot(levels)                   [B, Fp]  (F = n_base * n_levels, Fp = F rounded up to 64)
+//   X   = one_hot(levels)                   [B, Fp]  (F = n_base * n_levels, Fp = F rounded up to 64;
+//                                                  built tile by tile inside the layer-1 GEMM)
 //   A1  = bf16(relu(X W1^T + b1))           [B, H]   GEMM epilogue 1 (+ A1^T)
 //   A2  = bf16(relu(A1 W2^T + b2))          [B, H]   GEMM epilogue 1
 //   y   = A2 w3 + b3,  t = (ln makespan - mu) / sigma,  L = mean (y - t)^2
@@ -41,7 +42,9 @@ struct hesp_surrogate {
     // activations for up to max_batch rows
     int8_t *lv;        // gathered levels [B, n_base]
     int64_t *ms;       // gathered makespans [B]
-    __nv_bfloat16 *X, *XT, *A1, *A1T, *A2, *dZ2, *dZ2T, *dZ1, *dZ1T;
+    __nv_bfloat16 *XT, *A1, *A1T, *A2, *dZ2, *dZ2T, *dZ1, *dZ1T;
+    int8_t *lvp;  // levels with rows padded to ldp bytes, for the layer-1 GEMM
+    int64_t ldp;
     float *y, *dy, *loss;
     int32_t *err;
     void *mem;  // one device allocation holding all of the above
@@ -72,29 +75,20 @@ __global__ void to_bf16_kernel(const float *src, __nv_bfloat16 *dst, __nv_bfloat
     }
 }
 
-// X[b, f] = (levels[b, f / NL] == f % NL): one thread writes 8 columns
-// (16 bytes) of one row.
-__global__ void onehot_kernel(const int8_t *lv, int lv_stride, int B, int n_base, int NL, int Fp, __nv_bfloat16 *X) {
-    const int chunks = Fp >> 3;
-    const int64_t total = (int64_t)B * chunks;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int b = (int)(i / chunks), f0 = (int)(i % chunks) << 3;
-        int t = f0 / NL, v = f0 - t * NL;
-        int cur = t < n_base ? lv[(int64_t)b * lv_stride + t] : -1;
-        uint32_t w[4];
-#pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-            uint32_t lo = (cur == v) ? 0x3F80u : 0u;  // bf16 1.0
-            if (++v == NL) { v = 0; ++t; cur = t < n_base ? lv[(int64_t)b * lv_stride + t] : -1; }
-            uint32_t hi = (cur == v) ? 0x3F80u : 0u;
-            if (++v == NL) { v = 0; ++t; cur = t < n_base ? lv[(int64_t)b * lv_stride + t] : -1; }
-            w[q >> 1] = lo | (hi << 16);
-        }
-        *reinterpret_cast<uint4 *>(X + (int64_t)b * Fp + f0) = make_uint4(w[0], w[1], w[2], w[3]);
+// Copy B rows of n_base level bytes (row stride `stride`) into rows of ldp
+// bytes (a multiple of 16), the layout the layer-1 GEMM reads with TMA.
+__global__ void pad_levels_kernel(const int8_t *lv, int64_t stride, int B, int n_base, int ldp, int8_t *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)B * n_base;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / n_base, t = i - b * n_base;
+        out[b * ldp + t] = lv[b * stride + t];
     }
 }
 
-// XT[f, b] = X[b, f]: one thread writes 8 rows-of-b (16 bytes) of one feature.
+// XT[f, b] = X[b, f] = (levels[b, f / NL] == f % NL), the transposed one-hot
+// matrix of the weight-gradient GEMM: one thread writes 8 rows-of-b (16 bytes)
+// of one feature.  (The forward pass never materialises X: layer 1 builds
+// its A tiles from the levels inside the GEMM.)
 __global__ void onehot_t_kernel(const int8_t *lv, int lv_stride, int B, int n_base, int NL, int Fp,
                                 __nv_bfloat16 *XT) {
     const int chunks = B >> 3;
@@ -288,14 +282,38 @@ int forward(hesp_surrogate *s, const int8_t *lv, int B, const int64_t *ms, float
             bool backward) {
     const int H = s->H;
     const int64_t Fp = s->Fp;
-    onehot_kernel<<<grid_for((int64_t)B * (Fp / 8)), 256, 0, st>>>(lv, s->n_base, B, s->n_base, s->n_levels,
-                                                                    (int)Fp, s->X);
     if (backward)
         onehot_t_kernel<<<grid_for((int64_t)Fp * (B / 8)), 256, 0, st>>>(lv, s->n_base, B, s->n_base, s->n_levels,
                                                                           (int)Fp, s->XT);
     CK(cudaGetLastError());
-    RC(gemm(s->X, Fp, s->W1b, Fp, B, H, (int)Fp, 1, nullptr, 0, s->b1, s->A1, H, backward ? s->A1T : nullptr, B,
-            nullptr, 0, s->err, st));
+    {
+        // layer 1: relu(onehot(levels) W1^T + b1), the one-hot operand built inside the GEMM
+        GemmArgs g;
+        g.M = B;
+        g.N = H;
+        g.K = (int)Fp;
+        g.epi = 1;
+        g.C = nullptr;
+        g.ldc = 0;
+        g.bias = s->b1;
+        g.out = s->A1;
+        g.ldo = H;
+        g.out_t = backward ? s->A1T : nullptr;
+        g.ldt = B;
+        g.mask = nullptr;
+        g.ldm = 0;
+        g.err = s->err;
+        const int8_t *lvg = lv;
+        int64_t ld = s->n_base;
+        if ((s->n_base & 15) || ((uintptr_t)lv & 15)) {
+            pad_levels_kernel<<<grid_for((int64_t)B * s->n_base), 256, 0, st>>>(lv, s->n_base, B, (int)s->n_base,
+                                                                                 (int)s->ldp, s->lvp);
+            CK(cudaGetLastError());
+            lvg = s->lvp;
+            ld = s->ldp;
+        }
+        RC(launch_gemm_onehot(lvg, ld, (int)s->n_base, s->n_levels, s->W1b, Fp, g, st));
+    }
     RC(gemm(s->A1, H, s->W2b, H, B, H, H, 1, nullptr, 0, s->b2, s->A2, H, nullptr, 0, nullptr, 0, s->err, st));
     if (backward) CK(cudaMemsetAsync(s->loss, 0, sizeof(float), st));
     l3_kernel<<<(unsigned)((B * 32 + 255) / 256), 256, 0, st>>>(s->A2, H, s->w3, s->b3, B, pred, ms, s->mu, s->sigma,
@@ -361,7 +379,7 @@ int hesp_surrogate_create(int32_t n_base, int32_t n_levels, int32_t hidden, int3
                           hesp_surrogate **out) {
     if (!out) return HESP_ERR_ARG;
     *out = nullptr;
-    if (n_base < 1 || n_levels < 1 || n_levels > 127 || hidden < 64 || hidden % 64 || max_batch < 64 ||
+    if (n_base < 1 || n_levels < 1 || n_levels > HESP_MAX_LEVEL + 1 || hidden < 64 || hidden % 64 || max_batch < 64 ||
         max_batch % 64)
         return HESP_ERR_ARG;
     hesp_surrogate *s = (hesp_surrogate *)calloc(1, sizeof(hesp_surrogate));
@@ -395,7 +413,9 @@ int hesp_surrogate_create(int32_t n_base, int32_t n_levels, int32_t hidden, int3
     const size_t o_loss = take(sizeof(float) + sizeof(int32_t) + 2 * sizeof(double));
     const size_t o_W1b = take(nW1 * 2), o_W2b = take(nW2 * 2), o_W2Tb = take(nW2 * 2);
     const size_t o_lv = take((size_t)B * n_base), o_ms = take(B * 8);
-    const size_t o_X = take((size_t)B * Fp * 2), o_XT = take((size_t)B * Fp * 2);
+    const size_t o_XT = take((size_t)B * Fp * 2);
+    s->ldp = round_up(n_base, 16);
+    const size_t o_lvp = take((size_t)B * s->ldp);
     const size_t o_A1 = take(B * H * 2), o_A1T = take(B * H * 2), o_A2 = take(B * H * 2);
     const size_t o_dZ2 = take(B * H * 2), o_dZ2T = take(B * H * 2), o_dZ1 = take(B * H * 2),
                  o_dZ1T = take(B * H * 2);
@@ -425,8 +445,8 @@ int hesp_surrogate_create(int32_t n_base, int32_t n_levels, int32_t hidden, int3
     s->W2Tb = (__nv_bfloat16 *)(m + o_W2Tb);
     s->lv = (int8_t *)(m + o_lv);
     s->ms = (int64_t *)(m + o_ms);
-    s->X = (__nv_bfloat16 *)(m + o_X);
     s->XT = (__nv_bfloat16 *)(m + o_XT);
+    s->lvp = (int8_t *)(m + o_lvp);
     s->A1 = (__nv_bfloat16 *)(m + o_A1);
     s->A1T = (__nv_bfloat16 *)(m + o_A1T);
     s->A2 = (__nv_bfloat16 *)(m + o_A2);

@@ -296,3 +296,20 @@ def test_policies_parity(order, select):
             a, e = offs[c], offs[c + 1]
             assert np.array_equal(proc[a:e], r["proc"]) and np.array_equal(start[a:e], r["start"]), (key, c)
             assert np.array_equal(fin[a:e], r["finish"]), (key, c)
+
+
+def test_maximum_tiles_and_empty_batch():
+    """The largest matrix the ABI allows (64 x 64 tiles, 45,760 base tasks),
+    unsplit and with some splits, against the oracle; and an empty batch,
+    which launches nothing and succeeds."""
+    nb = W.base_count(hesp.MAX_TILES)
+    lv = np.zeros((2, nb), np.int8)
+    lv[1, ::97] = 1
+    for key in ("cfg1a", "cfg1b"):
+        g = gpu_sim(W.PLATFORMS[key], hesp.MAX_TILES, 512, lv, max_level=1)
+        check_parity(W.PLATFORMS[key], hesp.MAX_TILES, 512, lv, g, schedule=False)
+    plat = hesp.Platform(W.PLATFORMS["cfg0"])
+    ws = hesp.alloc_workspace(plat, 3, 1, 1)
+    empty = torch.empty(0, dtype=torch.int8, device="cuda")
+    ms, st, _ = hesp.simulate_batch(plat, hesp.cands_tensor(3, 1024, np.zeros(0, np.int64)), empty, 0, 3, 1, ws)
+    assert ms.numel() == 0 and st.numel() == 0

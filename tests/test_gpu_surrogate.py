@@ -40,7 +40,7 @@ def batch(rng, B, T, NL):
     return lv, ms
 
 
-SHAPES = [(10, 2, 64, 64), (816, 3, 512, 256), (120, 3, 128, 128)]
+SHAPES = [(10, 2, 64, 64), (816, 3, 512, 256), (120, 3, 128, 128), (40, 4, 128, 128), (33, 5, 64, 128), (20, 1, 64, 64)]
 
 
 @pytest.mark.parametrize("T,NL,H,B", SHAPES)
