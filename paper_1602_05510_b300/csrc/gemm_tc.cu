@@ -16,11 +16,13 @@
 //
 // With NL > 0 the A operand is the one-hot encoding of int8 levels,
 // X[r, f] = (levels[r, f / NL] == f % NL) for f < n_base NL (else 0), and
-// warps 10-13 build its tiles in shared memory (thread r writes row r, eight
-// 16-byte chunks per k-block, in the same swizzled layout), so the one-hot
-// matrix never exists in memory.  A chunk of 8 features starting at phase
-// v0 = f % NL spans at most S tasks; its 16 bytes are read from a table,
-// built once per CTA, indexed by (v0, the S levels).
+// warps 10-17 build its tiles in shared memory (two groups of four taking
+// alternate k-blocks; thread r of a group writes row r, eight 16-byte chunks
+// per k-block, in the same swizzled layout) from level windows that TMA
+// brings with B, so the one-hot matrix never exists in memory.  A chunk of
+// 8 features starting at phase v0 = f % NL spans at most S tasks; its 16
+// bytes are read from a table, built once per CTA, indexed by (v0, the S
+// levels).
 //
 // Every mbarrier wait is bounded: on expiry the role stops, the caller's error
 // flag is raised, and the CTA frees its TMEM and returns.
@@ -42,15 +44,8 @@ namespace {
 constexpr int BM = 128, BN = 256, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;  // 16 KiB
 constexpr int B_BYTES = BN * BK * 2;  // 32 KiB
-constexpr int LV_COLS = 80;           // level window box: 80 bytes x 128 rows (inner start rounded down to 16)
-constexpr int LV_BYTES = BM * LV_COLS;
-constexpr int TABLE_BYTES = 10240;    // one-hot chunk table: NL * NL^S entries of 16 bytes (<= 625 for NL <= 5)
-// per instantiation: TMA A operand (NL = 0), or A built from levels (NL > 0)
-__host__ __device__ constexpr int stages_of(int nl) { return nl > 0 ? 3 : 4; }
-__host__ __device__ constexpr int stage_bytes_of(int nl) { return A_BYTES + B_BYTES + (nl > 0 ? LV_BYTES : 0); }
-__host__ __device__ constexpr int smem_bytes_of(int nl) {
-    return 1024 + stages_of(nl) * stage_bytes_of(nl) + (nl > 0 ? TABLE_BYTES : 0) + 512;
-}
+constexpr int SMEM_LIMIT = 227 * 1024;  // dynamic shared memory of one CTA
+
 constexpr int TMEM_COLS = 2 * BN;  // two accumulators: all of TMEM, one CTA per SM
 constexpr int N_EPI_WARPS = 8;
 constexpr uint32_t kWaitLimit = 1u << 22;
@@ -61,6 +56,27 @@ __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * i
 // level bytes a 64-feature k-block reads (the S tasks from each chunk's first
 // task), in 32-bit words
 __host__ __device__ constexpr int window_words(int nl) { return ((nl - 1 + 56) / nl + span_of(nl) + 3) / 4; }
+// Per instantiation (NL = 0: TMA A operand; NL > 0: A built from levels):
+// the level box width (its start is rounded down to 16 bytes, and the window
+// is read as window_words + 1 words from a 4-byte boundary), the chunk
+// table, the stage size and as many stages (3 or 4) as shared memory holds.
+__host__ __device__ constexpr int lv_cols_of(int nl) {
+    return nl == 0 ? 0 : (12 + 4 * (window_words(nl) + 1) + 15) / 16 * 16;
+}
+__host__ __device__ constexpr int table_bytes_of(int nl) {
+    return nl == 0 ? 0 : (nl * ipow(nl, span_of(nl)) * 16 + 127) / 128 * 128;
+}
+__host__ __device__ constexpr int stage_bytes_of(int nl) { return A_BYTES + B_BYTES + BM * lv_cols_of(nl); }
+__host__ __device__ constexpr int smem_for(int nl, int stages) {
+    return 1024 + stages * stage_bytes_of(nl) + table_bytes_of(nl) + 512;
+}
+__host__ __device__ constexpr int stages_of(int nl) { return smem_for(nl, 4) <= SMEM_LIMIT ? 4 : 3; }
+__host__ __device__ constexpr int smem_bytes_of(int nl) { return smem_for(nl, stages_of(nl)); }
+static_assert(stage_bytes_of(1) % 1024 == 0 && stage_bytes_of(2) % 1024 == 0 && stage_bytes_of(3) % 1024 == 0 &&
+                  stage_bytes_of(4) % 1024 == 0 && stage_bytes_of(5) % 1024 == 0,
+              "stages must keep the 128-byte-swizzled tiles 1024-byte aligned");
+static_assert(smem_bytes_of(0) <= SMEM_LIMIT && smem_bytes_of(1) <= SMEM_LIMIT && smem_bytes_of(5) <= SMEM_LIMIT,
+              "shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -117,6 +133,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+// 16 consecutive accumulator columns of this warp's 32 TMEM lanes; the
+// caller waits (tmem_wait) before reading r.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -124,8 +142,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Epilogue of 16 accumulator columns of one output row.
 __device__ __forceinline__ void epilogue16(const GemmArgs &g, int row, int col0, const uint32_t (&r)[16]) {
@@ -145,10 +163,22 @@ __device__ __forceinline__ void epilogue16(const GemmArgs &g, int row, int col0,
         return;
     }
     if (g.epi == 1) {
+        const float *bp = g.bias + col0;
+        if (full && (((uintptr_t)bp) & 15) == 0) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const float bq = (col0 + q < g.N) ? g.bias[col0 + q] : 0.f;
-            v[q] = fmaxf(v[q] + bq, 0.f);
+            for (int q = 0; q < 16; q += 4) {
+                const float4 b4 = __ldg(reinterpret_cast<const float4 *>(bp + q));
+                v[q] = fmaxf(v[q] + b4.x, 0.f);
+                v[q + 1] = fmaxf(v[q + 1] + b4.y, 0.f);
+                v[q + 2] = fmaxf(v[q + 2] + b4.z, 0.f);
+                v[q + 3] = fmaxf(v[q + 3] + b4.w, 0.f);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float bq = (col0 + q < g.N) ? bp[q] : 0.f;
+                v[q] = fmaxf(v[q] + bq, 0.f);
+            }
         }
     } else {
         const __nv_bfloat16 *mk = g.mask + (int64_t)row * g.ldm + col0;
@@ -216,8 +246,10 @@ __device__ __forceinline__ void onehot_kblock(const uint32_t (&w)[WW], const uin
     }
 }
 
+constexpr int N_PROD_GROUPS = 2;  // A-producer groups of 4 warps, taking alternate k-blocks
+
 template <int NL>
-__global__ void __launch_bounds__(NL > 0 ? 448 : 320, 1)
+__global__ void __launch_bounds__(NL > 0 ? 320 + 128 * N_PROD_GROUPS : 320, 1)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmL, GemmArgs g) {
     constexpr int STAGES = stages_of(NL), STAGE_BYTES = stage_bytes_of(NL);
@@ -225,7 +257,7 @@ __global__ void __launch_bounds__(NL > 0 ? 448 : 320, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint4 *table = (uint4 *)(smem + STAGES * STAGE_BYTES);
-    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES + (NL > 0 ? TABLE_BYTES : 0));
+    uint64_t *bars = (uint64_t *)(smem + STAGES * STAGE_BYTES + table_bytes_of(NL));
     uint32_t *holder = (uint32_t *)(bars + NBARS);
     // full: the stage is ready for the MMA; empty: the MMA is done with it;
     // lfull (NL > 0): B and the level window have landed; tfull / tempty: an
@@ -239,7 +271,7 @@ __global__ void __launch_bounds__(NL > 0 ? 448 : 320, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full0 + 8 * s, NL > 0 ? 4 : 1);  // one lane per A-producer warp, or the TMA thread
+            mbar_init(full0 + 8 * s, NL > 0 ? 4 : 1);  // one lane per warp of the producer group, or the TMA thread
             mbar_init(empty0 + 8 * s, 1);
             mbar_init(lfull0 + 8 * s, 1);
         }
@@ -281,7 +313,7 @@ __global__ void __launch_bounds__(NL > 0 ? 448 : 320, 1)
                     } else {
                         // tasks from t_kb on; the box starts at t_kb rounded down to 16 bytes
                         const int t_kb = (kt * BK) / NL;
-                        mbar_expect_tx(lfull0 + 8 * s, B_BYTES + LV_BYTES);
+                        mbar_expect_tx(lfull0 + 8 * s, B_BYTES + BM * lv_cols_of(NL));
                         tma_load_2d(sa + A_BYTES, &tmB, lfull0 + 8 * s, kt * BK, n0);
                         tma_load_2d(sa + A_BYTES + B_BYTES, &tmL, lfull0 + 8 * s, t_kb & ~15, m0);
                     }
@@ -348,26 +380,33 @@ __global__ void __launch_bounds__(NL > 0 ? 448 : 320, 1)
             const int m0 = (tile / nN) * BM, n0 = (tile % nN) * BN;
             const int row = m0 + wq * 32 + lane;
             const bool rok = row < g.M;
-            for (int c0 = h * 128; c0 < h * 128 + 128; c0 += 16) {
-                uint32_t r[16];
-                tmem_ld16(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(acc_i * BN + c0), r);
-                if (rok && n0 + c0 < g.N) epilogue16(g, row, n0 + c0, r);
+            const uint32_t tbase = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(acc_i * BN);
+            for (int c0 = h * 128; c0 < h * 128 + 128; c0 += 32) {  // two loads in flight per wait
+                uint32_t r0[16], r1[16];
+                tmem_ld16(tbase + (uint32_t)c0, r0);
+                tmem_ld16(tbase + (uint32_t)(c0 + 16), r1);
+                tmem_wait();
+                if (rok && n0 + c0 < g.N) epilogue16(g, row, n0 + c0, r0);
+                if (rok && n0 + c0 + 16 < g.N) epilogue16(g, row, n0 + c0 + 16, r1);
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty0 + 8 * acc_i);
         }
     } else if constexpr (NL > 0) {
-        // A producers (warps 10-13): the chunk table, then for each k-block,
-        // once B and the level window have landed, thread r builds row r of
-        // the A tile from its window, with byte positions fixed by the
-        // k-block's phase.  The only barrier across the four warps is the one
-        // after the table is built, before any wait that can time out.
+        // A producers (warps 10 on, two groups of four taking alternate
+        // k-blocks): the chunk table, then for each of the group's k-blocks,
+        // once B and the level window have landed, thread r of the group
+        // builds row r of the A tile from its window, with byte positions
+        // fixed by the k-block's phase.  The only barrier across the producer
+        // warps is the one after the table is built, before any wait that can
+        // time out.
         constexpr int S = span_of(NL);
         constexpr int NE = NL * ipow(NL, S);
         constexpr int WW = window_words(NL);
-        const int tid = threadIdx.x - 32 * (2 + N_EPI_WARPS);
-        for (int e = tid; e < NE; e += 128) {
+        const int ptid = threadIdx.x - 32 * (2 + N_EPI_WARPS);
+        const int grp = ptid >> 7, tid = ptid & 127;
+        for (int e = ptid; e < NE; e += 128 * N_PROD_GROUPS) {
             int rem = e, lv_[S];
 #pragma unroll
             for (int i = S - 1; i >= 0; --i) {
@@ -385,12 +424,13 @@ __global__ void __launch_bounds__(NL > 0 ? 448 : 320, 1)
             }
             table[e] = make_uint4(w[0], w[1], w[2], w[3]);
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");  // the four producer warps
+        asm volatile("bar.sync 1, %0;" ::"n"(128 * N_PROD_GROUPS) : "memory");  // the producer warps
         const int r = tid;
         const int nb = g.oh_base;
         int it = 0;
         for (int tile = blockIdx.x; tile < n_tiles && !fail; tile += gridDim.x) {
             for (int kt = 0; kt < KT; ++kt, ++it) {
+                if ((it % N_PROD_GROUPS) != grp) continue;
                 const int s = it % STAGES, q = it / STAGES;
                 if (!__all_sync(0xFFFFFFFFu, mbar_wait(lfull0 + 8 * s, q & 1))) {
                     fail = true;
@@ -399,7 +439,7 @@ __global__ void __launch_bounds__(NL > 0 ? 448 : 320, 1)
                 const int t_kb = (kt * BK) / NL, v_kb = kt * BK - t_kb * NL;
                 const int o = t_kb & 15;  // window start inside the 16-byte aligned box
                 const uint32_t *lrow =
-                    (const uint32_t *)(smem + s * STAGE_BYTES + A_BYTES + B_BYTES + r * LV_COLS) + (o >> 2);
+                    (const uint32_t *)(smem + s * STAGE_BYTES + A_BYTES + B_BYTES + r * lv_cols_of(NL)) + (o >> 2);
                 uint32_t win[WW];
                 uint32_t prev = lrow[0];
 #pragma unroll
@@ -461,12 +501,12 @@ int make_map(CUtensorMap *tm, const void *ptr, int64_t rows, int64_t cols, int64
     return r == CUDA_SUCCESS ? HESP_OK : HESP_ERR_ARG;
 }
 
-// Tensor map of int8 levels [rows, ld bytes] read in 128-row x LV_COLS-byte
+// Tensor map of int8 levels [rows, ld bytes] read in 128-row x box_cols-byte
 // boxes (ld a multiple of 16; bytes past n_base read as 0).
-int make_level_map(CUtensorMap *tm, const int8_t *ptr, int64_t rows, int64_t n_base, int64_t ld) {
+int make_level_map(CUtensorMap *tm, const int8_t *ptr, int64_t rows, int64_t n_base, int64_t ld, int box_cols) {
     cuuint64_t dims[2] = {(cuuint64_t)n_base, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)ld};
-    cuuint32_t box[2] = {LV_COLS, BM};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, BM};
     cuuint32_t estr[2] = {1, 1};
     const CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<int8_t *>(ptr), dims, strides, box,
                                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -498,7 +538,7 @@ int launch_persistent(const CUtensorMap &ta, const CUtensorMap &tb, const CUtens
     }
     const int64_t tiles = (int64_t)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
     const int64_t grid = tiles < sm_count() ? tiles : sm_count();
-    gemm_bf16_kernel<NL><<<(unsigned)grid, NL > 0 ? 448 : 320, SMEM, st>>>(ta, tb, tl, g);
+    gemm_bf16_kernel<NL><<<(unsigned)grid, NL > 0 ? 320 + 128 * N_PROD_GROUPS : 320, SMEM, st>>>(ta, tb, tl, g);
     return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
 }
 
@@ -532,7 +572,7 @@ int launch_gemm_onehot(const int8_t *levels, int64_t stride, int n_base, int NL,
     if (rc) return rc;
     CUtensorMap tb, tl;
     if ((rc = make_map(&tb, B, g0.N, g0.K, ldb, BN))) return rc;
-    if ((rc = make_level_map(&tl, levels, g0.M, n_base, stride))) return rc;
+    if ((rc = make_level_map(&tl, levels, g0.M, n_base, stride, lv_cols_of(NL)))) return rc;
     GemmArgs g = g0;
     g.oh_lv = levels;
     g.oh_stride = stride;
