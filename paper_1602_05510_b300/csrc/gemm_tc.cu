@@ -145,7 +145,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 __device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Epilogue of 16 accumulator columns of one output row.
+// bf16 bits of x, round to nearest even
+__device__ __forceinline__ uint32_t bf16_bits(float x) { return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+
+// Epilogue of 16 accumulator columns of one output row.  Every index is a
+// compile-time constant, so the values stay in registers.
 __device__ __forceinline__ void epilogue16(const GemmArgs &g, int row, int col0, const uint32_t (&r)[16]) {
     float v[16];
 #pragma unroll
@@ -158,7 +162,9 @@ __device__ __forceinline__ void epilogue16(const GemmArgs &g, int row, int col0,
             for (int q = 0; q < 16; q += 4)
                 *reinterpret_cast<float4 *>(dst + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
         } else {
-            for (int q = 0; q < 16 && col0 + q < g.N; ++q) dst[q] = v[q];
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (col0 + q < g.N) dst[q] = v[q];
         }
         return;
     }
@@ -186,18 +192,24 @@ __device__ __forceinline__ void epilogue16(const GemmArgs &g, int row, int col0,
         for (int q = 0; q < 16; ++q)
             if (col0 + q < g.N && !(__bfloat162float(mk[q]) > 0.f)) v[q] = 0.f;
     }
-    __nv_bfloat16 h[16];
+    uint32_t w[8];  // bf16 pairs
 #pragma unroll
-    for (int q = 0; q < 16; ++q) h[q] = __float2bfloat16_rn(v[q]);
+    for (int q = 0; q < 8; ++q) w[q] = bf16_bits(v[2 * q]) | (bf16_bits(v[2 * q + 1]) << 16);
     __nv_bfloat16 *dst = g.out + (int64_t)row * g.ldo + col0;
     if (full && (((uintptr_t)dst) & 15) == 0) {
-        *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(h);
-        *reinterpret_cast<uint4 *>(dst + 8) = *reinterpret_cast<const uint4 *>(h + 8);
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(dst + 8) = make_uint4(w[4], w[5], w[6], w[7]);
     } else {
-        for (int q = 0; q < 16 && col0 + q < g.N; ++q) dst[q] = h[q];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (col0 + q < g.N) dst[q] = __ushort_as_bfloat16((unsigned short)(w[q >> 1] >> (16 * (q & 1))));
     }
     if (g.out_t) {
-        for (int q = 0; q < 16 && col0 + q < g.N; ++q) g.out_t[(int64_t)(col0 + q) * g.ldt + row] = h[q];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (col0 + q < g.N)
+                g.out_t[(int64_t)(col0 + q) * g.ldt + row] =
+                    __ushort_as_bfloat16((unsigned short)(w[q >> 1] >> (16 * (q & 1))));
     }
 }
 
