@@ -126,6 +126,7 @@ def run_gpu(args):
     import torch.distributed as dist
 
     from paper_1602_05510_b300 import build, hesp
+    from paper_1602_05510_b300.sharding import rank_first, reduce_timing
 
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
@@ -138,7 +139,6 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     nb = W.base_count(N_TILES)
     C = args.candidates
-    first0 = rank * C
 
     plats = [hesp.Platform(W.PLATFORMS[k]) for k in PLATS]
     ws = [hesp.alloc_workspace(p, N_TILES, MAX_LEVEL, C) for p in plats]
@@ -148,19 +148,26 @@ def run_gpu(args):
     stt = [torch.empty(C, dtype=torch.int32, device=dev) for _ in plats]
     nts = [torch.empty(C, dtype=torch.int64, device=dev) for _ in plats]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+    # largest DAG first (LPT): the persistent kernel's tail is then the smallest candidates
+    scands = torch.empty(C * 16, dtype=torch.uint8, device=dev)
+    perm = torch.empty(C, dtype=torch.int32, device=dev)
+    sort_ws = hesp.sort_workspace(C, dev)
 
     def step(first, ev=None):
         hesp.generate_candidates(hesp.GEN_UNIFORM, WORKLOAD.seed, first, C, N_TILES, B, N_LEVELS, levels, cands)
+        sim_c = cands
+        if args.lpt:
+            sim_c, _ = hesp.sort_cands_by_size(cands, levels, C, scands, perm, sort_ws)
         for i, p in enumerate(plats):
             if ev is not None:
                 ev[i][0].record(stream)
-            hesp.simulate_batch(p, cands, levels, C, N_TILES, MAX_LEVEL, ws[i], makespan=ms[i], status=stt[i],
+            hesp.simulate_batch(p, sim_c, levels, C, N_TILES, MAX_LEVEL, ws[i], makespan=ms[i], status=stt[i],
                                 ntasks=nts[i])
             if ev is not None:
                 ev[i][1].record(stream)
 
     for w in range(args.warmup):
-        step(first0 + w * world * C)
+        step(rank_first(rank, world, C, w))
     torch.cuda.synchronize()
     for i in range(len(plats)):
         bad = int((stt[i] != 0).sum().item())
@@ -182,7 +189,7 @@ def run_gpu(args):
     for k in range(K):
         flush.fill_(k & 0xFF)  # evict L2 between timed steps (outside the step's events)
         step_ev[k][0].record(stream)
-        step(first0 + (args.warmup + k) * world * C, kern_ev[k])
+        step(rank_first(rank, world, C, args.warmup + k), kern_ev[k])
         step_ev[k][1].record(stream)
         for i in range(len(plats)):
             task_events += nts[i].sum()  # device-side accumulation, read after the loop
@@ -195,21 +202,14 @@ def run_gpu(args):
             raise RuntimeError("candidates failed on %s" % PLATS[i])
     t_steps = sum(step_ev[k][0].elapsed_time(step_ev[k][1]) for k in range(K)) / 1e3
     t_kern = [sum(kern_ev[k][i][0].elapsed_time(kern_ev[k][i][1]) for k in range(K)) / 1e3 for i in range(len(plats))]
-    t_max = t_steps
-    tot_events = task_events
-    if world > 1:
-        tt = torch.tensor([t_steps], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        ev = torch.tensor([task_events], dtype=torch.int64, device=dev)
-        dist.all_reduce(ev, op=dist.ReduceOp.SUM)
-        tot_events = int(ev.item())
+    t_max, tot_events = reduce_timing(t_steps, task_events, world, dev)
 
     # ---- end to end through the public API with host buffers
     e2e = None
     if args.e2e_steps > 0:
-        lv_host = [torch.from_numpy(W.uniform_levels(WORKLOAD.seed, first0 + (1000 + s) * C, C, nb, N_LEVELS)
-                                    .reshape(-1)).pin_memory() for s in range(min(args.e2e_steps, 2))]
+        lv_host = [torch.from_numpy(W.uniform_levels(WORKLOAD.seed, rank_first(rank, world, C, 1000 + s), C, nb,
+                                                     N_LEVELS).reshape(-1)).pin_memory()
+                   for s in range(min(args.e2e_steps, 2))]
         cand_host = hesp.cands_tensor(N_TILES, B, np.arange(C, dtype=np.int64) * nb, device="cpu").pin_memory()
         out_host = [torch.empty(C, dtype=torch.int64).pin_memory() for _ in plats]
         e2e_ev = []
@@ -223,8 +223,9 @@ def run_gpu(args):
             a.record(stream)
             levels.copy_(lv_host[s % len(lv_host)], non_blocking=True)
             cands.copy_(cand_host, non_blocking=True)
+            sim_c = hesp.sort_cands_by_size(cands, levels, C, scands, perm, sort_ws)[0] if args.lpt else cands
             for i, p in enumerate(plats):
-                hesp.simulate_batch(p, cands, levels, C, N_TILES, MAX_LEVEL, ws[i], makespan=ms[i], status=stt[i],
+                hesp.simulate_batch(p, sim_c, levels, C, N_TILES, MAX_LEVEL, ws[i], makespan=ms[i], status=stt[i],
                                     ntasks=nts[i])
                 out_host[i].copy_(ms[i], non_blocking=True)
             b_.record(stream)
@@ -234,16 +235,10 @@ def run_gpu(args):
         torch.cuda.synchronize()
         t_e2e = sum(a.elapsed_time(b_) for a, b_ in e2e_ev) / 1e3
         e2e_tasks = int(e2e_tasks.item())
-        if world > 1:
-            tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = float(tt.item())
-            ev = torch.tensor([e2e_tasks], dtype=torch.int64, device=dev)
-            dist.all_reduce(ev, op=dist.ReduceOp.SUM)
-            e2e_tasks = int(ev.item())
+        t_e2e, e2e_tasks = reduce_timing(t_e2e, e2e_tasks, world, dev)
         e2e = {"value": e2e_tasks / t_e2e, "unit": UNIT, "h2d_bytes_per_step": C * nb + C * 16,
                "d2h_bytes_per_step": 8 * C * len(plats), "steps": args.e2e_steps,
-               "path": "pinned host partition vectors -> hesp_simulate_batch x2 -> host makespans"}
+               "path": "pinned host partition vectors -> largest-first order -> hesp_simulate_batch x2 -> host makespans"}
 
     if rank == 0:
         peaks = measured_peaks()
@@ -258,7 +253,7 @@ def run_gpu(args):
             "candidates_per_s": 2 * C * world * K / t_max if t_max > 0 else None,
             "task_events": tot_events,
             "wall_s": wall,
-            "gpu_launches": 3 * K,
+            "gpu_launches": (6 if args.lpt else 3) * K,  # generation, [3 sort kernels,] 2 simulations
             "clocks": clk,
             "e2e": e2e,
         }
@@ -664,6 +659,8 @@ def main():
     ap.add_argument("--impl", default="hesp", choices=["hesp", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-lpt", dest="lpt", action="store_false",
+                    help="simulate candidates in generation order instead of largest DAG first")
     ap.add_argument("--cpu-sample", type=int, default=65536)
     ap.add_argument("--ref-sample", type=int, default=256)
     ap.add_argument("--candidates", type=int, default=N_CAND,

@@ -589,6 +589,14 @@ def autotune(platform, cands, levels, n_sample, max_tiles, max_level, workspace,
     return (c.value, b.value), times.tolist()
 
 
+def sort_workspace(n_cand, device="cuda"):
+    """Device workspace for sort_cands_by_size of up to n_cand candidates."""
+    import torch
+    sz = ctypes.c_size_t()
+    check(lib().hesp_sort_cands_workspace_size(n_cand, ctypes.byref(sz)), "hesp_sort_cands_workspace_size")
+    return torch.empty(sz.value, dtype=torch.uint8, device=device)
+
+
 def sort_cands_by_size(cands, levels, n_cand, sorted_cands=None, perm=None, ws=None, stream=None):
     """Candidates reordered largest DAG first; returns (sorted_cands, perm)."""
     import torch
