@@ -141,7 +141,20 @@ def run_gpu(args):
     C = args.candidates
 
     plats = [hesp.Platform(W.PLATFORMS[k]) for k in PLATS]
-    ws = [hesp.alloc_workspace(p, N_TILES, MAX_LEVEL, C) for p in plats]
+    if args.share_dag:
+        # one arena per candidate: the first platform's launch builds and keeps
+        # each DAG, the second simulates the kept DAGs
+        kept = hesp.alloc_workspace_kept(N_TILES, MAX_LEVEL, C)
+        ws = [kept for _ in plats]
+    else:
+        ws = [hesp.alloc_workspace(p, N_TILES, MAX_LEVEL, C) for p in plats]
+
+    def simulate(i, p, cands_, levels_):
+        if not args.share_dag:
+            f = hesp.simulate_batch
+        else:
+            f = hesp.simulate_batch_keep if i == 0 else hesp.simulate_batch_reuse
+        f(p, cands_, levels_, C, N_TILES, MAX_LEVEL, ws[i], makespan=ms[i], status=stt[i], ntasks=nts[i])
     levels = torch.empty(C * nb, dtype=torch.int8, device=dev)
     cands = torch.empty(C * 16, dtype=torch.uint8, device=dev)
     ms = [torch.empty(C, dtype=torch.int64, device=dev) for _ in plats]
@@ -161,8 +174,7 @@ def run_gpu(args):
         for i, p in enumerate(plats):
             if ev is not None:
                 ev[i][0].record(stream)
-            hesp.simulate_batch(p, sim_c, levels, C, N_TILES, MAX_LEVEL, ws[i], makespan=ms[i], status=stt[i],
-                                ntasks=nts[i])
+            simulate(i, p, sim_c, levels)
             if ev is not None:
                 ev[i][1].record(stream)
 
@@ -225,8 +237,7 @@ def run_gpu(args):
             cands.copy_(cand_host, non_blocking=True)
             sim_c = hesp.sort_cands_by_size(cands, levels, C, scands, perm, sort_ws)[0] if args.lpt else cands
             for i, p in enumerate(plats):
-                hesp.simulate_batch(p, sim_c, levels, C, N_TILES, MAX_LEVEL, ws[i], makespan=ms[i], status=stt[i],
-                                    ntasks=nts[i])
+                simulate(i, p, sim_c, levels)
                 out_host[i].copy_(ms[i], non_blocking=True)
             b_.record(stream)
             e2e_ev.append((a, b_))
@@ -249,6 +260,9 @@ def run_gpu(args):
             "data": "synthetic (seeded SplitMix64 partition vectors generated on the device)",
             "config": dict(CONFIG, candidates_per_step=C,
                            parallelism="candidates sharded across ranks (dp%d)" % world,
+                           dag=("built once per candidate (first platform's launch keeps it, the second "
+                                "simulates it)") if args.share_dag else "built in each platform's launch",
+                           order="largest DAG first" if args.lpt else "generation order",
                            l2="256 MB buffer written between timed steps; per-step working set ~GBs > L2"),
             "candidates_per_s": 2 * C * world * K / t_max if t_max > 0 else None,
             "task_events": tot_events,
@@ -659,6 +673,8 @@ def main():
     ap.add_argument("--impl", default="hesp", choices=["hesp", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-share-dag", dest="share_dag", action="store_false",
+                    help="build each candidate's DAG in both platform launches instead of once")
     ap.add_argument("--no-lpt", dest="lpt", action="store_false",
                     help="simulate candidates in generation order instead of largest DAG first")
     ap.add_argument("--cpu-sample", type=int, default=65536)

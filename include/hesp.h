@@ -231,6 +231,34 @@ int hesp_schedule_metrics(const hesp_cand *cands_dev, const int8_t *levels_dev, 
                           int64_t *busy_dev, int64_t *ntasks_dev, int64_t *sum_block_dev, int32_t *depth_dev,
                           void *stream);
 
+/* Several platforms, one DAG build.  A candidate's DAG (tasks, dependences)
+ * depends only on its partition, so simulating the same candidates on
+ * several platforms (or scheduling policies) need not expand and analyse
+ * them again: hesp_simulate_batch_keep simulates like hesp_simulate_batch
+ * and keeps each candidate's DAG in its own arena of the workspace;
+ * hesp_simulate_batch_reuse then simulates the candidates on another
+ * platform from the kept DAGs.  Results equal hesp_simulate_batch's.
+ *   - The workspace holds one arena per candidate (n_cand arenas, laid out
+ *     for HESP_MAX_MEMS memories whatever the platform): size it with
+ *     hesp_sim_workspace_size_kept; ERR_ARG if it is smaller.
+ *   - A reuse call must pass the same cands_dev (same order), levels,
+ *     max_tiles, max_level and task_cap as the keep call whose DAGs are in
+ *     the workspace; each arena records the layout and a hash of its
+ *     candidate's (n_tiles, b, levels), and a candidate whose record does
+ *     not match gets HESP_ERR_STATE (a candidate whose build failed gets the
+ *     build's status).
+ *   - Any number of reuse calls may follow one keep call. */
+int hesp_sim_workspace_size_kept(int32_t max_tiles, int32_t max_level, int64_t task_cap, int64_t n_cand,
+                                 size_t *bytes_out);
+int hesp_simulate_batch_keep(const hesp_platform *p, const hesp_cand *cands_dev, const int8_t *levels_dev,
+                             int64_t n_cand, int32_t max_tiles, int32_t max_level, int64_t task_cap,
+                             int64_t *makespan_dev, int32_t *status_dev, int64_t *ntasks_dev, void *workspace_dev,
+                             size_t workspace_bytes, void *stream);
+int hesp_simulate_batch_reuse(const hesp_platform *p, const hesp_cand *cands_dev, const int8_t *levels_dev,
+                              int64_t n_cand, int32_t max_tiles, int32_t max_level, int64_t task_cap,
+                              int64_t *makespan_dev, int32_t *status_dev, int64_t *ntasks_dev, void *workspace_dev,
+                              size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------------ iterative partition solver
  * HeSP's iterative solver (Sec. 2.1 "Iterative solver"): each iteration is a
  * schedule stage (simulate the partition) and a partition stage (list

@@ -52,6 +52,8 @@ Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem, int64_t ta
     a.off_bitmap = o; o = align256(o + 4 * ((a.Tcap + 31) / 32));
     a.off_xt = o; o = align256(o + 8 * a.Kcap);
     a.off_hist = o; o = align256(o + 4 * 256);  // radix histogram of the priority-list sort
+    a.off_pend0 = o; o = align256(o + 2 * a.Tcap);  // keep / reuse: the DAG's initial pending counts
+    a.off_hdr = o; o = align256(o + 64);            // keep / reuse: the candidate's header
     a.slot_bytes = o;
     return a;
 }
@@ -351,7 +353,42 @@ int simulate_common(const hesp_platform *p, const hesp_cand *cands, const int8_t
     if (slots > n_cand) slots = n_cand;
     const DevPlatform dp = dev_platform(p);
     return launch_sim(p, dp, ar, slots, cands, levels, n_cand, max_tiles, max_level, makespan, status, ntasks,
-                      sched_off, sproc, sstart, sfinish, crit, (char *)ws, (cudaStream_t)stream);
+                      sched_off, sproc, sstart, sfinish, crit, 0, 0, (char *)ws, (cudaStream_t)stream);
+}
+
+// Layout signature of keep / reuse arenas: their layout fields, mixed.
+uint64_t layout_signature(const Arena &ar, int32_t max_tiles, int32_t max_level) {
+    const uint64_t f[8] = {(uint64_t)ar.slot_bytes, (uint64_t)ar.Tcap, (uint64_t)ar.Ecap, (uint64_t)ar.Acap,
+                           (uint64_t)ar.off_pend0, (uint64_t)ar.off_hdr, (uint64_t)max_tiles, (uint64_t)max_level};
+    uint64_t h = 0x8C6B0F2D1E3A5947ull;
+    for (int i = 0; i < 8; ++i) {
+        h ^= f[i] + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+    }
+    return h | 1;  // never 0, so a zeroed arena never matches
+}
+
+// Keep (dag_mode 1) and reuse (dag_mode 2): one arena per candidate, laid
+// out for the largest memory count so every platform uses the same offsets.
+int simulate_kept(const hesp_platform *p, const hesp_cand *cands, const int8_t *levels, int64_t n_cand,
+                  int32_t max_tiles, int32_t max_level, int64_t task_cap, int64_t *makespan, int32_t *status,
+                  int64_t *ntasks, int dag_mode, void *ws, size_t ws_bytes, void *stream) {
+    if (!p || n_cand < 0 || task_cap < 0) return HESP_ERR_ARG;
+    if (n_cand == 0) return HESP_OK;
+    if (!cands || !levels || !makespan || !status || !ws) return HESP_ERR_ARG;
+    if (((uintptr_t)ws & 255) != 0) return HESP_ERR_ARG;
+    if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_level < 0 || max_level > HESP_MAX_LEVEL)
+        return HESP_ERR_UNSUPPORTED;
+    const Arena ar = make_arena(max_tiles, max_level, HESP_MAX_MEMS, task_cap);
+    if ((int64_t)ws_bytes < kWsHeaderBytes || ((int64_t)ws_bytes - kWsHeaderBytes) / ar.slot_bytes < n_cand)
+        return HESP_ERR_ARG;
+    int64_t resident = 0;
+    int rc = sim_slots_for(p, ar, &resident);
+    if (rc) return rc;
+    const int64_t warps = resident < n_cand ? resident : n_cand;
+    const DevPlatform dp = dev_platform(p);
+    return launch_sim(p, dp, ar, warps, cands, levels, n_cand, max_tiles, max_level, makespan, status, ntasks,
+                      nullptr, nullptr, nullptr, nullptr, nullptr, dag_mode, layout_signature(ar, max_tiles, max_level),
+                      (char *)ws, (cudaStream_t)stream);
 }
 
 }  // namespace
@@ -375,6 +412,30 @@ int hesp_schedule_metrics(const hesp_cand *cands, const int8_t *levels, int64_t 
     if (any_s && !(sched_off && start && finish)) return HESP_ERR_ARG;
     return launch_metrics(cands, levels, n_cand, sched_off, start, finish, busy, ntasks, sum_block, depth,
                           (cudaStream_t)stream);
+}
+
+int hesp_sim_workspace_size_kept(int32_t max_tiles, int32_t max_level, int64_t task_cap, int64_t n_cand,
+                                 size_t *bytes_out) {
+    if (!bytes_out || n_cand < 0 || task_cap < 0) return HESP_ERR_ARG;
+    if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_level < 0 || max_level > HESP_MAX_LEVEL)
+        return HESP_ERR_UNSUPPORTED;
+    const Arena ar = make_arena(max_tiles, max_level, HESP_MAX_MEMS, task_cap);
+    *bytes_out = (size_t)(kWsHeaderBytes + n_cand * ar.slot_bytes);
+    return HESP_OK;
+}
+
+int hesp_simulate_batch_keep(const hesp_platform *p, const hesp_cand *cands, const int8_t *levels, int64_t n_cand,
+                             int32_t max_tiles, int32_t max_level, int64_t task_cap, int64_t *makespan,
+                             int32_t *status, int64_t *ntasks, void *ws, size_t ws_bytes, void *stream) {
+    return simulate_kept(p, cands, levels, n_cand, max_tiles, max_level, task_cap, makespan, status, ntasks, 1, ws,
+                         ws_bytes, stream);
+}
+
+int hesp_simulate_batch_reuse(const hesp_platform *p, const hesp_cand *cands, const int8_t *levels, int64_t n_cand,
+                              int32_t max_tiles, int32_t max_level, int64_t task_cap, int64_t *makespan,
+                              int32_t *status, int64_t *ntasks, void *ws, size_t ws_bytes, void *stream) {
+    return simulate_kept(p, cands, levels, n_cand, max_tiles, max_level, task_cap, makespan, status, ntasks, 2, ws,
+                         ws_bytes, stream);
 }
 
 int hesp_simulate_critical(const hesp_platform *p, const hesp_cand *cands, const int8_t *levels, int64_t n_cand,

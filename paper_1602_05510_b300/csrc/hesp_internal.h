@@ -78,7 +78,7 @@ struct Arena {
     // link area and the per-task marks in the successor offsets: neither is
     // in use at the same time as what it shares memory with.
     int64_t off_desc, off_pending, off_link, off_next, off_succoff, off_succ, off_epred, off_esucc, off_lw,
-        off_vfrom, off_bitmap, off_xt, off_hist;
+        off_vfrom, off_bitmap, off_xt, off_hist, off_pend0, off_hdr;
 };
 
 // Header at the start of the workspace.
@@ -97,7 +97,8 @@ int sim_slots_for(const hesp_platform *p, const Arena &ar, int64_t *resident_war
 int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, int64_t n_slots,
                const hesp_cand *cands, const int8_t *levels, int64_t n_cand, int32_t max_tiles, int32_t max_level,
                int64_t *makespan, int32_t *status, int64_t *ntasks, const int64_t *sched_off, int16_t *sproc,
-               int64_t *sstart, int64_t *sfinish, int8_t *crit, char *ws, cudaStream_t stream);
+               int64_t *sstart, int64_t *sfinish, int8_t *crit, int dag_mode, uint64_t layout_sig, char *ws,
+               cudaStream_t stream);
 int sim_kernel_occupancy(int n_mem, int n_procs, int64_t Tcap, int *blocks_per_sm, int *threads_per_block);
 int launch_metrics(const hesp_cand *cands, const int8_t *levels, int64_t n_cand, const int64_t *sched_off,
                    const int64_t *start, const int64_t *finish, int64_t *busy, int64_t *ntasks, int64_t *sum_block,

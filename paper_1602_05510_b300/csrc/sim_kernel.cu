@@ -236,6 +236,10 @@ struct KArgs {
     int64_t *sstart, *sfinish;
     char *ws;
     int8_t *crit;  // optional: per base task, 1 if one of its tasks is on the critical path
+    // 0: arenas per warp; 1 (keep): one arena per candidate, whose DAG is kept
+    // for later launches; 2 (reuse): simulate the DAG a keep launch left there
+    int32_t dag_mode;
+    uint64_t layout_sig;  // identifies the arena layout of keep / reuse launches
     Arena ar;
     int64_t n_slots;
     int32_t bm_smem_words;  // > 0: the released-task bitmap lives in shared memory
@@ -245,6 +249,15 @@ template <typename T>
 __device__ __forceinline__ T *at(char *base, int64_t off) {
     return reinterpret_cast<T *>(base + off);
 }
+
+// Header of a candidate arena whose DAG is kept (keep / reuse launches).
+struct KeptHeader {
+    uint64_t sig;     // arena layout
+    uint64_t lvhash;  // hash of the candidate (n, b, levels)
+    int64_t T, E;     // tasks, dependence edges
+    int32_t status;   // of the DAG build
+    int32_t pad;
+};
 
 // Coherence state of one atom: for each memory the time from which its copy
 // is usable there, or -1 if the memory holds no valid copy.  Stored as MP
@@ -536,9 +549,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
     const int lane = threadIdx.x & 31;
     const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (slot >= a.n_slots) return;  // whole warp
-    char *const base = a.ws + slot * a.ar.slot_bytes;
-    uint32_t *const bm = a.bm_smem_words > 0 ? s_bitmap + (threadIdx.x >> 5) * a.bm_smem_words
-                                             : at<uint32_t>(base, a.ar.off_bitmap);
+    char *const slot_base = a.ws + slot * a.ar.slot_bytes;
     constexpr int MP = AtomState<M>::MP;
 
     int pm[NS], pt[NS];
@@ -558,6 +569,10 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
         if ((int64_t)cl >= a.n_cand) break;
         const int64_t c = (int64_t)cl;
 
+        // keep / reuse launches address one arena per candidate
+        char *const base = a.dag_mode ? a.ws + c * a.ar.slot_bytes : slot_base;
+        uint32_t *const bm = a.bm_smem_words > 0 ? s_bitmap + (threadIdx.x >> 5) * a.bm_smem_words
+                                                 : at<uint32_t>(base, a.ar.off_bitmap);
         const hesp_cand cd = a.cands[c];
         const int n = cd.n_tiles;
         const int b = cd.b;
@@ -570,10 +585,17 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
         const int64_t nb = bad_nb ? 0 : (int64_t)n * (n + 1) * (n + 2) / 6;
         int lmax = 0;
         bool badl = false;
+        uint64_t lvh = 0;  // (keep / reuse) hash of the levels: sum of (l + 1) (t + 1) gamma
         for (int64_t t0 = lane; t0 < nb; t0 += 32) {
             const int l = a.levels[loff + t0];
             lmax = max(lmax, l);
             badl |= (l < 0 || l > a.max_level);
+            lvh += (uint64_t)(l + 1) * ((uint64_t)(t0 + 1) * kGamma);
+        }
+        if (a.dag_mode) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) lvh += __shfl_xor_sync(FULL, lvh, o);
+            lvh ^= ((uint64_t)(uint32_t)n << 32) ^ (uint64_t)(uint32_t)b;
         }
         lmax = __reduce_max_sync(FULL, lmax);
         badl = __any_sync(FULL, badl);
@@ -596,8 +618,9 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
         }
 
         // ---- 1. count and expand tasks
+        const bool reuse = a.dag_mode == 2;
         uint64_t *const desc = at<uint64_t>(base, a.ar.off_desc);
-        if (status == HESP_OK) {
+        if (!reuse && status == HESP_OK) {
             int64_t tcount = 0;
             for (int64_t t0 = 0; t0 < nb; t0 += 32) {
                 const int64_t t = t0 + lane;
@@ -613,7 +636,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
             if (T > a.ar.Tcap || T >= INT_MAX / 2 || (a.bm_smem_words > 0 && ((T + 31) >> 5) > a.bm_smem_words))
                 status = HESP_ERR_CAPACITY;
         }
-        if (status == HESP_OK) {
+        if (!reuse && status == HESP_OK) {
             int64_t off = 0;
             for (int64_t t0 = 0; t0 < nb; t0 += 32) {
                 const int64_t t = t0 + lane;
@@ -651,7 +674,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
 
         // ---- 2. dependences from per-atom last writers
         int64_t E = 0;
-        if (status == HESP_OK) {
+        if (!reuse && status == HESP_OK) {
             int32_t *const lw = at<int32_t>(base, a.ar.off_lw);
             int32_t *const mark = at<int32_t>(base, a.ar.off_succoff);  // offsets are built after this phase
             int32_t *const scnt = at<int32_t>(base, a.ar.off_next);
@@ -711,7 +734,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
         }
 
         // ---- 3. successor lists (CSR)
-        if (status == HESP_OK) {
+        if (!reuse && status == HESP_OK) {
             int32_t *const scnt = at<int32_t>(base, a.ar.off_next);
             int32_t *const succoff = at<int32_t>(base, a.ar.off_succoff);
             int32_t *const succ = at<int32_t>(base, a.ar.off_succ);
@@ -733,6 +756,45 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
             for (int64_t e = lane; e < E; e += 32) {
                 const int pos = atomicAdd(&scnt[epred[e]], 1);
                 succ[pos] = esucc[e];
+            }
+            __syncwarp();
+        }
+
+        // ---- keep: save the DAG's state for reuse launches; reuse: check
+        // that the kept DAG is this candidate's, then restore it
+        if (a.dag_mode) {
+            KeptHeader *const hd = at<KeptHeader>(base, a.ar.off_hdr);
+            uint16_t *const pending = at<uint16_t>(base, a.ar.off_pending);
+            uint16_t *const pend0 = at<uint16_t>(base, a.ar.off_pend0);
+            if (!reuse) {
+                if (status == HESP_OK)
+                    for (int64_t j = lane; j < T; j += 32) pend0[j] = pending[j];
+                if (lane == 0) {
+                    hd->sig = a.layout_sig;
+                    hd->lvhash = lvh;
+                    hd->T = T;
+                    hd->E = E;
+                    hd->status = status;
+                }
+            } else if (status == HESP_OK) {
+                const bool same = hd->sig == a.layout_sig && hd->lvhash == lvh && hd->T >= 0 && hd->T <= a.ar.Tcap &&
+                                  hd->E >= 0 && hd->E <= a.ar.Ecap;
+                if (!same) {
+                    status = HESP_ERR_STATE;
+                } else if (hd->status != HESP_OK) {
+                    status = hd->status;
+                } else {
+                    T = hd->T;
+                    E = hd->E;
+                    for (int64_t j = lane; j < T; j += 32) pending[j] = pend0[j];
+                    // warm L2 with the DAG the event loop reads
+                    const char *d0 = (const char *)desc;
+                    for (int64_t q = (int64_t)lane * 128; q < 8 * T; q += 32 * 128)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(d0 + q));
+                    const char *s0 = (const char *)at<int32_t>(base, a.ar.off_succ);
+                    for (int64_t q = (int64_t)lane * 128; q < 4 * E; q += 32 * 128)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(s0 + q));
+                }
             }
             __syncwarp();
         }
@@ -1223,7 +1285,8 @@ int sim_kernel_occupancy(int n_mem, int n_procs, int64_t Tcap, int *blocks_per_s
 int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, int64_t n_slots,
                const hesp_cand *cands, const int8_t *levels, int64_t n_cand, int32_t max_tiles, int32_t max_level,
                int64_t *makespan, int32_t *status, int64_t *ntasks, const int64_t *sched_off, int16_t *sproc,
-               int64_t *sstart, int64_t *sfinish, int8_t *crit, char *ws, cudaStream_t stream) {
+               int64_t *sstart, int64_t *sfinish, int8_t *crit, int dag_mode, uint64_t layout_sig, char *ws,
+               cudaStream_t stream) {
     KArgs a;
     a.cands = cands;
     a.levels = levels;
@@ -1238,6 +1301,8 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
     a.sstart = sstart;
     a.sfinish = sfinish;
     a.crit = crit;
+    a.dag_mode = dag_mode;
+    a.layout_sig = layout_sig;
     a.ar = ar;
     a.n_slots = n_slots;
     a.ws = ws + kWsHeaderBytes;

@@ -38,6 +38,7 @@ EXPORTS = (
     "hesp_graph_launch", "hesp_graph_destroy", "hesp_platform_set_tuning", "hesp_platform_get_tuning",
     "hesp_sim_autotune", "hesp_sort_cands_workspace_size", "hesp_sort_cands_by_size", "hesp_platform_set_policy",
     "hesp_simulate_critical", "hesp_solver_moves", "hesp_solver_pick", "hesp_schedule_metrics",
+    "hesp_sim_workspace_size_kept", "hesp_simulate_batch_keep", "hesp_simulate_batch_reuse",
 )
 SOLVER_ALL, SOLVER_CP, SOLVER_SHALLOW = 0, 1, 2
 PICK_HARD, PICK_SOFT = 0, 1
@@ -99,6 +100,9 @@ def lib():
         L.hesp_simulate_batch.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         L.hesp_simulate_batch_noalloc.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.hesp_simulate_critical.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, sz, vp]
+        L.hesp_sim_workspace_size_kept.argtypes = [i32, i32, i64, i64, ctypes.POINTER(sz)]
+        L.hesp_simulate_batch_keep.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, sz, vp]
+        L.hesp_simulate_batch_reuse.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, sz, vp]
         L.hesp_solver_moves.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp]
         L.hesp_solver_pick.argtypes = [vp, vp, vp, vp, i32, u64, i64, vp, vp, vp, vp]
         L.hesp_schedule_metrics.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -307,6 +311,42 @@ def simulate_batch_noalloc(platform: Platform, cands, levels, n_cand, max_tiles,
                                             _ptr(ss), _ptr(sf), _stream(stream)),
           "hesp_simulate_batch_noalloc")
     return makespan, status, ntasks
+
+
+def alloc_workspace_kept(max_tiles, max_level, n_cand, task_cap=0):
+    """Workspace of one arena per candidate, for simulate_batch_keep / _reuse."""
+    import torch
+    n = ctypes.c_size_t()
+    check(lib().hesp_sim_workspace_size_kept(max_tiles, max_level, task_cap, n_cand, ctypes.byref(n)),
+          "hesp_sim_workspace_size_kept")
+    return torch.empty(n.value, dtype=torch.uint8, device="cuda")
+
+
+def _simulate_kept(fn, name, platform, cands, levels, n_cand, max_tiles, max_level, workspace, makespan, status,
+                   ntasks, stream, task_cap):
+    import torch
+    dev = levels.device
+    if makespan is None:
+        makespan = torch.empty(n_cand, dtype=torch.int64, device=dev)
+    if status is None:
+        status = torch.empty(n_cand, dtype=torch.int32, device=dev)
+    check(fn(platform.h, _ptr(cands), _ptr(levels), n_cand, max_tiles, max_level, task_cap, _ptr(makespan),
+             _ptr(status), _ptr(ntasks), _ptr(workspace), workspace.numel(), _stream(stream)), name)
+    return makespan, status, ntasks
+
+
+def simulate_batch_keep(platform: Platform, cands, levels, n_cand, max_tiles, max_level, workspace, makespan=None,
+                        status=None, ntasks=None, stream=None, task_cap=0):
+    """hesp_simulate_batch_keep: simulate and keep each candidate's DAG."""
+    return _simulate_kept(lib().hesp_simulate_batch_keep, "hesp_simulate_batch_keep", platform, cands, levels,
+                          n_cand, max_tiles, max_level, workspace, makespan, status, ntasks, stream, task_cap)
+
+
+def simulate_batch_reuse(platform: Platform, cands, levels, n_cand, max_tiles, max_level, workspace, makespan=None,
+                         status=None, ntasks=None, stream=None, task_cap=0):
+    """hesp_simulate_batch_reuse: simulate the kept DAGs on another platform."""
+    return _simulate_kept(lib().hesp_simulate_batch_reuse, "hesp_simulate_batch_reuse", platform, cands, levels,
+                          n_cand, max_tiles, max_level, workspace, makespan, status, ntasks, stream, task_cap)
 
 
 def simulate_critical(platform: Platform, cands, levels, n_cand, max_tiles, max_level, workspace, crit,

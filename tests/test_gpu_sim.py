@@ -313,3 +313,48 @@ def test_maximum_tiles_and_empty_batch():
     empty = torch.empty(0, dtype=torch.int8, device="cuda")
     ms, st, _ = hesp.simulate_batch(plat, hesp.cands_tensor(3, 1024, np.zeros(0, np.int64)), empty, 0, 3, 1, ws)
     assert ms.numel() == 0 and st.numel() == 0
+
+
+def test_keep_and_reuse_equal_separate_simulations():
+    """One DAG build, several platforms: hesp_simulate_batch_keep on the CPU+GPU
+    platform, then hesp_simulate_batch_reuse on big.LITTLE, on the first
+    platform again and on a PL / EIT-P platform, each equal to a separate
+    hesp_simulate_batch; a candidate whose levels changed after the keep call
+    gets HESP_ERR_STATE, one whose build failed keeps the build's status."""
+    C, nb = 300, 120
+    lvh = W.workload_levels("cfg1", 4000, C)
+    lvh[7, 5] = 3  # above max_level: the build fails (HESP_ERR_ARG)
+    lv = torch.from_numpy(lvh.reshape(-1).copy()).cuda()
+    order = np.random.default_rng(0).permutation(C).astype(np.int64)  # any candidate order works
+    cands = hesp.cands_tensor(8, 2048, order * nb)
+    ws = hesp.alloc_workspace_kept(8, 2, C)
+    specs = [hesp.Platform(W.PLATFORMS["cfg1a"]), hesp.Platform(W.PLATFORMS["cfg1b"]),
+             hesp.Platform(W.PLATFORMS["cfg1a"]), hesp.Platform(W.PLATFORMS["cfg2"], order=1, select=1)]
+    for i, plat in enumerate(specs):
+        f = hesp.simulate_batch_keep if i == 0 else hesp.simulate_batch_reuse
+        nt = torch.empty(C, dtype=torch.int64, device="cuda")
+        ms, st, _ = f(plat, cands, lv, C, 8, 2, ws, ntasks=nt)
+        ref_ws = hesp.alloc_workspace(plat, 8, 2, C)
+        nt2 = torch.empty(C, dtype=torch.int64, device="cuda")
+        ms2, st2, _ = hesp.simulate_batch(plat, cands, lv, C, 8, 2, ref_ws, ntasks=nt2)
+        torch.cuda.synchronize()
+        assert torch.equal(st, st2) and torch.equal(ms, ms2) and torch.equal(nt[st == 0], nt2[st2 == 0]), i
+        bad = int(np.nonzero(order == 7)[0][0])
+        assert int(st[bad].item()) == -1 and int((st == 0).sum().item()) == C - 1
+    # change two candidates' levels after the keep call
+    lv2 = lv.clone()
+    lv2[3 * nb + 10] = (lv2[3 * nb + 10] + 1) % 3
+    lv2[11 * nb + 0] = (lv2[11 * nb + 0] + 1) % 3
+    ms, st, _ = hesp.simulate_batch_reuse(specs[1], cands, lv2, C, 8, 2, ws)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    changed = {int(np.nonzero(order == 3)[0][0]), int(np.nonzero(order == 11)[0][0])}
+    for c in range(C):
+        if c in changed:
+            assert st[c] == -5
+        elif order[c] == 7:
+            assert st[c] == -1
+        else:
+            assert st[c] == 0
+    with pytest.raises(hesp.HespError):
+        hesp.simulate_batch_keep(specs[0], cands, lv, C, 8, 2, ws[:ws.numel() // 2])
