@@ -74,6 +74,8 @@ class Platform(ctypes.Structure):
         ("order", ctypes.c_int32),
         ("select", ctypes.c_int32),
         ("rp_seed", ctypes.c_uint64),
+        ("cache", ctypes.c_int32),
+        ("pad_", ctypes.c_int32),
     ]
 
 
@@ -120,13 +122,15 @@ def lib():
 
 ORDER_FCFS, ORDER_PL = 0, 1
 SELECT_EFT, SELECT_EIT, SELECT_FP, SELECT_RP = 0, 1, 2, 3
+CACHE_WB, CACHE_WT, CACHE_WA = 0, 1, 2
 
 
-def make_platform(desc, order: int = ORDER_FCFS, select: int = SELECT_EFT, rp_seed: int = 0) -> Platform:
+def make_platform(desc, order: int = ORDER_FCFS, select: int = SELECT_EFT, rp_seed: int = 0,
+                  cache: int = CACHE_WB) -> Platform:
     """Oracle platform from a plain description (a dict or an object with the
     fields of ``paper_1602_05510_b300.workloads.PlatformSpec``), with the
     task order (FCFS / PL), the processor selection (EFT-P / EIT-P / F-P /
-    R-P) and the seed of R-P's draws."""
+    R-P), the seed of R-P's draws and the caching policy (WB / WT / WA)."""
     g = (lambda k: desc[k]) if isinstance(desc, dict) else (lambda k: getattr(desc, k))
     pl = Platform()
     pl.n_mem = g("n_mem")
@@ -151,7 +155,7 @@ def make_platform(desc, order: int = ORDER_FCFS, select: int = SELECT_EFT, rp_se
     pl.n_ovr = len(ovr)
     for i, (op, ty, bs, ns) in enumerate(ovr):
         pl.ovr_op[i], pl.ovr_type[i], pl.ovr_bs[i], pl.ovr_ns[i] = op, ty, bs, ns
-    pl.order, pl.select, pl.rp_seed = order, select, rp_seed
+    pl.order, pl.select, pl.rp_seed, pl.cache = order, select, rp_seed, cache
     return pl
 
 

@@ -23,8 +23,9 @@
  *     ceil(flops / rate) and transfer times latency + ceil(bytes / bw).
  *   - Sec. 2.1 "Task and data scheduling heuristics": FCFS or priority-list
  *     (PL) task order at release time with the EFT-P, EIT-P, F-P or R-P
- *     processor choice, accelerator memories as write-back software caches
- *     of host memory (MSI), transfers issued at scheduling time (prefetch).
+ *     processor choice, accelerator memories as write-back, write-through or
+ *     write-around software caches of host memory (MSI), transfers issued
+ *     at scheduling time (prefetch).
  *   - Sec. 2 (problem statement): output is the task set, the task-to-
  *     processor mapping, and the makespan.
  *
@@ -74,6 +75,10 @@ typedef struct {
     int32_t order;
     int32_t select;
     uint64_t rp_seed; /* R-P: seed of the per-task processor draws */
+    /* caching of accelerator memories (Sec. 2.1): 0 = write-back (WB),
+     * 1 = write-through (WT), 2 = write-around (WA) */
+    int32_t cache;
+    int32_t pad_;
 } or_platform;
 
 /* A square data region in element coordinates of the full matrix. */
@@ -667,26 +672,38 @@ static int schedule_task(sched_state *S, int32_t j, int64_t t) {
     for (int m = 0; m < M; m++) {
         drt[m] = 0;
         if (!S->mem_used[m]) continue;
-        int64_t elems_from[OR_MAX_MEMS];
-        for (int sm = 0; sm < M; sm++) elems_from[sm] = 0;
+        int64_t elems_from[OR_MAX_MEMS], depart[OR_MAX_MEMS];
+        for (int sm = 0; sm < M; sm++) {
+            elems_from[sm] = 0;
+            depart[sm] = t;
+        }
         for (int64_t e = 0; e < na; e++) {
             int64_t x = ax[e];
             src[e * M + m] = -1;
             if (valid[x * M + m]) {
                 if (vfrom[x * M + m] > drt[m]) drt[m] = vfrom[x * M + m];
             } else {
+                /* the lowest memory with a copy usable at t; if there is none
+                 * (under WA a block may be valid only in flight to the host),
+                 * the copy usable first (ties to the lower memory) */
                 int found = -1;
                 for (int sm = 0; sm < M; sm++)
                     if (valid[x * M + sm] && vfrom[x * M + sm] <= t) { found = sm; break; }
+                if (found < 0)
+                    for (int sm = 0; sm < M; sm++)
+                        if (valid[x * M + sm] && (found < 0 || vfrom[x * M + sm] < vfrom[x * M + found])) found = sm;
                 if (found < 0) return OR_ERR_STATE;
                 src[e * M + m] = found;
                 elems_from[found] += atom_elems;
+                if (vfrom[x * M + found] > depart[found]) depart[found] = vfrom[x * M + found];
             }
         }
+        /* one message per source, issued when the last of its data is usable
+         * there (at t under WB) */
         for (int sm = 0; sm < M; sm++) {
             arrive[m][sm] = 0;
             if (elems_from[sm] > 0) {
-                arrive[m][sm] = t + or_xfer_ns(pl, elems_from[sm]);
+                arrive[m][sm] = depart[sm] + or_xfer_ns(pl, elems_from[sm]);
                 if (arrive[m][sm] > drt[m]) drt[m] = arrive[m][sm];
             }
         }
@@ -737,12 +754,25 @@ static int schedule_task(sched_state *S, int32_t j, int64_t t) {
     }
     for (int sm = 0; sm < M; sm++)
         if (elems_from2[sm] > 0) { S->st->n_transfers++; S->st->xfer_elems += elems_from2[sm]; }
+    /* the written block: WB valid only in mem(p*) from the finish; WT also
+     * in host memory, from the arrival of a message of the whole block issued
+     * at the finish; WA (from an accelerator) only in host memory, from that
+     * arrival.  Every other copy is invalidated. */
+    int64_t written = 0;
+    for (int64_t e = 0; e < na; e++) written += axw[e];
+    const int64_t through = ms != 0 && pl->cache != 0 ? best_eft + or_xfer_ns(pl, written * atom_elems) : best_eft;
     for (int64_t e = 0; e < na; e++) {
         if (!axw[e]) continue;
         int64_t x = ax[e];
         for (int m = 0; m < M; m++) valid[x * M + m] = 0;
-        valid[x * M + ms] = 1;
-        vfrom[x * M + ms] = best_eft;
+        if (pl->cache != 2 || ms == 0) {
+            valid[x * M + ms] = 1;
+            vfrom[x * M + ms] = best_eft;
+        }
+        if (ms != 0 && pl->cache != 0) {
+            valid[x * M + 0] = 1;
+            vfrom[x * M + 0] = through;
+        }
     }
     S->avail[best] = best_eft;
     S->finish_j = best_eft;
@@ -788,9 +818,11 @@ static int by_crit_desc(const void *a, const void *b) {
  *   - for each memory m holding a processor, the data ready time DRT(j, m):
  *     every atom x of j's regions that is valid in m is usable from
  *     vfrom[x][m]; every other atom is fetched from the lowest-numbered
- *     memory holding a copy usable at t; the missing atoms with the same
- *     source travel as one message issued at t and arrive at
- *     t + xfer(elements); DRT is the latest of these times;
+ *     memory holding a copy usable at t (if none is, from the copy usable
+ *     first); the missing atoms with the same source travel as one message,
+ *     issued at t or, if later, when the last of them is usable at the
+ *     source, and arrive xfer(elements) later; DRT is the latest of these
+ *     times;
  *   - EFT(p) = max(t, avail[p], DRT(j, mem(p))) + exec(op, type(p), bs);
  *     EFT-P (pl->select 0): p* = argmin EFT, ties to the lowest processor
  *     id; EIT-P (select 1): p* = argmin max(t, avail[p]), ties likewise;
@@ -799,8 +831,12 @@ static int by_crit_desc(const void *a, const void *b) {
  *     the idle processors in id order, the one at a uniform draw from the
  *     SplitMix64 stream (rp_seed, j); the task still waits for its data;
  *   - commit: start = EFT - exec, avail[p*] = EFT; the fetched atoms become
- *     valid in mem(p*) from their arrival; then the written atoms become
- *     valid only in mem(p*), from the finish time (write-back invalidation).
+ *     valid in mem(p*) from their arrival; then the written atoms are
+ *     invalidated everywhere and become valid: under WB (pl->cache 0) in
+ *     mem(p*) from the finish time; under WT (1) there and, when mem(p*) is
+ *     not the host, in host memory from finish + xfer(block); under WA (2),
+ *     when mem(p*) is not the host, only in host memory from finish +
+ *     xfer(block) (else as WB).
  *   - the makespan is the largest finish time. */
 int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *code, int64_t code_len,
                     int64_t cap_t, int32_t atom_level, int32_t dep_mode, int16_t *proc_out,

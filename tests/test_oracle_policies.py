@@ -313,3 +313,52 @@ def test_fp_rp_replay_with_transfers(order, select, key, n, b):
         if order == O.ORDER_FCFS:
             by_queue = sorted(rel_seen)
             assert [x[2] for x in by_queue] == sorted(x[2] for x in by_queue)
+
+
+# ---------------------------------------------------------------- WT, WA
+
+def test_write_around_worked_example():
+    g = GOLD["n2_b1024_cpu4_gpu1_write_around"]
+    r = O.simulate(O.make_platform(W.PLATFORMS["cfg0"], cache=O.CACHE_WA), 2, 1024, g["levels"])
+    assert r["proc"].tolist() == g["proc"] and r["start"].tolist() == g["start"]
+    assert r["finish"].tolist() == g["finish"] and r["makespan"] == g["makespan"]
+    wt = O.simulate(O.make_platform(W.PLATFORMS["cfg0"], cache=O.CACHE_WT), 2, 1024, g["levels"])
+    assert wt["makespan"] == g["write_through_makespan"] == GOLD["n2_b1024_all_level0_cpu4_gpu1"]["makespan"]
+
+
+def test_write_through_and_around_on_the_transfer_back_example():
+    e = GOLD["n2_b1024_cpu1_gpu1_overrides"]
+    spec = dataclasses.replace(W.cpu_gpu_platform(1, 1), exec_overrides=tuple(tuple(x) for x in e["overrides"]))
+    for cache in (O.CACHE_WT, O.CACHE_WA):
+        r = O.simulate(O.make_platform(spec, cache=cache), 2, 1024, [0, 0, 0, 0])
+        assert r["proc"].tolist() == e["proc"] and r["finish"].tolist() == e["finish"]
+        assert r["n_transfers"] == 1
+
+
+@pytest.mark.parametrize("key", ["cfg1b", "id3"])
+def test_caches_coincide_with_one_memory(key):
+    spec = W.PLATFORMS["cfg1b"] if key == "cfg1b" else identical(3)
+    rng = np.random.default_rng(8)
+    for n in (3, 4):
+        lv = rng.integers(0, 3, O.base_count(n)).astype(np.int8)
+        rs = [O.simulate(O.make_platform(spec, cache=c), n, 1024, lv) for c in (0, 1, 2)]
+        for r in rs[1:]:
+            assert np.array_equal(r["start"], rs[0]["start"]) and np.array_equal(r["proc"], rs[0]["proc"])
+
+
+@pytest.mark.parametrize("cache", [1, 2])
+@pytest.mark.parametrize("order,select", [(0, 0), (1, 1), (0, 2)])
+@pytest.mark.parametrize("key,n,b", [("cfg0", 3, 1024), ("cfg1a", 3, 2048), ("cfg2", 3, 512), ("cfg4", 2, 2048)])
+def test_cache_replay(cache, order, select, key, n, b):
+    """An independent replay of the oracle's order, choices and issue times
+    under WT / WA reproduces every start and finish."""
+    spec = W.PLATFORMS[key]
+    rng = np.random.default_rng(cache * 100 + order * 10 + select + n)
+    for rep_ in range(3):
+        lv = rng.integers(0, 3, O.base_count(n)).astype(np.int8)
+        r = O.simulate(O.make_platform(spec, order=order, select=select, rp_seed=5, cache=cache), n, b, lv)
+        assert r["status"] == 0
+        o = r["order"].tolist()
+        s_, f_ = replay(spec, n, b, lv, o, [int(r["proc"][j]) for j in o], issue=r["issue"], cache=cache)
+        assert [s_[j] for j in range(r["n_tasks"])] == r["start"].tolist()
+        assert [f_[j] for j in range(r["n_tasks"])] == r["finish"].tolist()

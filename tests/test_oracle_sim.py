@@ -121,11 +121,12 @@ def test_worked_example_with_transfers(key, ncpu):
 # ----------------------------------------------- replay and brute force
 
 
-def replay(spec, n, b, levels, order, procs, atom_level=None, issue=None):
-    """Evaluate a given (task order, assignment) with the write-back caching
-    and transfer rules, each task issued at its release time (the latest
-    finish of its predecessors), or at issue[j] when given.  Independent of
-    the oracle's event loop."""
+def replay(spec, n, b, levels, order, procs, atom_level=None, issue=None, cache=0):
+    """Evaluate a given (task order, assignment) with the caching and
+    transfer rules, each task issued at its release time (the latest finish
+    of its predecessors), or at issue[j] when given.  cache: 0 write-back,
+    1 write-through, 2 write-around.  Independent of the oracle's event
+    loop."""
     pl = O.make_platform(spec)
     code = O.levels_to_code(n, levels)
     d = O.expand(n, b, code)
@@ -139,6 +140,9 @@ def replay(spec, n, b, levels, order, procs, atom_level=None, issue=None):
     def atoms(r):
         s = r[2] // a
         return [(r[0] // a + i, r[1] // a + j) for i in range(s) for j in range(s)]
+
+    def is_valid(x, m):
+        return valid.get((x, m), m == 0)
 
     avail = [0] * len(spec.procs)
     start = {}
@@ -156,12 +160,19 @@ def replay(spec, n, b, levels, order, procs, atom_level=None, issue=None):
         for ri, r in enumerate(regs):
             for x in atoms(r):
                 xs.append((x, ri == len(regs) - 1))
-                if valid.get((x, m), m == 0):
+                if is_valid(x, m):
                     drt = max(drt, vfrom.get((x, m), 0))
                 else:
-                    src = min(s for s in range(M) if valid.get((x, s), s == 0) and vfrom.get((x, s), 0) <= t)
+                    usable = [s for s in range(M) if is_valid(x, s) and vfrom.get((x, s), 0) <= t]
+                    if usable:
+                        src = min(usable)
+                    else:  # only copies still in flight: the one usable first
+                        src = min((s for s in range(M) if is_valid(x, s)), key=lambda s: (vfrom.get((x, s), 0), s))
                     groups.setdefault(src, []).append(x)
-        arr = {s: t + O.xfer_ns(pl, len(v) * a * a) for s, v in groups.items()}
+        arr = {}
+        for s, v in groups.items():
+            dep = max([t] + [vfrom.get((x, s), 0) for x in v])
+            arr[s] = dep + O.xfer_ns(pl, len(v) * a * a)
         drt = max([drt] + list(arr.values()))
         ex = O.exec_ns(pl, int(d["op"][j]), spec.procs[p][1], int(d["bs"][j]))
         st = max(t, avail[p], drt)
@@ -169,12 +180,17 @@ def replay(spec, n, b, levels, order, procs, atom_level=None, issue=None):
             for x in v:
                 valid[(x, m)] = True
                 vfrom[(x, m)] = arr[s]
-        for x, w in xs:
-            if w:
-                for mm in range(M):
-                    valid[(x, mm)] = False
+        written = [x for x, w in xs if w]
+        through = st + ex + O.xfer_ns(pl, len(written) * a * a)
+        for x in written:
+            for mm in range(M):
+                valid[(x, mm)] = False
+            if cache != 2 or m == 0:
                 valid[(x, m)] = True
                 vfrom[(x, m)] = st + ex
+            if m != 0 and cache != 0:
+                valid[(x, 0)] = True
+                vfrom[(x, 0)] = through
         avail[p] = st + ex
         start[j], fin[j] = st, st + ex
     return start, fin
