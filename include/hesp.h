@@ -129,6 +129,23 @@ int hesp_platform_set_exec_table(hesp_platform *p, int32_t op, int32_t type, int
 #define HESP_SELECT_FP 2
 #define HESP_SELECT_RP 3
 int hesp_platform_set_policy(hesp_platform *p, int32_t order, int32_t select, uint64_t rp_seed);
+/* Caching of accelerator memories (Sec. 2.1), applied to the block a task
+ * writes (every other copy of it is invalidated):
+ *   HESP_CACHE_WB (0, default): write-back -- valid only in the memory of the
+ *   task's processor, from its finish;
+ *   HESP_CACHE_WT (1): write-through -- also sent to host memory at the
+ *   finish: valid there from finish + xfer(block elements);
+ *   HESP_CACHE_WA (2): write-around -- when the processor is not in host
+ *   memory, valid only in host memory, from finish + xfer(block elements).
+ * A fetch of data that no memory can supply at the scheduling time t (under
+ * WT / WA a copy may still be in flight to the host) takes the copy usable
+ * first (ties to the lower memory); one message per source memory, issued at
+ * t or, if later, when the last of its data is usable there.  ERR_ARG for an
+ * unknown policy. */
+#define HESP_CACHE_WB 0
+#define HESP_CACHE_WT 1
+#define HESP_CACHE_WA 2
+int hesp_platform_set_cache(hesp_platform *p, int32_t cache);
 /* Host queries of the models, as used by the simulator. */
 int hesp_platform_exec_ns(const hesp_platform *p, int32_t op, int32_t type, int64_t block, int64_t *ns_out);
 int hesp_platform_xfer_ns(const hesp_platform *p, int64_t elems, int64_t *ns_out);

@@ -74,6 +74,7 @@ static DevPlatform dev_platform(const hesp_platform *p) {
     d.order = p->order;
     d.select = p->select;
     d.rp_seed = p->rp_seed;
+    d.cache = p->cache;
     for (int op = 0; op < 4; ++op)
         for (int l = 0; l < HESP_LB; ++l) {
             int64_t s = 0;
@@ -195,6 +196,12 @@ int hesp_platform_set_policy(hesp_platform *p, int32_t order, int32_t select, ui
     p->order = order;
     p->select = select;
     p->rp_seed = rp_seed;
+    return HESP_OK;
+}
+
+int hesp_platform_set_cache(hesp_platform *p, int32_t cache) {
+    if (!p || cache < HESP_CACHE_WB || cache > HESP_CACHE_WA) return HESP_ERR_ARG;
+    p->cache = cache;
     return HESP_OK;
 }
 

@@ -284,6 +284,20 @@ struct AtomState {
             if (v[s] >= 0 && v[s] <= t) src = s;
         return src;
     }
+    // memory whose copy is usable first (ties to the lowest), or -1
+    __device__ __forceinline__ int earliest() const {
+        int src = -1;
+#pragma unroll
+        for (int s = 0; s < M; ++s)
+            if (v[s] >= 0 && (src < 0 || v[s] < v[src < 0 ? 0 : src])) src = s;
+        return src;
+    }
+    // the source of a fetch at t: the lowest memory with a copy usable at t,
+    // else (write-through / write-around only) the copy usable first
+    __device__ __forceinline__ int fetch_source(int64_t t, int cache) const {
+        const int s = source(t);
+        return (s < 0 && cache != HESP_CACHE_WB) ? earliest() : s;
+    }
 };
 
 // Packed per-(destination m, source s != m) atom counts: counter q =
@@ -313,16 +327,17 @@ struct Counts {
 };
 
 // Schedule task j at time t: data-ready time per memory, the processor
-// choice `sel` (ties to the lowest id), commit of the coherence state, append
-// to the chosen processor's FIFO.  Under F-P / R-P the caller guarantees a
-// processor idle at t.  Clears `ok` on an internal inconsistency.
+// choice `sel` (ties to the lowest id), commit of the coherence state (the
+// caching policy `cache`), append to the chosen processor's FIFO.  Under
+// F-P / R-P the caller guarantees a processor idle at t.  Clears `ok` on an
+// internal inconsistency.
 template <int M, int NS, bool FIFO, bool REC>
 __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, const KArgs &a, int Lc, int lb_b,
                                                  int lane, const int64_t *s_exec, const int8_t *s_pmem,
                                                  const int8_t *s_ptype, const int pm[NS], const int pt[NS],
                                                  const bool pv[NS], int64_t avail[NS], int head[NS], int tail[NS],
                                                  int64_t hfin[NS], int64_t &mk, bool &ok, int64_t sched_base,
-                                                 int sel, uint64_t rp_seed) {
+                                                 int sel, uint64_t rp_seed, int cache) {
     const uint64_t d = at<uint64_t>(base, a.ar.off_desc)[j];
     const int32_t *const succoff = at<int32_t>(base, a.ar.off_succoff);
     const int se0 = succoff[j], se1 = succoff[j + 1];  // kept with the task while it is in flight
@@ -341,13 +356,21 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
     cnt.clear();
 #pragma unroll
     for (int m = 0; m < M; ++m) drt_off[m] = 0;
+    // Leads over t (usable-from time - t).  Under FCFS a task starts once all
+    // its predecessors finished, so a copy can lead t by one message time at
+    // most (31 bits, else an error status); under the priority-list order a
+    // copy issued for a task placed earlier may arrive far beyond t, so 64
+    // bits.  dlead (write-through / write-around): lead of the departure of
+    // the message m <- s, which leaves when the last of its data is usable at
+    // the source.
+    using Lead = typename std::conditional<FIFO, unsigned, uint64_t>::type;
+    Lead dlead[M][M];
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int s = 0; s < M; ++s) dlead[m][s] = 0;
     if (M > 1) {
-        // latest (usable-from time - t) of a valid copy per memory.  Under
-        // FCFS a task starts once all its predecessors finished, so a copy can
-        // lead t by one message time at most (31 bits, else an error status);
-        // under the priority-list order a copy issued for a task placed
-        // earlier may arrive far beyond t, so 64 bits.
-        using Lead = typename std::conditional<FIFO, unsigned, uint64_t>::type;
+        // latest lead of a valid copy per memory
         Lead amax[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) amax[m] = 0;
@@ -357,7 +380,17 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
                 const uint32_t x = desc_atom(d, i >> sh) + (uint32_t)(i & ((1 << sh) - 1));
                 AtomState<M> st;
                 st.load(vfrom + (int64_t)x * MP);
-                const int src = st.source(t);
+                const int src = st.fetch_source(t, cache);
+                Lead slead = 0;  // lead of the source copy over t
+                if (cache != HESP_CACHE_WB && src >= 0) {
+#pragma unroll
+                    for (int q = 0; q < M; ++q)
+                        if (q == src && st.v[q] > t) {
+                            const int64_t dl = st.v[q] - t;
+                            if (FIFO) ok &= dl <= 0x7FFFFFFFLL;
+                            slead = FIFO ? (Lead)min(dl, (int64_t)0x7FFFFFFF) : (Lead)dl;
+                        }
+                }
 #pragma unroll
                 for (int m = 0; m < M; ++m) {
                     if (st.v[m] >= 0) {
@@ -373,12 +406,26 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
                     } else {
                         ok &= src >= 0;
                         cnt.add(m, src);
+                        if (cache != HESP_CACHE_WB) {
+#pragma unroll
+                            for (int q = 0; q < M; ++q)
+                                if (q == src) dlead[m][q] = max(dlead[m][q], slead);
+                        }
                     }
                 }
             }
         }
 #pragma unroll
         for (int k = 0; k < Counts<M>::NW; ++k) cnt.w[k] = __reduce_add_sync(FULL, cnt.w[k]);
+        if (cache != HESP_CACHE_WB) {
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+#pragma unroll
+                for (int q = 0; q < M; ++q)
+                    if (q != m)
+                        dlead[m][q] = FIFO ? (Lead)__reduce_max_sync(FULL, (unsigned)dlead[m][q])
+                                           : (Lead)warp_max_u64((uint64_t)dlead[m][q]);
+        }
 #pragma unroll
         for (int m = 0; m < M; ++m) {
             int64_t off = FIFO ? (int64_t)__reduce_max_sync(FULL, (unsigned)amax[m])
@@ -387,7 +434,7 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
             for (int s = 0; s < M; ++s) {
                 if (s == m) continue;
                 const unsigned c = cnt.get(m, s);
-                if (c > 0) off = max(off, xt[c]);
+                if (c > 0) off = max(off, (cache != HESP_CACHE_WB ? (int64_t)dlead[m][s] : 0) + xt[c]);
             }
             drt_off[m] = off;
         }
@@ -461,14 +508,20 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
                 const uint32_t x = desc_atom(d, r) + (uint32_t)(i & ((1 << sh) - 1));
                 int64_t *px = vfrom + (int64_t)x * MP;
                 if (r == nr - 1) {
-                    // written block: valid only in the chosen memory, from the finish time
+                    // written block, every other copy invalidated: WB valid in
+                    // the chosen memory from the finish; WT also in host memory
+                    // from finish + xfer(block); WA (from an accelerator) only
+                    // in host memory, from finish + xfer(block)
+                    const bool acc = ms != 0 && cache != HESP_CACHE_WB;
+                    const int64_t v_ms = (cache == HESP_CACHE_WA && ms != 0) ? -1 : eft;
+                    const int64_t v_host = acc ? eft + xt[1 << sh] : -1;
                     longlong2 w0, w1;
-                    w0.x = ms == 0 ? eft : -1;
-                    w0.y = ms == 1 ? eft : -1;
+                    w0.x = ms == 0 ? v_ms : v_host;
+                    w0.y = ms == 1 ? v_ms : -1;
                     *reinterpret_cast<longlong2 *>(px) = w0;
                     if (MP == 4) {
-                        w1.x = ms == 2 ? eft : -1;
-                        w1.y = ms == 3 ? eft : -1;
+                        w1.x = ms == 2 ? v_ms : -1;
+                        w1.y = ms == 3 ? v_ms : -1;
                         *reinterpret_cast<longlong2 *>(px + 2) = w1;
                     }
                 } else {
@@ -480,14 +533,18 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
                         if (m == ms) vm = st.v[m];
                     if (vm < 0) {
                         // fetched: valid in the chosen memory from its message's arrival
-                        const int src = st.source(t);
+                        const int src = st.fetch_source(t, cache);
                         unsigned c = 0;
+                        int64_t lead = 0;
 #pragma unroll
                         for (int m = 0; m < M; ++m)
 #pragma unroll
                             for (int s = 0; s < M; ++s)
-                                if (m != s && m == ms && s == src) c = cnt.get(m, s);
-                        px[ms] = t + xt[c];
+                                if (m != s && m == ms && s == src) {
+                                    c = cnt.get(m, s);
+                                    lead = (int64_t)dlead[m][s];
+                                }
+                        px[ms] = t + lead + xt[c];
                     }
                 }
             }
@@ -824,11 +881,12 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                     xt[k] = k == 0 ? 0 : pl.lat + (bytes + pl.bw - 1) / pl.bw;
                 }
             }
-            // GEN = false: the FCFS + EFT-P instantiation; GEN = true: every
-            // policy, chosen at run time from the platform.
+            // GEN = false: the FCFS + EFT-P + write-back instantiation; GEN =
+            // true: every policy, chosen at run time from the platform.
             const int sel = GEN ? pl.select : HESP_SELECT_EFT;
             const bool waits = GEN && sel >= HESP_SELECT_FP;  // F-P, R-P: idle processors only
             const uint64_t rp_seed = pl.rp_seed;
+            const int cache = GEN ? pl.cache : HESP_CACHE_WB;
             if (GEN && pl.order == HESP_ORDER_PL) {
                 // ---- PL: a priority list by critical time (HEFT-like); each task
                 // is scheduled at its release time, the latest finish among its
@@ -929,7 +987,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                     }
                     const int64_t fj = schedule_task<M, NS, false, GEN>(j, tj, base, a, Lc, lb_b, lane, s_exec, s_pmem,
                                                                    s_ptype, pm, pt, pv, avail, head, tail, hfin, mk,
-                                                                   ok, sched_base, sel, rp_seed);
+                                                                   ok, sched_base, sel, rp_seed, cache);
                     const int e0 = succoff[j], e1 = succoff[j + 1];
                     for (int e = e0 + lane; e < e1; e += 32) {
                         const int sj = succ[e];
@@ -992,7 +1050,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                             continue;
                         }
                         schedule_task<M, NS, true, GEN>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
-                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed);
+                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache);
                         ++scheduled;
                     }
                     direct = false;
@@ -1020,7 +1078,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                                 }
                                 schedule_task<M, NS, true, GEN>(jb + bit, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype,
                                                            pm, pt, pv, avail, head, tail, hfin, mk, ok, sched_base,
-                                                           sel, rp_seed);
+                                                           sel, rp_seed, cache);
                                 ++scheduled;
                             }
                         }
@@ -1039,7 +1097,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                         const int j = link[qh].rq;
                         ++qh;
                         schedule_task<M, NS, true, GEN>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
-                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed);
+                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache);
                         ++scheduled;
                     }
                 }
@@ -1314,7 +1372,8 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
     const int64_t blocks = (n_slots * 32 + threads - 1) / threads;
     const bool two = p->n_procs > 32;
     const unsigned ub = (unsigned)blocks;
-    const bool gen = p->order != HESP_ORDER_FCFS || p->select != HESP_SELECT_EFT || crit != nullptr;
+    const bool gen = p->order != HESP_ORDER_FCFS || p->select != HESP_SELECT_EFT || p->cache != HESP_CACHE_WB ||
+                     crit != nullptr;
     switch (p->n_mem) {
     case 1: two ? launch_one<1, 2>(gen, ub, threads, smem, stream, dp, a, ctr)
                 : launch_one<1, 1>(gen, ub, threads, smem, stream, dp, a, ctr); break;

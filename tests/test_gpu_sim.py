@@ -261,10 +261,7 @@ def test_cfg4_full_size_candidates():
     check_parity(W.PLATFORMS["cfg4"], 32, 2048, lv, g, schedule=False)
 
 
-@pytest.mark.parametrize("order,select", [(0, 1), (1, 0), (1, 1), (0, 2), (0, 3), (1, 2), (1, 3)])
-def test_policies_parity(order, select):
-    """PL task order and the EIT-P, F-P and R-P processor choices (Sec. 2.1)
-    against the oracle: schedules bit-exact on every workload shape."""
+def policy_parity(order, select, cache=0):
     seed = 0x8000000000000000 + 12345 * (order + 1)
     cases = [("cfg0", 3, 1024, W.workload_levels("cfg0")[::8], 1),
              ("cfg1a", 8, 2048, W.workload_levels("cfg1", 300, 48), 2),
@@ -273,7 +270,7 @@ def test_policies_parity(order, select):
              ("cfg4", 5, 2048, np.random.default_rng(2).integers(0, 4, (16, W.base_count(5))).astype(np.int8), 3)]
     for key, n, b, lv, L in cases:
         spec = W.PLATFORMS[key]
-        plat = hesp.Platform(spec, order=order, select=select, rp_seed=seed)
+        plat = hesp.Platform(spec, order=order, select=select, rp_seed=seed, cache=cache)
         C, nb = lv.shape
         d_lv = torch.from_numpy(np.ascontiguousarray(lv).reshape(-1).copy()).cuda()
         cands = hesp.cands_tensor(n, b, np.arange(C, dtype=np.int64) * nb)
@@ -289,13 +286,28 @@ def test_policies_parity(order, select):
         torch.cuda.synchronize()
         ms, st = ms.cpu().numpy(), st.cpu().numpy()
         proc, start, fin = (x.cpu().numpy() for x in sched[1:])
-        pl = O.make_platform(spec, order=order, select=select, rp_seed=seed)
+        pl = O.make_platform(spec, order=order, select=select, rp_seed=seed, cache=cache)
         for c in range(C):
             r = O.simulate(pl, n, b, lv[c])
             assert st[c] == 0 and ms[c] == r["makespan"], (key, c)
             a, e = offs[c], offs[c + 1]
             assert np.array_equal(proc[a:e], r["proc"]) and np.array_equal(start[a:e], r["start"]), (key, c)
             assert np.array_equal(fin[a:e], r["finish"]), (key, c)
+
+
+@pytest.mark.parametrize("order,select", [(0, 1), (1, 0), (1, 1), (0, 2), (0, 3), (1, 2), (1, 3)])
+def test_policies_parity(order, select):
+    """PL task order and the EIT-P, F-P and R-P processor choices (Sec. 2.1)
+    against the oracle: schedules bit-exact on every workload shape."""
+    policy_parity(order, select)
+
+
+@pytest.mark.parametrize("cache", [1, 2])
+@pytest.mark.parametrize("order,select", [(0, 0), (1, 0), (0, 2), (1, 3)])
+def test_cache_policies_parity(cache, order, select):
+    """Write-through and write-around caching (Sec. 2.1) against the oracle,
+    with several task orders and processor choices: schedules bit-exact."""
+    policy_parity(order, select, cache)
 
 
 def test_maximum_tiles_and_empty_batch():
