@@ -370,3 +370,56 @@ def test_keep_and_reuse_equal_separate_simulations():
             assert st[c] == 0
     with pytest.raises(hesp.HespError):
         hesp.simulate_batch_keep(specs[0], cands, lv, C, 8, 2, ws[:ws.numel() // 2])
+
+
+def test_cfg2_full_ragged_launch_sampled():
+    """The full 16,384-candidate ragged batch (n 4..32, b 512..2048), ordered
+    largest DAG first as the benchmark runs it: every candidate succeeds, task
+    counts match the closed forms, and a sample across sizes matches the
+    oracle."""
+    C = 16384
+    cands = torch.empty(C * 16, dtype=torch.uint8, device="cuda")
+    lv = torch.empty(C * W.base_count(32), dtype=torch.int8, device="cuda")
+    used = torch.zeros(1, dtype=torch.int64, device="cuda")
+    hesp.generate_uneven(2, 0, C, cands, lv, used)
+    scands, perm = hesp.sort_cands_by_size(cands, lv, C)
+    spec = W.PLATFORMS["cfg2"]
+    plat = hesp.Platform(spec)
+    ws = hesp.alloc_workspace(plat, 32, 2, C, max_bytes=16 << 30)
+    nt = torch.empty(C, dtype=torch.int64, device="cuda")
+    ms, st, _ = hesp.simulate_batch(plat, scands, lv, C, 32, 2, ws, ntasks=nt)
+    torch.cuda.synchronize()
+    ms, st, nt, perm = ms.cpu().numpy(), st.cpu().numpy(), nt.cpu().numpy(), perm.cpu().numpy()
+    assert (st == 0).all()
+    assert (np.diff(np.minimum(nt >> 4, 65535)) <= 0).all()  # largest first, in buckets of 16 tasks
+    assert np.array_equal(np.sort(perm), np.arange(C))
+    n, b, off, lvh = W.uneven_candidates(2, 0, C)
+    pl = O.make_platform(spec)
+    order = np.argsort(nt)
+    pick = list(order[:8]) + list(order[C // 2:C // 2 + 6]) + list(order[-3:])
+    for i in pick:
+        c = int(perm[i])  # original candidate index
+        r = O.simulate(pl, int(n[c]), int(b[c]), lvh[off[c]:off[c + 1]], schedule=False)
+        assert r["makespan"] == ms[i] and r["n_tasks"] == nt[i], (i, c)
+
+
+def test_cfg3_full_label_launch_sampled():
+    """A full 65,536-candidate labelling launch of the surrogate workload
+    (16 x 16 tiles, levels {0,1,2}, 16 CPU + 2 GPU): all succeed, sampled
+    candidates match the oracle."""
+    C, n, b = 65536, 16, 2048
+    nb = W.base_count(n)
+    lv = torch.empty(C * nb, dtype=torch.int8, device="cuda")
+    hesp.generate_candidates(hesp.GEN_UNIFORM, 3, 0, C, n, b, 3, lv)
+    spec = W.PLATFORMS["cfg3"]
+    plat = hesp.Platform(spec)
+    ws = hesp.alloc_workspace(plat, n, 2, C, max_bytes=16 << 30)
+    ms, st, _ = hesp.simulate_batch(plat, hesp.cands_tensor(n, b, np.arange(C, dtype=np.int64) * nb), lv, C, n, 2, ws)
+    torch.cuda.synchronize()
+    ms, st = ms.cpu().numpy(), st.cpu().numpy()
+    assert (st == 0).all()
+    pl = O.make_platform(spec)
+    idx = np.sort(np.random.default_rng(3).choice(C, 12, replace=False))
+    for c in idx:
+        lvc = W.uniform_levels(3, int(c), 1, nb, 3)[0]
+        assert O.simulate(pl, n, b, lvc, schedule=False)["makespan"] == ms[c], c
