@@ -469,6 +469,16 @@ typedef struct hesp_surrogate hesp_surrogate;
 int hesp_surrogate_create(int32_t n_base, int32_t n_levels, int32_t hidden, int32_t max_batch, uint64_t seed,
                           hesp_surrogate **out);
 void hesp_surrogate_destroy(hesp_surrogate *s);
+/* Checkpoints (synchronous, host files): hesp_surrogate_save writes the
+ * shape, the seed, the Adam step count, the target standardisation (mu,
+ * sigma), the FP32 parameters and both Adam moment tensors, followed by a
+ * 64-bit FNV-1a hash of the file's bytes (written to path.tmp, then renamed).
+ * hesp_surrogate_load creates a new handle from such a file: training resumed
+ * from it continues exactly as the saved handle would.  ERR_ARG for a file
+ * that cannot be written / read, has another layout, is truncated, carries
+ * trailing bytes or fails the hash (then *out stays NULL). */
+int hesp_surrogate_save(const hesp_surrogate *s, const char *path);
+int hesp_surrogate_load(const char *path, hesp_surrogate **out);
 int hesp_surrogate_shape(const hesp_surrogate *s, int64_t *F_out, int64_t *Fp_out, int32_t *H_out);
 /* Target standardisation: set directly, or fit (mean and population standard
  * deviation of ln makespan over makespan_dev[n]; synchronises the stream). */

@@ -45,7 +45,7 @@ struct hesp_surrogate {
     __nv_bfloat16 *XT, *A1, *A1T, *A2, *dZ2, *dZ2T, *dZ1, *dZ1T;
     int8_t *lvp;  // levels with rows padded to ldp bytes, for the layer-1 GEMM
     int64_t ldp;
-    float *y, *dy, *loss;
+    float *y, *dy, *sq, *loss;
     int32_t *err;
     void *mem;  // one device allocation holding all of the above
 };
@@ -107,9 +107,10 @@ __global__ void onehot_t_kernel(const int8_t *lv, int lv_stride, int B, int n_ba
     }
 }
 
-// One warp per row: y = A2[b] . w3 + b3; with targets, dy and the loss.
+// One warp per row: y = A2[b] . w3 + b3; with targets, dy and the row's
+// squared error (summed by loss_kernel in a fixed order).
 __global__ void l3_kernel(const __nv_bfloat16 *A2, int H, const float *w3, const float *b3, int B, float *y,
-                          const int64_t *ms, double mu, double sigma, float *dy, float *loss) {
+                          const int64_t *ms, double mu, double sigma, float *dy, float *sq) {
     const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (warp >= B) return;
@@ -124,9 +125,23 @@ __global__ void l3_kernel(const __nv_bfloat16 *A2, int H, const float *w3, const
             const float t = (float)((log((double)ms[warp]) - mu) / sigma);
             const float d = yy - t;
             dy[warp] = 2.f * d / (float)B;
-            atomicAdd(loss, d * d / (float)B);
+            sq[warp] = d * d;
         }
     }
+}
+
+// loss = mean of sq[0 .. B), one block in a fixed order (deterministic).
+__global__ void loss_kernel(const float *sq, int B, float *loss) {
+    __shared__ float part[1024];
+    float s = 0.f;
+    for (int i = threadIdx.x; i < B; i += blockDim.x) s += sq[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = part[0] / (float)B;
 }
 
 // dZ2 = bf16(dy w3^T * [A2 > 0]) and its transpose, 32 x 32 tiles.
@@ -315,9 +330,9 @@ int forward(hesp_surrogate *s, const int8_t *lv, int B, const int64_t *ms, float
         RC(launch_gemm_onehot(lvg, ld, (int)s->n_base, s->n_levels, s->W1b, Fp, g, st));
     }
     RC(gemm(s->A1, H, s->W2b, H, B, H, H, 1, nullptr, 0, s->b2, s->A2, H, nullptr, 0, nullptr, 0, s->err, st));
-    if (backward) CK(cudaMemsetAsync(s->loss, 0, sizeof(float), st));
     l3_kernel<<<(unsigned)((B * 32 + 255) / 256), 256, 0, st>>>(s->A2, H, s->w3, s->b3, B, pred, ms, s->mu, s->sigma,
-                                                               s->dy, s->loss);
+                                                               s->dy, s->sq);
+    if (backward) loss_kernel<<<1, 1024, 0, st>>>(s->sq, B, s->loss);
     CK(cudaGetLastError());
     if (!backward) return HESP_OK;
     dz2_kernel<<<dim3((unsigned)((H + 31) / 32), (unsigned)((B + 31) / 32)), dim3(32, 8), 0, st>>>(
@@ -409,7 +424,7 @@ int hesp_surrogate_create(int32_t n_base, int32_t n_levels, int32_t hidden, int3
     };
     const size_t o_f = take(4 * (size_t)nparam * sizeof(float));
     const size_t o_y = take(B * sizeof(float));
-    const size_t o_dy = take(B * sizeof(float));
+    const size_t o_dy = take(B * sizeof(float)), o_sq = take(B * sizeof(float));
     const size_t o_loss = take(sizeof(float) + sizeof(int32_t) + 2 * sizeof(double));
     const size_t o_W1b = take(nW1 * 2), o_W2b = take(nW2 * 2), o_W2Tb = take(nW2 * 2);
     const size_t o_lv = take((size_t)B * n_base), o_ms = take(B * 8);
@@ -439,6 +454,7 @@ int hesp_surrogate_create(int32_t n_base, int32_t n_levels, int32_t hidden, int3
     s->y = (float *)(m + o_y);
     s->dy = (float *)(m + o_dy);
     s->loss = (float *)(m + o_loss);
+    s->sq = (float *)(m + o_sq);
     s->err = (int32_t *)(m + o_loss + sizeof(float));
     s->W1b = (__nv_bfloat16 *)(m + o_W1b);
     s->W2b = (__nv_bfloat16 *)(m + o_W2b);
@@ -624,3 +640,134 @@ int hesp_surrogate_error(hesp_surrogate *s, int32_t *err_host) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- checkpoints
+// File layout, little-endian: the 8 bytes "HESPSUR1"; int32 n_base,
+// n_levels, H, max_batch; uint64 seed; int64 step; float64 mu, sigma; int64
+// F, Fp; then the six FP32 tensors (W1, b1, W2, b2, w3, b3) of the
+// parameters, of the Adam first moments and of the second moments; then the
+// 64-bit FNV-1a hash of every byte before it.
+
+namespace {
+
+constexpr char kMagic[8] = {'H', 'E', 'S', 'P', 'S', 'U', 'R', '1'};
+
+struct CkptHeader {
+    char magic[8];
+    int32_t n_base, n_levels, H, max_batch;
+    uint64_t seed;
+    int64_t step;
+    double mu, sigma;
+    int64_t F, Fp;
+};
+
+uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+int64_t ckpt_floats(const hesp_surrogate *s) {
+    float *ptrs[6];
+    int64_t sizes[6];
+    tensor_list(s, 0, ptrs, sizes);
+    int64_t tot = 0;
+    for (int t = 0; t < 6; ++t) tot += sizes[t];
+    return tot;
+}
+
+}  // namespace
+
+int hesp_surrogate_save(const hesp_surrogate *s, const char *path) {
+    if (!s || !path) return HESP_ERR_ARG;
+    CkptHeader hd;
+    memset(&hd, 0, sizeof hd);
+    memcpy(hd.magic, kMagic, 8);
+    hd.n_base = s->n_base;
+    hd.n_levels = s->n_levels;
+    hd.H = s->H;
+    hd.max_batch = s->max_batch;
+    hd.seed = s->seed;
+    hd.step = s->step;
+    hd.mu = s->mu;
+    hd.sigma = s->sigma;
+    hd.F = s->F;
+    hd.Fp = s->Fp;
+    const int64_t nf = ckpt_floats(s);
+    float *buf = (float *)malloc((size_t)nf * sizeof(float));
+    if (!buf) return HESP_ERR_CAPACITY;
+    char *tmp = (char *)malloc(strlen(path) + 8);
+    if (!tmp) {
+        free(buf);
+        return HESP_ERR_CAPACITY;
+    }
+    sprintf(tmp, "%s.tmp", path);
+    FILE *f = fopen(tmp, "wb");
+    int rc = f ? HESP_OK : HESP_ERR_ARG;
+    uint64_t h = 0xcbf29ce484222325ull;
+    if (rc == HESP_OK) {
+        h = fnv1a(h, &hd, sizeof hd);
+        if (fwrite(&hd, sizeof hd, 1, f) != 1) rc = HESP_ERR_ARG;
+    }
+    const int which[3] = {0, 2, 3};
+    for (int k = 0; k < 3 && rc == HESP_OK; ++k) {
+        rc = hesp_surrogate_get(s, which[k], buf, nf);
+        if (rc) break;
+        h = fnv1a(h, buf, (size_t)nf * sizeof(float));
+        if (fwrite(buf, sizeof(float), (size_t)nf, f) != (size_t)nf) rc = HESP_ERR_ARG;
+    }
+    if (rc == HESP_OK && fwrite(&h, sizeof h, 1, f) != 1) rc = HESP_ERR_ARG;
+    if (f && fclose(f) != 0 && rc == HESP_OK) rc = HESP_ERR_ARG;
+    if (rc == HESP_OK && rename(tmp, path) != 0) rc = HESP_ERR_ARG;
+    if (rc != HESP_OK) remove(tmp);
+    free(tmp);
+    free(buf);
+    return rc;
+}
+
+int hesp_surrogate_load(const char *path, hesp_surrogate **out) {
+    if (!path || !out) return HESP_ERR_ARG;
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) return HESP_ERR_ARG;
+    CkptHeader hd;
+    if (fread(&hd, sizeof hd, 1, f) != 1 || memcmp(hd.magic, kMagic, 8) != 0) {
+        fclose(f);
+        return HESP_ERR_ARG;
+    }
+    hesp_surrogate *s = nullptr;
+    int rc = hesp_surrogate_create(hd.n_base, hd.n_levels, hd.H, hd.max_batch, hd.seed, &s);
+    if (rc) {
+        fclose(f);
+        return rc;
+    }
+    if (s->F != hd.F || s->Fp != hd.Fp || !(hd.sigma > 0) || hd.step < 0) rc = HESP_ERR_ARG;
+    const int64_t nf = ckpt_floats(s);
+    float *buf[3] = {nullptr, nullptr, nullptr};
+    uint64_t h = fnv1a(0xcbf29ce484222325ull, &hd, sizeof hd);
+    for (int k = 0; k < 3 && rc == HESP_OK; ++k) {
+        buf[k] = (float *)malloc((size_t)nf * sizeof(float));
+        if (!buf[k]) rc = HESP_ERR_CAPACITY;
+        else if (fread(buf[k], sizeof(float), (size_t)nf, f) != (size_t)nf) rc = HESP_ERR_ARG;
+        else h = fnv1a(h, buf[k], (size_t)nf * sizeof(float));
+    }
+    uint64_t want = 0;
+    if (rc == HESP_OK && (fread(&want, sizeof want, 1, f) != 1 || want != h)) rc = HESP_ERR_ARG;
+    if (rc == HESP_OK && fgetc(f) != EOF) rc = HESP_ERR_ARG;  // trailing bytes
+    fclose(f);
+    const int which[3] = {0, 2, 3};
+    for (int k = 0; k < 3 && rc == HESP_OK; ++k) rc = hesp_surrogate_set(s, which[k], buf[k], nf);
+    for (int k = 0; k < 3; ++k) free(buf[k]);
+    if (rc == HESP_OK) {
+        s->step = hd.step;
+        s->mu = hd.mu;
+        s->sigma = hd.sigma;
+        *out = s;
+    } else {
+        hesp_surrogate_destroy(s);
+    }
+    return rc;
+}

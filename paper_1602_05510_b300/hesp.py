@@ -39,7 +39,7 @@ EXPORTS = (
     "hesp_sim_autotune", "hesp_sort_cands_workspace_size", "hesp_sort_cands_by_size", "hesp_platform_set_policy",
     "hesp_simulate_critical", "hesp_solver_moves", "hesp_solver_pick", "hesp_schedule_metrics",
     "hesp_sim_workspace_size_kept", "hesp_simulate_batch_keep", "hesp_simulate_batch_reuse",
-    "hesp_platform_set_cache",
+    "hesp_platform_set_cache", "hesp_surrogate_save", "hesp_surrogate_load",
 )
 CACHE_WB, CACHE_WT, CACHE_WA = 0, 1, 2
 SOLVER_ALL, SOLVER_CP, SOLVER_SHALLOW = 0, 1, 2
@@ -112,6 +112,8 @@ def lib():
                                      vp, vp]
         f32, f64 = ctypes.c_float, ctypes.c_double
         L.hesp_surrogate_create.argtypes = [i32, i32, i32, i32, u64, ctypes.POINTER(vp)]
+        L.hesp_surrogate_save.argtypes = [vp, ctypes.c_char_p]
+        L.hesp_surrogate_load.argtypes = [ctypes.c_char_p, vp]
         L.hesp_surrogate_destroy.argtypes = [vp]
         L.hesp_surrogate_destroy.restype = None
         L.hesp_surrogate_shape.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)]
@@ -440,10 +442,13 @@ class Surrogate:
 
     PARTS = ("W1", "b1", "W2", "b2", "w3", "b3")
 
-    def __init__(self, n_base, n_levels, hidden=512, max_batch=4096, seed=0):
+    def __init__(self, n_base, n_levels, hidden=512, max_batch=4096, seed=0, _handle=None):
         h = ctypes.c_void_p()
-        check(lib().hesp_surrogate_create(n_base, n_levels, hidden, max_batch, seed, ctypes.byref(h)),
-              "hesp_surrogate_create")
+        if _handle is None:
+            check(lib().hesp_surrogate_create(n_base, n_levels, hidden, max_batch, seed, ctypes.byref(h)),
+                  "hesp_surrogate_create")
+        else:
+            h = _handle
         self.h = h
         F, Fp, H = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
         check(lib().hesp_surrogate_shape(h, ctypes.byref(F), ctypes.byref(Fp), ctypes.byref(H)),
@@ -452,6 +457,20 @@ class Surrogate:
         self.max_batch = max_batch
         self.sizes = (self.H * self.Fp, self.H, self.H * self.H, self.H, self.H, 1)
         self.shapes = ((self.H, self.Fp), (self.H,), (self.H, self.H), (self.H,), (self.H,), (1,))
+
+    def save(self, path):
+        """hesp_surrogate_save: parameters, Adam state and statistics to a file."""
+        check(lib().hesp_surrogate_save(self.h, os.fsencode(path)), "hesp_surrogate_save")
+
+    @classmethod
+    def load(cls, path):
+        """hesp_surrogate_load: a new surrogate from a saved file."""
+        h = ctypes.c_void_p()
+        check(lib().hesp_surrogate_load(os.fsencode(path), ctypes.byref(h)), "hesp_surrogate_load")
+        import struct
+        with open(path, "rb") as f:
+            n_base, n_levels, H, max_batch = struct.unpack("<4i", f.read(24)[8:24])
+        return cls(n_base, n_levels, H, max_batch, _handle=h)
 
     def _flat(self, parts):
         return np.concatenate([np.asarray(parts[k], np.float32).reshape(-1) for k in self.PARTS])
