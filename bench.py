@@ -544,6 +544,71 @@ def run_uneven(args):
     print(json.dumps(line))
 
 
+def run_exhaustive(args):
+    """The exhaustive search of the 3 x 3-tile problem (N = 3072, b = 1024):
+    all 1,024 partitions (each base task split once or not), generated,
+    simulated on 4 CPU + 1 GPU-type processors and reduced to the best
+    makespan on the device, captured as one CUDA graph and replayed; the
+    oracle runs the same search on the host cores."""
+    import torch
+
+    import oracle as O
+    from paper_1602_05510_b300 import build, hesp
+
+    build.build()
+    C, n, b, L = 1024, 3, 1024, 1
+    spec = W.PLATFORMS["cfg0"]
+    plat = hesp.Platform(spec)
+    ws = hesp.alloc_workspace(plat, n, L, C)
+    s = torch.cuda.Stream()
+    levels = torch.empty(C * 10, dtype=torch.int8, device="cuda")
+    cands = torch.empty(C * 16, dtype=torch.uint8, device="cuda")
+    ms = torch.empty(C, dtype=torch.int64, device="cuda")
+    st = torch.empty(C, dtype=torch.int32, device="cuda")
+    nt = torch.empty(C, dtype=torch.int64, device="cuda")
+    best = torch.empty(2, dtype=torch.int64, device="cuda")
+    R = 50  # exhaustive searches per graph
+
+    def step():
+        for _ in range(R):
+            hesp.generate_candidates(hesp.GEN_EXHAUSTIVE, 0, 0, C, n, b, 2, levels, cands, stream=s)
+            hesp.simulate_batch(plat, cands, levels, C, n, L, ws, makespan=ms, status=st, ntasks=nt, stream=s)
+            hesp.best_makespan(ms, st, nt, out=best, stream=s)
+
+    step()
+    s.synchronize()
+    g = hesp.Graph.capture(s, step)
+    for _ in range(max(args.warmup, 3)):
+        g.launch(s)
+    s.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b_ in ev:
+        a.record(s)
+        g.launch(s)
+        b_.record(s)
+    s.synchronize()
+    t = sum(a.elapsed_time(b_) for a, b_ in ev) / 1e3
+    searches = R * args.steps
+    tasks = int(nt.sum().item())
+    best_ms, _ = (int(x) for x in best.cpu().numpy())
+    lv_host = W.exhaustive_levels(10)
+    pl = O.make_platform(spec)
+    t0 = time.perf_counter()
+    oms, ost, otasks = O.simulate_many(pl, n, b, lv_host, threads=os.cpu_count() or 1)
+    t_cpu = time.perf_counter() - t0
+    assert (ost == 0).all() and int(oms.min()) == best_ms
+    line = {"metric": "sim task-events/s (bit-exact)", "value": tasks * searches / t, "unit": "task-events/s",
+            "n_gpus": 1, "steps": args.steps, "higher_is_better": True,
+            "workload": "exhaustive search, N=3072, b=1024 (3x3 tiles, 10 base tasks split once or not: 1,024 "
+                        "partitions, %d task-events), 4 CPU + 1 GPU-type processors; %d searches per CUDA graph"
+                        % (tasks, R),
+            "us_per_search": 1e6 * t / searches, "best_makespan": best_ms,
+            "best_partition_count": int((oms == best_ms).sum()),
+            "cpu_baseline": {"value": int(otasks.sum()) / t_cpu, "unit": "task-events/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "us_per_search": 1e6 * t_cpu}}
+    print(json.dumps(line))
+
+
 def run_search(args):
     """32 x 32 tiles (5984 base tasks, levels 0..3) on 32 CPU + 2 GPU-type
     processors: plain batched random search against surrogate-guided search,
@@ -681,7 +746,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=256)
     ap.add_argument("--candidates", type=int, default=N_CAND,
                     help="candidates per step (default: the workload's 65,536; smaller only for profiling)")
-    ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search", "uneven", "solver", "table1"],
+    ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search", "uneven", "solver", "table1", "exhaustive"],
                     help="random: the default benchmark line; surrogate: label/train/rank/re-score "
                          "pipeline; search: surrogate-guided vs random search")
     ap.add_argument("--labels", type=int, default=1 << 20)
@@ -708,6 +773,8 @@ def main():
         return run_solver(args)
     if args.workload == "table1":
         return run_table1(args)
+    if args.workload == "exhaustive":
+        return run_exhaustive(args)
     if args.impl == "reference":
         run_reference(args)
     else:
