@@ -75,7 +75,9 @@ class Platform(ctypes.Structure):
         ("select", ctypes.c_int32),
         ("rp_seed", ctypes.c_uint64),
         ("cache", ctypes.c_int32),
-        ("pad_", ctypes.c_int32),
+        ("use_links", ctypes.c_int32),
+        ("link_lat", (ctypes.c_int64 * MAX_MEMS) * MAX_MEMS),
+        ("link_bw", (ctypes.c_int64 * MAX_MEMS) * MAX_MEMS),
     ]
 
 
@@ -126,11 +128,13 @@ CACHE_WB, CACHE_WT, CACHE_WA = 0, 1, 2
 
 
 def make_platform(desc, order: int = ORDER_FCFS, select: int = SELECT_EFT, rp_seed: int = 0,
-                  cache: int = CACHE_WB) -> Platform:
+                  cache: int = CACHE_WB, links=None) -> Platform:
     """Oracle platform from a plain description (a dict or an object with the
     fields of ``paper_1602_05510_b300.workloads.PlatformSpec``), with the
     task order (FCFS / PL), the processor selection (EFT-P / EIT-P / F-P /
-    R-P), the seed of R-P's draws and the caching policy (WB / WT / WA)."""
+    R-P), the seed of R-P's draws, the caching policy (WB / WT / WA) and,
+    optionally, per-link costs {(src, dst): (latency_ns, bytes_per_ns)} (the
+    other pairs keep the platform's scalars)."""
     g = (lambda k: desc[k]) if isinstance(desc, dict) else (lambda k: getattr(desc, k))
     pl = Platform()
     pl.n_mem = g("n_mem")
@@ -156,6 +160,13 @@ def make_platform(desc, order: int = ORDER_FCFS, select: int = SELECT_EFT, rp_se
     for i, (op, ty, bs, ns) in enumerate(ovr):
         pl.ovr_op[i], pl.ovr_type[i], pl.ovr_bs[i], pl.ovr_ns[i] = op, ty, bs, ns
     pl.order, pl.select, pl.rp_seed, pl.cache = order, select, rp_seed, cache
+    if links:
+        pl.use_links = 1
+        for s_ in range(MAX_MEMS):
+            for d_ in range(MAX_MEMS):
+                lat, bw = links.get((s_, d_), (pl.xfer_latency_ns, pl.bw_bytes_per_ns))
+                pl.link_lat[s_][d_] = lat
+                pl.link_bw[s_][d_] = bw
     return pl
 
 

@@ -78,7 +78,12 @@ typedef struct {
     /* caching of accelerator memories (Sec. 2.1): 0 = write-back (WB),
      * 1 = write-through (WT), 2 = write-around (WA) */
     int32_t cache;
-    int32_t pad_;
+    /* network topology: with use_links, a message from memory s to memory d
+     * takes link_lat[s][d] + ceil(bytes / link_bw[s][d]) ns (a direct link per
+     * ordered pair, no contention); otherwise every pair uses the scalars */
+    int32_t use_links;
+    int64_t link_lat[OR_MAX_MEMS][OR_MAX_MEMS];
+    int64_t link_bw[OR_MAX_MEMS][OR_MAX_MEMS];
 } or_platform;
 
 /* A square data region in element coordinates of the full matrix. */
@@ -134,6 +139,13 @@ int64_t or_exec_ns(const or_platform *p, int32_t op, int32_t type, int64_t bs) {
 int64_t or_xfer_ns(const or_platform *p, int64_t elems) {
     __int128 bytes = (__int128)elems * p->bytes_per_elem;
     return p->xfer_latency_ns + ceil_div128(bytes, p->bw_bytes_per_ns);
+}
+
+/* A message of `elems` elements from memory s to memory d. */
+int64_t or_xfer_pair_ns(const or_platform *p, int32_t s, int32_t d, int64_t elems) {
+    if (!p->use_links) return or_xfer_ns(p, elems);
+    __int128 bytes = (__int128)elems * p->bytes_per_elem;
+    return p->link_lat[s][d] + ceil_div128(bytes, p->link_bw[s][d]);
 }
 
 /* ------------------------------------------------------------------ */
@@ -703,7 +715,7 @@ static int schedule_task(sched_state *S, int32_t j, int64_t t) {
         for (int sm = 0; sm < M; sm++) {
             arrive[m][sm] = 0;
             if (elems_from[sm] > 0) {
-                arrive[m][sm] = depart[sm] + or_xfer_ns(pl, elems_from[sm]);
+                arrive[m][sm] = depart[sm] + or_xfer_pair_ns(pl, sm, m, elems_from[sm]);
                 if (arrive[m][sm] > drt[m]) drt[m] = arrive[m][sm];
             }
         }
@@ -760,7 +772,8 @@ static int schedule_task(sched_state *S, int32_t j, int64_t t) {
      * arrival.  Every other copy is invalidated. */
     int64_t written = 0;
     for (int64_t e = 0; e < na; e++) written += axw[e];
-    const int64_t through = ms != 0 && pl->cache != 0 ? best_eft + or_xfer_ns(pl, written * atom_elems) : best_eft;
+    const int64_t through =
+        ms != 0 && pl->cache != 0 ? best_eft + or_xfer_pair_ns(pl, ms, 0, written * atom_elems) : best_eft;
     for (int64_t e = 0; e < na; e++) {
         if (!axw[e]) continue;
         int64_t x = ax[e];
@@ -845,6 +858,10 @@ int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *c
     if (!pl || pl->n_mem < 1 || pl->n_mem > OR_MAX_MEMS || pl->n_procs < 1 || pl->n_procs > OR_MAX_PROCS)
         return OR_ERR_ARG;
     if (pl->n_mem > 1 && pl->bw_bytes_per_ns < 1) return OR_ERR_ARG;
+    if (pl->use_links)
+        for (int s = 0; s < pl->n_mem; s++)
+            for (int d = 0; d < pl->n_mem; d++)
+                if (s != d && (pl->link_bw[s][d] < 1 || pl->link_lat[s][d] < 0)) return OR_ERR_ARG;
     for (int p = 0; p < pl->n_procs; p++)
         if (pl->proc_mem[p] < 0 || pl->proc_mem[p] >= pl->n_mem || pl->proc_type[p] < 0 ||
             pl->proc_type[p] >= pl->n_types)

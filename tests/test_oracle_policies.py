@@ -362,3 +362,45 @@ def test_cache_replay(cache, order, select, key, n, b):
         s_, f_ = replay(spec, n, b, lv, o, [int(r["proc"][j]) for j in o], issue=r["issue"], cache=cache)
         assert [s_[j] for j in range(r["n_tasks"])] == r["start"].tolist()
         assert [f_[j] for j in range(r["n_tasks"])] == r["finish"].tolist()
+
+
+# ---------------------------------------------------------------- network topology
+
+def test_link_costs_worked_example():
+    g = GOLD["n2_b1024_cpu4_gpu1_fast_host_link"]
+    links = {(s, d): (lat, bw) for s, d, lat, bw in g["links"]}
+    r = O.simulate(O.make_platform(W.PLATFORMS["cfg0"], links=links), 2, 1024, g["levels"])
+    assert r["proc"].tolist() == g["proc"] and r["finish"].tolist() == g["finish"]
+    r2 = O.simulate(O.make_platform(W.PLATFORMS["cfg0"], links={(1, 0): (1000, 24)}), 2, 1024, g["levels"])
+    assert r2["makespan"] == GOLD["n2_b1024_all_level0_cpu4_gpu1"]["makespan"]
+
+
+def test_uniform_links_equal_the_scalar_model():
+    spec = W.PLATFORMS["cfg2"]
+    uni = {(s, d): (spec.xfer_latency_ns, spec.bw_bytes_per_ns) for s in range(3) for d in range(3) if s != d}
+    rng = np.random.default_rng(21)
+    for _ in range(3):
+        lv = rng.integers(0, 3, O.base_count(3)).astype(np.int8)
+        a = O.simulate(O.make_platform(spec), 3, 1024, lv)
+        b = O.simulate(O.make_platform(spec, links=uni), 3, 1024, lv)
+        assert np.array_equal(a["start"], b["start"]) and np.array_equal(a["proc"], b["proc"])
+
+
+@pytest.mark.parametrize("cache", [0, 1, 2])
+@pytest.mark.parametrize("key,n,b", [("cfg2", 3, 1024), ("cfg4", 2, 2048), ("cfg1a", 3, 2048)])
+def test_link_replay(cache, key, n, b):
+    """Asymmetric per-link costs (a fast GPU-GPU link, slow host links): an
+    independent replay reproduces every start and finish."""
+    spec = W.PLATFORMS[key]
+    links = {(0, 1): (20000, 6), (1, 0): (15000, 9)}
+    if spec.n_mem > 2:
+        links.update({(1, 2): (1000, 50), (2, 1): (1500, 40), (0, 2): (9000, 12), (2, 0): (4000, 30)})
+    rng = np.random.default_rng(cache + n)
+    for _ in range(3):
+        lv = rng.integers(0, 3, O.base_count(n)).astype(np.int8)
+        r = O.simulate(O.make_platform(spec, cache=cache, links=links), n, b, lv)
+        assert r["status"] == 0
+        o = r["order"].tolist()
+        s_, f_ = replay(spec, n, b, lv, o, [int(r["proc"][j]) for j in o], cache=cache, links=links)
+        assert [s_[j] for j in range(r["n_tasks"])] == r["start"].tolist()
+        assert [f_[j] for j in range(r["n_tasks"])] == r["finish"].tolist()

@@ -121,13 +121,20 @@ def test_worked_example_with_transfers(key, ncpu):
 # ----------------------------------------------- replay and brute force
 
 
-def replay(spec, n, b, levels, order, procs, atom_level=None, issue=None, cache=0):
+def replay(spec, n, b, levels, order, procs, atom_level=None, issue=None, cache=0, links=None):
     """Evaluate a given (task order, assignment) with the caching and
     transfer rules, each task issued at its release time (the latest finish
     of its predecessors), or at issue[j] when given.  cache: 0 write-back,
-    1 write-through, 2 write-around.  Independent of the oracle's event
-    loop."""
+    1 write-through, 2 write-around.  links: {(src, dst): (latency_ns,
+    bytes_per_ns)} for pairs whose cost differs from the platform's.
+    Independent of the oracle's event loop."""
     pl = O.make_platform(spec)
+
+    def xfer(s, d, elems):
+        if links and (s, d) in links:
+            lat, bw = links[(s, d)]
+            return lat + -(-(elems * spec.bytes_per_elem) // bw)
+        return O.xfer_ns(pl, elems)
     code = O.levels_to_code(n, levels)
     d = O.expand(n, b, code)
     L = int(max(levels)) if atom_level is None else atom_level
@@ -172,7 +179,7 @@ def replay(spec, n, b, levels, order, procs, atom_level=None, issue=None, cache=
         arr = {}
         for s, v in groups.items():
             dep = max([t] + [vfrom.get((x, s), 0) for x in v])
-            arr[s] = dep + O.xfer_ns(pl, len(v) * a * a)
+            arr[s] = dep + xfer(s, m, len(v) * a * a)
         drt = max([drt] + list(arr.values()))
         ex = O.exec_ns(pl, int(d["op"][j]), spec.procs[p][1], int(d["bs"][j]))
         st = max(t, avail[p], drt)
@@ -181,7 +188,7 @@ def replay(spec, n, b, levels, order, procs, atom_level=None, issue=None, cache=
                 valid[(x, m)] = True
                 vfrom[(x, m)] = arr[s]
         written = [x for x, w in xs if w]
-        through = st + ex + O.xfer_ns(pl, len(written) * a * a)
+        through = st + ex + xfer(m, 0, len(written) * a * a)
         for x in written:
             for mm in range(M):
                 valid[(x, mm)] = False
