@@ -146,6 +146,13 @@ int hesp_platform_set_policy(hesp_platform *p, int32_t order, int32_t select, ui
 #define HESP_CACHE_WT 1
 #define HESP_CACHE_WA 2
 int hesp_platform_set_cache(hesp_platform *p, int32_t cache);
+/* Network topology (Sec. 2): a direct link per ordered pair of memories.
+ * After this call a message from memory src to memory dst of E elements
+ * takes latency_ns + ceil(E * bytes_per_elem / bw_bytes_per_ns) ns; pairs
+ * never set keep the platform's xfer_latency_ns / bw_bytes_per_ns.  Links
+ * carry any number of messages at once (no contention).  ERR_ARG for src ==
+ * dst, a memory out of range, latency < 0 or bandwidth < 1. */
+int hesp_platform_set_link(hesp_platform *p, int32_t src, int32_t dst, int64_t latency_ns, int64_t bw_bytes_per_ns);
 /* Host queries of the models, as used by the simulator. */
 int hesp_platform_exec_ns(const hesp_platform *p, int32_t op, int32_t type, int64_t block, int64_t *ns_out);
 int hesp_platform_xfer_ns(const hesp_platform *p, int64_t elems, int64_t *ns_out);

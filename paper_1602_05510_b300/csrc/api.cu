@@ -50,7 +50,7 @@ Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem, int64_t ta
     a.off_lw = o; o = align256(o + 4 * a.Acap);
     a.off_vfrom = o; o = align256(o + 8 * a.Acap * mp);
     a.off_bitmap = o; o = align256(o + 4 * ((a.Tcap + 31) / 32));
-    a.off_xt = o; o = align256(o + 8 * a.Kcap);
+    a.off_xt = o; o = align256(o + 8 * a.Kcap * (n_mem > 1 ? HESP_MAX_MEMS * HESP_MAX_MEMS : 1));  // per link
     a.off_hist = o; o = align256(o + 4 * 256);  // radix histogram of the priority-list sort
     a.off_pend0 = o; o = align256(o + 2 * a.Tcap);  // keep / reuse: the DAG's initial pending counts
     a.off_hdr = o; o = align256(o + 64);            // keep / reuse: the candidate's header
@@ -75,6 +75,12 @@ static DevPlatform dev_platform(const hesp_platform *p) {
     d.select = p->select;
     d.rp_seed = p->rp_seed;
     d.cache = p->cache;
+    d.use_links = p->use_links;
+    for (int s = 0; s < HESP_MAX_MEMS; ++s)
+        for (int t = 0; t < HESP_MAX_MEMS; ++t) {
+            d.link_lat[s * HESP_MAX_MEMS + t] = p->use_links ? p->link_lat[s][t] : p->xfer_latency_ns;
+            d.link_bw[s * HESP_MAX_MEMS + t] = p->use_links ? p->link_bw[s][t] : p->bw_bytes_per_ns;
+        }
     for (int op = 0; op < 4; ++op)
         for (int l = 0; l < HESP_LB; ++l) {
             int64_t s = 0;
@@ -196,6 +202,24 @@ int hesp_platform_set_policy(hesp_platform *p, int32_t order, int32_t select, ui
     p->order = order;
     p->select = select;
     p->rp_seed = rp_seed;
+    return HESP_OK;
+}
+
+int hesp_platform_set_link(hesp_platform *p, int32_t src, int32_t dst, int64_t latency_ns, int64_t bw_bytes_per_ns) {
+    if (!p || src < 0 || dst < 0 || src >= p->n_mem || dst >= p->n_mem || src == dst || latency_ns < 0 ||
+        bw_bytes_per_ns < 1)
+        return HESP_ERR_ARG;
+    if (latency_ns > (1LL << 40)) return HESP_ERR_UNSUPPORTED;
+    if (!p->use_links) {  // every other pair keeps the platform's scalars
+        for (int s = 0; s < HESP_MAX_MEMS; ++s)
+            for (int t = 0; t < HESP_MAX_MEMS; ++t) {
+                p->link_lat[s][t] = p->xfer_latency_ns;
+                p->link_bw[s][t] = p->bw_bytes_per_ns;
+            }
+        p->use_links = 1;
+    }
+    p->link_lat[src][dst] = latency_ns;
+    p->link_bw[src][dst] = bw_bytes_per_ns;
     return HESP_OK;
 }
 

@@ -25,6 +25,10 @@ struct hesp_platform {
     int32_t order, select;
     uint64_t rp_seed;
     int32_t cache;  // 0 write-back, 1 write-through, 2 write-around
+    // network topology: with use_links, a message s -> d takes
+    // link_lat[s][d] + ceil(bytes / link_bw[s][d]) ns
+    int32_t use_links;
+    int64_t link_lat[HESP_MAX_MEMS][HESP_MAX_MEMS], link_bw[HESP_MAX_MEMS][HESP_MAX_MEMS];
 };
 
 struct hesp_dag {
@@ -59,7 +63,8 @@ struct DevPlatform {
     int32_t n_mem, n_types, n_procs, pad;
     int32_t order, select;  // task order (0 FCFS, 1 PL) and processor choice (0 EFT-P, 1 EIT-P, 2 F-P, 3 R-P)
     uint64_t rp_seed;       // R-P: seed of the per-task draws
-    int32_t cache, pad2;    // caching policy (0 WB, 1 WT, 2 WA)
+    int32_t cache, use_links;  // caching policy (0 WB, 1 WT, 2 WA); per-link transfer costs
+    int64_t link_lat[HESP_MAX_MEMS * HESP_MAX_MEMS], link_bw[HESP_MAX_MEMS * HESP_MAX_MEMS];
     int64_t exec[4 * HESP_MAX_TYPES * HESP_LB];
     int64_t wsum[4 * HESP_LB];  // task time summed over all processors, per (op, log2 block); -1 if any is -1
     int8_t proc_mem[HESP_MAX_PROCS];

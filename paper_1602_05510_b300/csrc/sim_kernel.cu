@@ -337,7 +337,7 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
                                                  const int8_t *s_ptype, const int pm[NS], const int pt[NS],
                                                  const bool pv[NS], int64_t avail[NS], int head[NS], int tail[NS],
                                                  int64_t hfin[NS], int64_t &mk, bool &ok, int64_t sched_base,
-                                                 int sel, uint64_t rp_seed, int cache) {
+                                                 int sel, uint64_t rp_seed, int cache, bool links) {
     const uint64_t d = at<uint64_t>(base, a.ar.off_desc)[j];
     const int32_t *const succoff = at<int32_t>(base, a.ar.off_succoff);
     const int se0 = succoff[j], se1 = succoff[j + 1];  // kept with the task while it is in flight
@@ -349,7 +349,12 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
     const int lb = lb_b - lvl;
     constexpr int MP = AtomState<M>::MP;
     int64_t *vfrom = at<int64_t>(base, a.ar.off_vfrom);
+    // transfer time of k atoms: one table, or (links) one per ordered pair
+    // of memories, table s * HESP_MAX_MEMS + d for messages s -> d
     const int64_t *xt = at<int64_t>(base, a.ar.off_xt);
+    auto xtab = [&](int s, int d) -> const int64_t * {
+        return links ? xt + (int64_t)(s * HESP_MAX_MEMS + d) * a.ar.Kcap : xt;
+    };
 
     int64_t drt_off[M];
     Counts<M> cnt;
@@ -434,7 +439,7 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
             for (int s = 0; s < M; ++s) {
                 if (s == m) continue;
                 const unsigned c = cnt.get(m, s);
-                if (c > 0) off = max(off, (cache != HESP_CACHE_WB ? (int64_t)dlead[m][s] : 0) + xt[c]);
+                if (c > 0) off = max(off, (cache != HESP_CACHE_WB ? (int64_t)dlead[m][s] : 0) + xtab(s, m)[c]);
             }
             drt_off[m] = off;
         }
@@ -514,7 +519,7 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
                     // in host memory, from finish + xfer(block)
                     const bool acc = ms != 0 && cache != HESP_CACHE_WB;
                     const int64_t v_ms = (cache == HESP_CACHE_WA && ms != 0) ? -1 : eft;
-                    const int64_t v_host = acc ? eft + xt[1 << sh] : -1;
+                    const int64_t v_host = acc ? eft + xtab(ms, 0)[1 << sh] : -1;
                     longlong2 w0, w1;
                     w0.x = ms == 0 ? v_ms : v_host;
                     w0.y = ms == 1 ? v_ms : -1;
@@ -544,7 +549,7 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
                                     c = cnt.get(m, s);
                                     lead = (int64_t)dlead[m][s];
                                 }
-                        px[ms] = t + lead + xt[c];
+                        px[ms] = t + lead + xtab(src < 0 ? 0 : src, ms)[c];
                     }
                 }
             }
@@ -872,13 +877,27 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                         *reinterpret_cast<longlong2 *>(vfrom + x * MP + 2) = v0;
                     }
                 }
-                // transfer time of k atoms (k * (b >> Lc)^2 elements)
+                // transfer time of k atoms (k * (b >> Lc)^2 elements): one
+                // table, or (links) one per ordered pair of memories
                 int64_t *const xt = at<int64_t>(base, a.ar.off_xt);
                 const int64_t ae = (int64_t)(b >> Lc) * (int64_t)(b >> Lc);
                 const int kmax = 3 << (2 * Lc);
                 for (int k = lane; k <= kmax; k += 32) {
                     const int64_t bytes = (int64_t)k * ae * pl.bpe;
                     xt[k] = k == 0 ? 0 : pl.lat + (bytes + pl.bw - 1) / pl.bw;
+                }
+                if (GEN && pl.use_links) {
+                    for (int pr = 0; pr < M * M; ++pr) {
+                        const int s = pr / M, d = pr % M;
+                        if (s == d) continue;
+                        int64_t *const xp = xt + (int64_t)(s * HESP_MAX_MEMS + d) * a.ar.Kcap;
+                        const int64_t lat = pl.link_lat[s * HESP_MAX_MEMS + d];
+                        const int64_t bw = pl.link_bw[s * HESP_MAX_MEMS + d];
+                        for (int k = lane; k <= kmax; k += 32) {
+                            const int64_t bytes = (int64_t)k * ae * pl.bpe;
+                            xp[k] = k == 0 ? 0 : lat + (bytes + bw - 1) / bw;
+                        }
+                    }
                 }
             }
             // GEN = false: the FCFS + EFT-P + write-back instantiation; GEN =
@@ -887,6 +906,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
             const bool waits = GEN && sel >= HESP_SELECT_FP;  // F-P, R-P: idle processors only
             const uint64_t rp_seed = pl.rp_seed;
             const int cache = GEN ? pl.cache : HESP_CACHE_WB;
+            const bool links = GEN && pl.use_links;
             if (GEN && pl.order == HESP_ORDER_PL) {
                 // ---- PL: a priority list by critical time (HEFT-like); each task
                 // is scheduled at its release time, the latest finish among its
@@ -987,7 +1007,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                     }
                     const int64_t fj = schedule_task<M, NS, false, GEN>(j, tj, base, a, Lc, lb_b, lane, s_exec, s_pmem,
                                                                    s_ptype, pm, pt, pv, avail, head, tail, hfin, mk,
-                                                                   ok, sched_base, sel, rp_seed, cache);
+                                                                   ok, sched_base, sel, rp_seed, cache, links);
                     const int e0 = succoff[j], e1 = succoff[j + 1];
                     for (int e = e0 + lane; e < e1; e += 32) {
                         const int sj = succ[e];
@@ -1050,7 +1070,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                             continue;
                         }
                         schedule_task<M, NS, true, GEN>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
-                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache);
+                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache, links);
                         ++scheduled;
                     }
                     direct = false;
@@ -1078,7 +1098,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                                 }
                                 schedule_task<M, NS, true, GEN>(jb + bit, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype,
                                                            pm, pt, pv, avail, head, tail, hfin, mk, ok, sched_base,
-                                                           sel, rp_seed, cache);
+                                                           sel, rp_seed, cache, links);
                                 ++scheduled;
                             }
                         }
@@ -1097,7 +1117,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
                         const int j = link[qh].rq;
                         ++qh;
                         schedule_task<M, NS, true, GEN>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
-                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache);
+                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache, links);
                         ++scheduled;
                     }
                 }
@@ -1373,7 +1393,7 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
     const bool two = p->n_procs > 32;
     const unsigned ub = (unsigned)blocks;
     const bool gen = p->order != HESP_ORDER_FCFS || p->select != HESP_SELECT_EFT || p->cache != HESP_CACHE_WB ||
-                     crit != nullptr;
+                     p->use_links || crit != nullptr;
     switch (p->n_mem) {
     case 1: two ? launch_one<1, 2>(gen, ub, threads, smem, stream, dp, a, ctr)
                 : launch_one<1, 1>(gen, ub, threads, smem, stream, dp, a, ctr); break;

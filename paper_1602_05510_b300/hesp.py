@@ -39,7 +39,7 @@ EXPORTS = (
     "hesp_sim_autotune", "hesp_sort_cands_workspace_size", "hesp_sort_cands_by_size", "hesp_platform_set_policy",
     "hesp_simulate_critical", "hesp_solver_moves", "hesp_solver_pick", "hesp_schedule_metrics",
     "hesp_sim_workspace_size_kept", "hesp_simulate_batch_keep", "hesp_simulate_batch_reuse",
-    "hesp_platform_set_cache", "hesp_surrogate_save", "hesp_surrogate_load",
+    "hesp_platform_set_cache", "hesp_surrogate_save", "hesp_surrogate_load", "hesp_platform_set_link",
 )
 CACHE_WB, CACHE_WT, CACHE_WA = 0, 1, 2
 SOLVER_ALL, SOLVER_CP, SOLVER_SHALLOW = 0, 1, 2
@@ -146,6 +146,7 @@ def lib():
         L.hesp_sort_cands_by_size.argtypes = [vp, vp, i64, vp, vp, vp, sz, vp]
         L.hesp_platform_set_policy.argtypes = [vp, i32, i32, u64]
         L.hesp_platform_set_cache.argtypes = [vp, i32]
+        L.hesp_platform_set_link.argtypes = [vp, i32, i32, i64, i64]
         L.hesp_best_makespan.argtypes = [vp, vp, vp, i64, vp, vp]
         L.hesp_gather_rows.argtypes = [vp, vp, i64, i64, vp, vp]
         L.hesp_generate_mutants.argtypes = [vp, i32, i32, i32, ctypes.c_double, u64, i64, i64, vp, vp]
@@ -175,7 +176,7 @@ class Platform:
     """A simulated platform (hesp_platform handle) built from a
     ``workloads.PlatformSpec``."""
 
-    def __init__(self, spec, order=0, select=0, rp_seed=0, cache=0):
+    def __init__(self, spec, order=0, select=0, rp_seed=0, cache=0, links=None):
         self.spec = spec
         L = lib()
         types = (_PType * len(spec.types))()
@@ -195,6 +196,8 @@ class Platform:
             check(L.hesp_platform_set_exec_table(h, op, ty, bs, ns), "hesp_platform_set_exec_table")
         check(L.hesp_platform_set_policy(h, order, select, rp_seed & ((1 << 64) - 1)), "hesp_platform_set_policy")
         check(L.hesp_platform_set_cache(h, cache), "hesp_platform_set_cache")
+        for (s_, d_), (lat, bw) in sorted((links or {}).items()):
+            check(L.hesp_platform_set_link(h, s_, d_, lat, bw), "hesp_platform_set_link")
 
     @property
     def n_mem(self):

@@ -261,7 +261,14 @@ def test_cfg4_full_size_candidates():
     check_parity(W.PLATFORMS["cfg4"], 32, 2048, lv, g, schedule=False)
 
 
-def policy_parity(order, select, cache=0):
+def links_for(spec):
+    links = {(0, 1): (20000, 6), (1, 0): (15000, 9)}
+    if spec.n_mem > 2:
+        links.update({(1, 2): (1000, 50), (2, 1): (1500, 40), (0, 2): (9000, 12), (2, 0): (4000, 30)})
+    return links
+
+
+def policy_parity(order, select, cache=0, with_links=False):
     seed = 0x8000000000000000 + 12345 * (order + 1)
     cases = [("cfg0", 3, 1024, W.workload_levels("cfg0")[::8], 1),
              ("cfg1a", 8, 2048, W.workload_levels("cfg1", 300, 48), 2),
@@ -270,7 +277,8 @@ def policy_parity(order, select, cache=0):
              ("cfg4", 5, 2048, np.random.default_rng(2).integers(0, 4, (16, W.base_count(5))).astype(np.int8), 3)]
     for key, n, b, lv, L in cases:
         spec = W.PLATFORMS[key]
-        plat = hesp.Platform(spec, order=order, select=select, rp_seed=seed, cache=cache)
+        links = links_for(spec) if with_links and spec.n_mem > 1 else None
+        plat = hesp.Platform(spec, order=order, select=select, rp_seed=seed, cache=cache, links=links)
         C, nb = lv.shape
         d_lv = torch.from_numpy(np.ascontiguousarray(lv).reshape(-1).copy()).cuda()
         cands = hesp.cands_tensor(n, b, np.arange(C, dtype=np.int64) * nb)
@@ -286,7 +294,7 @@ def policy_parity(order, select, cache=0):
         torch.cuda.synchronize()
         ms, st = ms.cpu().numpy(), st.cpu().numpy()
         proc, start, fin = (x.cpu().numpy() for x in sched[1:])
-        pl = O.make_platform(spec, order=order, select=select, rp_seed=seed, cache=cache)
+        pl = O.make_platform(spec, order=order, select=select, rp_seed=seed, cache=cache, links=links)
         for c in range(C):
             r = O.simulate(pl, n, b, lv[c])
             assert st[c] == 0 and ms[c] == r["makespan"], (key, c)
@@ -308,6 +316,14 @@ def test_cache_policies_parity(cache, order, select):
     """Write-through and write-around caching (Sec. 2.1) against the oracle,
     with several task orders and processor choices: schedules bit-exact."""
     policy_parity(order, select, cache)
+
+
+@pytest.mark.parametrize("cache", [0, 1, 2])
+@pytest.mark.parametrize("order,select", [(0, 0), (1, 2)])
+def test_link_costs_parity(cache, order, select):
+    """Per-link transfer costs (asymmetric, a fast GPU-GPU link) against the
+    oracle: schedules bit-exact."""
+    policy_parity(order, select, cache, with_links=True)
 
 
 def test_maximum_tiles_and_empty_batch():
