@@ -284,8 +284,8 @@ def run_gpu(args):
 # for the kernel source they were taken on: DRAM bytes per 4,096 candidates on the
 # CPU+GPU platform (scaled to a launch by candidates; traffic grows in proportion)
 # and the share of issue slots busy.
-SIM_NCU = {"source_sha1_12": "8cf98aa5e230", "dram_bytes_per_4096": 1.360603e9 + 1.226109e9,
-           "issue_active_pct": 60.42, "warps_per_sm": 25.6, "alu_pipe_pct": 50.2}
+SIM_NCU = {"source_sha1_12": "fd7ba30af648", "dram_bytes_per_4096": 1.360899e9 + 1.227563e9,
+           "issue_active_pct": 60.41, "warps_per_sm": 25.7, "alu_pipe_pct": 50.3}
 
 
 def sim_source_matches():
