@@ -149,9 +149,18 @@ def run_gpu(args):
     else:
         ws = [hesp.alloc_workspace(p, N_TILES, MAX_LEVEL, C) for p in plats]
 
+    bst = torch.empty(C, dtype=torch.int32, device=dev)
+    build_apart = args.share_dag and not args.keep_in_first
+
+    def build(cands_, levels_):
+        # the DAGs alone, in a launch of their own (platform independent)
+        hesp.dag_build_kept(cands_, levels_, C, N_TILES, MAX_LEVEL, ws[0], status=bst)
+
     def simulate(i, p, cands_, levels_):
         if not args.share_dag:
             f = hesp.simulate_batch
+        elif build_apart:
+            f = hesp.simulate_batch_reuse
         else:
             f = hesp.simulate_batch_keep if i == 0 else hesp.simulate_batch_reuse
         f(p, cands_, levels_, C, N_TILES, MAX_LEVEL, ws[i], makespan=ms[i], status=stt[i], ntasks=nts[i])
@@ -171,6 +180,12 @@ def run_gpu(args):
         sim_c = cands
         if args.lpt:
             sim_c, _ = hesp.sort_cands_by_size(cands, levels, C, scands, perm, sort_ws)
+        if build_apart:
+            if ev is not None:
+                ev[-1][0].record(stream)
+            build(sim_c, levels)
+            if ev is not None:
+                ev[-1][1].record(stream)
         for i, p in enumerate(plats):
             if ev is not None:
                 ev[i][0].record(stream)
@@ -188,7 +203,8 @@ def run_gpu(args):
 
     K = args.steps
     step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    kern_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in plats]
+    # per step: one event pair per platform's simulation launch, and one for the DAG build
+    kern_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(len(plats) + 1)]
                for _ in range(K)]
     task_events = 0
     clocks = ClockSampler(local)
@@ -214,6 +230,7 @@ def run_gpu(args):
             raise RuntimeError("candidates failed on %s" % PLATS[i])
     t_steps = sum(step_ev[k][0].elapsed_time(step_ev[k][1]) for k in range(K)) / 1e3
     t_kern = [sum(kern_ev[k][i][0].elapsed_time(kern_ev[k][i][1]) for k in range(K)) / 1e3 for i in range(len(plats))]
+    t_build = (sum(kern_ev[k][-1][0].elapsed_time(kern_ev[k][-1][1]) for k in range(K)) / 1e3) if build_apart else None
     t_max, tot_events = reduce_timing(t_steps, task_events, world, dev)
 
     # ---- end to end through the public API with host buffers
@@ -236,6 +253,8 @@ def run_gpu(args):
             levels.copy_(lv_host[s % len(lv_host)], non_blocking=True)
             cands.copy_(cand_host, non_blocking=True)
             sim_c = hesp.sort_cands_by_size(cands, levels, C, scands, perm, sort_ws)[0] if args.lpt else cands
+            if build_apart:
+                build(sim_c, levels)
             for i, p in enumerate(plats):
                 simulate(i, p, sim_c, levels)
                 out_host[i].copy_(ms[i], non_blocking=True)
@@ -249,7 +268,8 @@ def run_gpu(args):
         t_e2e, e2e_tasks = reduce_timing(t_e2e, e2e_tasks, world, dev)
         e2e = {"value": e2e_tasks / t_e2e, "unit": UNIT, "h2d_bytes_per_step": C * nb + C * 16,
                "d2h_bytes_per_step": 8 * C * len(plats), "steps": args.e2e_steps,
-               "path": "pinned host partition vectors -> largest-first order -> hesp_simulate_batch x2 -> host makespans"}
+               "path": "pinned host partition vectors -> largest-first order -> DAG build -> simulation on both "
+                       "platforms -> host makespans"}
 
     if rank == 0:
         peaks = measured_peaks()
@@ -260,14 +280,19 @@ def run_gpu(args):
             "data": "synthetic (seeded SplitMix64 partition vectors generated on the device)",
             "config": dict(CONFIG, candidates_per_step=C,
                            parallelism="candidates sharded across ranks (dp%d)" % world,
-                           dag=("built once per candidate (first platform's launch keeps it, the second "
+                           dag=("built once per candidate in a launch of its own, then simulated on both "
+                                "platforms" if build_apart else
+                                "built once per candidate (the first platform's launch keeps it, the second "
                                 "simulates it)") if args.share_dag else "built in each platform's launch",
                            order="largest DAG first" if args.lpt else "generation order",
                            l2="256 MB buffer written between timed steps; per-step working set ~GBs > L2"),
             "candidates_per_s": 2 * C * world * K / t_max if t_max > 0 else None,
             "task_events": tot_events,
             "wall_s": wall,
-            "gpu_launches": (6 if args.lpt else 3) * K,  # generation, [3 sort kernels,] 2 simulations
+            # generation, [3 sort kernels,] [the DAG build,] 2 simulations
+            "gpu_launches": (3 + (3 if args.lpt else 0) + (1 if build_apart else 0)) * K,
+            "kernel_ms_per_step": {"dag_build": 1e3 * t_build / K if build_apart else None,
+                                   PLATS[0]: 1e3 * t_kern[0] / K, PLATS[1]: 1e3 * t_kern[1] / K},
             "clocks": clk,
             "e2e": e2e,
         }
@@ -738,6 +763,9 @@ def main():
     ap.add_argument("--impl", default="hesp", choices=["hesp", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--keep-in-first", action="store_true",
+                    help="build the DAGs inside the first platform's simulation launch instead of a launch of "
+                         "their own")
     ap.add_argument("--no-share-dag", dest="share_dag", action="store_false",
                     help="build each candidate's DAG in both platform launches instead of once")
     ap.add_argument("--no-lpt", dest="lpt", action="store_false",

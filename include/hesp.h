@@ -274,6 +274,14 @@ int hesp_schedule_metrics(const hesp_cand *cands_dev, const int8_t *levels_dev, 
  *   - Any number of reuse calls may follow one keep call. */
 int hesp_sim_workspace_size_kept(int32_t max_tiles, int32_t max_level, int64_t task_cap, int64_t n_cand,
                                  size_t *bytes_out);
+/* The DAG part of a keep call alone (no platform, no simulation): expand and
+ * analyse every candidate and keep its DAG in its arena, for
+ * hesp_simulate_batch_reuse calls.  status_dev[c] is the build's status
+ * (HESP_OK, HESP_ERR_ARG or HESP_ERR_CAPACITY), ntasks_dev (nullable) the
+ * task counts. */
+int hesp_dag_build_kept(const hesp_cand *cands_dev, const int8_t *levels_dev, int64_t n_cand, int32_t max_tiles,
+                        int32_t max_level, int64_t task_cap, int32_t *status_dev, int64_t *ntasks_dev,
+                        void *workspace_dev, size_t workspace_bytes, void *stream);
 int hesp_simulate_batch_keep(const hesp_platform *p, const hesp_cand *cands_dev, const int8_t *levels_dev,
                              int64_t n_cand, int32_t max_tiles, int32_t max_level, int64_t task_cap,
                              int64_t *makespan_dev, int32_t *status_dev, int64_t *ntasks_dev, void *workspace_dev,

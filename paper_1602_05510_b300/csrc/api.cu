@@ -455,6 +455,21 @@ int hesp_sim_workspace_size_kept(int32_t max_tiles, int32_t max_level, int64_t t
     return HESP_OK;
 }
 
+int hesp_dag_build_kept(const hesp_cand *cands, const int8_t *levels, int64_t n_cand, int32_t max_tiles,
+                        int32_t max_level, int64_t task_cap, int32_t *status, int64_t *ntasks, void *ws,
+                        size_t ws_bytes, void *stream) {
+    if (n_cand < 0 || task_cap < 0) return HESP_ERR_ARG;
+    if (n_cand == 0) return HESP_OK;
+    if (!cands || !levels || !status || !ws || ((uintptr_t)ws & 255) != 0) return HESP_ERR_ARG;
+    if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_level < 0 || max_level > HESP_MAX_LEVEL)
+        return HESP_ERR_UNSUPPORTED;
+    const Arena ar = make_arena(max_tiles, max_level, HESP_MAX_MEMS, task_cap);
+    if ((int64_t)ws_bytes < kWsHeaderBytes || ((int64_t)ws_bytes - kWsHeaderBytes) / ar.slot_bytes < n_cand)
+        return HESP_ERR_ARG;
+    return launch_build(ar, cands, levels, n_cand, max_tiles, max_level, ntasks, status,
+                        layout_signature(ar, max_tiles, max_level), (char *)ws, (cudaStream_t)stream);
+}
+
 int hesp_simulate_batch_keep(const hesp_platform *p, const hesp_cand *cands, const int8_t *levels, int64_t n_cand,
                              int32_t max_tiles, int32_t max_level, int64_t task_cap, int64_t *makespan,
                              int32_t *status, int64_t *ntasks, void *ws, size_t ws_bytes, void *stream) {

@@ -107,6 +107,9 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
                int64_t *sstart, int64_t *sfinish, int8_t *crit, int dag_mode, uint64_t layout_sig, char *ws,
                cudaStream_t stream);
 int sim_kernel_occupancy(int n_mem, int n_procs, int64_t Tcap, int *blocks_per_sm, int *threads_per_block);
+int launch_build(const Arena &ar, const hesp_cand *cands, const int8_t *levels, int64_t n_cand, int32_t max_tiles,
+                 int32_t max_level, int64_t *ntasks, int32_t *status, uint64_t layout_sig, char *ws,
+                 cudaStream_t stream);
 int launch_metrics(const hesp_cand *cands, const int8_t *levels, int64_t n_cand, const int64_t *sched_off,
                    const int64_t *start, const int64_t *finish, int64_t *busy, int64_t *ntasks, int64_t *sum_block,
                    int32_t *depth, cudaStream_t stream);

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 #include <limits.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -593,8 +594,11 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
     return eft;
 }
 
-template <int M, int NS, bool GEN>
-__global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, unsigned long long *work_counter) {
+// BUILD: expand and analyse each candidate's DAG and keep it (a keep launch
+// without the simulation; platform independent, so one instantiation).
+template <int M, int NS, bool GEN, bool BUILD = false>
+__global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl, KArgs a,
+                                                                 unsigned long long *work_counter) {
     __shared__ int64_t s_exec[4 * HESP_MAX_TYPES * HESP_LB];
     __shared__ int64_t s_wsum[4 * HESP_LB];
     __shared__ int8_t s_pmem[HESP_MAX_PROCS];
@@ -668,7 +672,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
         const int64_t A = (int64_t)n * (n + 1) / 2 << (2 * Lc);
         if (status == HESP_OK && (A > a.ar.Acap || A >= (1 << 19))) status = HESP_ERR_CAPACITY;
         // task times used by this candidate must be representable
-        if (status == HESP_OK) {
+        if (!BUILD && status == HESP_OK) {
             bool bad = false;
             for (int e = lane; e < 4 * HESP_MAX_TYPES * (Lc + 1); e += 32) {
                 const int op = e / (HESP_MAX_TYPES * (Lc + 1));
@@ -862,7 +866,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
         }
 
         // ---- 4. event-driven FCFS + EFT-P simulation
-        if (status == HESP_OK) {
+        if (!BUILD && status == HESP_OK) {
             uint16_t *const pending = at<uint16_t>(base, a.ar.off_pending);
             if (M > 1) {
                 int64_t *const vfrom = at<int64_t>(base, a.ar.off_vfrom);
@@ -1195,7 +1199,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
         // ---- 5. critical-path flags per base task: a task is critical when the
         // longest path through it, weighted by the scheduled task times, is as
         // long as the longest path of the DAG (the iterative solver's CP choice)
-        if (GEN && a.crit && status == HESP_OK) {
+        if (!BUILD && GEN && a.crit && status == HESP_OK) {
             const uint16_t *const prc = at<uint16_t>(base, a.ar.off_pending);
             const int32_t *const succoff = at<int32_t>(base, a.ar.off_succoff);
             const int32_t *const succ = at<int32_t>(base, a.ar.off_succ);
@@ -1252,7 +1256,7 @@ __global__ void __launch_bounds__(256, 4) sim_kernel(DevPlatform pl, KArgs a, un
 
         if (lane == 0) {
             a.status[c] = status;
-            a.makespan[c] = status == HESP_OK ? mk : -1;
+            if (a.makespan) a.makespan[c] = status == HESP_OK ? mk : -1;
             if (a.ntasks) a.ntasks[c] = T;
         }
         __syncwarp();
@@ -1330,6 +1334,41 @@ int launch_metrics(const hesp_cand *cands, const int8_t *levels, int64_t n_cand,
     const int64_t blocks = (n_cand * 32 + 255) / 256;
     metrics_kernel<<<(unsigned)blocks, 256, 0, stream>>>(cands, levels, n_cand, sched_off, start, finish, busy, ntasks,
                                                         sum_block, depth);
+    return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
+}
+
+// The build-only launch: expansion, dependences and successor lists of every
+// candidate, kept in its own arena (dag_mode 1), no simulation.
+int launch_build(const Arena &ar, const hesp_cand *cands, const int8_t *levels, int64_t n_cand, int32_t max_tiles,
+                 int32_t max_level, int64_t *ntasks, int32_t *status, uint64_t layout_sig, char *ws,
+                 cudaStream_t stream) {
+    KArgs a;
+    memset(&a, 0, sizeof a);
+    a.cands = cands;
+    a.levels = levels;
+    a.n_cand = n_cand;
+    a.max_tiles = max_tiles;
+    a.max_level = max_level;
+    a.status = status;
+    a.ntasks = ntasks;
+    a.dag_mode = 1;
+    a.layout_sig = layout_sig;
+    a.ar = ar;
+    a.ws = ws + kWsHeaderBytes;
+    a.bm_smem_words = 0;
+    DevPlatform dp;
+    memset(&dp, 0, sizeof dp);
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sim_kernel<1, 1, false, true>, 256, 0) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess)
+        return HESP_ERR_CUDA;
+    int64_t warps = (int64_t)per_sm * sms * 8;
+    if (warps > n_cand) warps = n_cand;
+    a.n_slots = warps;
+    unsigned long long *ctr = &((WsHeader *)ws)->work_counter;
+    if (cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), stream) != cudaSuccess) return HESP_ERR_CUDA;
+    sim_kernel<1, 1, false, true><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, stream>>>(dp, a, ctr);
     return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
 }
 

@@ -40,6 +40,7 @@ EXPORTS = (
     "hesp_simulate_critical", "hesp_solver_moves", "hesp_solver_pick", "hesp_schedule_metrics",
     "hesp_sim_workspace_size_kept", "hesp_simulate_batch_keep", "hesp_simulate_batch_reuse",
     "hesp_platform_set_cache", "hesp_surrogate_save", "hesp_surrogate_load", "hesp_platform_set_link",
+    "hesp_dag_build_kept",
 )
 CACHE_WB, CACHE_WT, CACHE_WA = 0, 1, 2
 SOLVER_ALL, SOLVER_CP, SOLVER_SHALLOW = 0, 1, 2
@@ -104,6 +105,7 @@ def lib():
         L.hesp_simulate_critical.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, sz, vp]
         L.hesp_sim_workspace_size_kept.argtypes = [i32, i32, i64, i64, ctypes.POINTER(sz)]
         L.hesp_simulate_batch_keep.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, sz, vp]
+        L.hesp_dag_build_kept.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp, vp, sz, vp]
         L.hesp_simulate_batch_reuse.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, sz, vp]
         L.hesp_solver_moves.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp]
         L.hesp_solver_pick.argtypes = [vp, vp, vp, vp, i32, u64, i64, vp, vp, vp, vp]
@@ -342,6 +344,18 @@ def _simulate_kept(fn, name, platform, cands, levels, n_cand, max_tiles, max_lev
     check(fn(platform.h, _ptr(cands), _ptr(levels), n_cand, max_tiles, max_level, task_cap, _ptr(makespan),
              _ptr(status), _ptr(ntasks), _ptr(workspace), workspace.numel(), _stream(stream)), name)
     return makespan, status, ntasks
+
+
+def dag_build_kept(cands, levels, n_cand, max_tiles, max_level, workspace, status=None, ntasks=None, stream=None,
+                   task_cap=0):
+    """hesp_dag_build_kept: build and keep every candidate's DAG (no simulation)."""
+    import torch
+    if status is None:
+        status = torch.empty(n_cand, dtype=torch.int32, device=levels.device)
+    check(lib().hesp_dag_build_kept(_ptr(cands), _ptr(levels), n_cand, max_tiles, max_level, task_cap, _ptr(status),
+                                    _ptr(ntasks), _ptr(workspace), workspace.numel(), _stream(stream)),
+          "hesp_dag_build_kept")
+    return status, ntasks
 
 
 def simulate_batch_keep(platform: Platform, cands, levels, n_cand, max_tiles, max_level, workspace, makespan=None,

@@ -71,3 +71,18 @@ def test_dag_counts(L):
         for lvl in range(4):
             s = n << lvl
             assert d.count_tasks(np.full(d.n_base, lvl, np.int8))[0] == s * (s + 1) * (s + 2) // 6
+
+
+def test_no_unresolved_internal_symbols():
+    """Every internal (namespace hesp) symbol the library uses is defined in
+    it: a shared-library link does not catch a function left in an anonymous
+    namespace of another file, only loading does."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    from paper_1602_05510_b300 import build
+    lib = build.build()
+    out = subprocess.run([nm, "-D", "--undefined-only", lib], capture_output=True, text=True, check=True).stdout
+    assert not [l for l in out.splitlines() if "_ZN4hesp" in l]

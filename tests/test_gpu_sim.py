@@ -439,3 +439,25 @@ def test_cfg3_full_label_launch_sampled():
     for c in idx:
         lvc = W.uniform_levels(3, int(c), 1, nb, 3)[0]
         assert O.simulate(pl, n, b, lvc, schedule=False)["makespan"] == ms[c], c
+
+
+def test_build_apart_then_reuse():
+    """hesp_dag_build_kept (no platform) followed by reuse launches on two
+    platforms equals separate hesp_simulate_batch calls; a failed build keeps
+    its status."""
+    C, nb = 256, 120
+    lvh = W.workload_levels("cfg1", 9000, C)
+    lvh[5, 3] = 4  # above max_level: the build fails (HESP_ERR_ARG)
+    lv = torch.from_numpy(lvh.reshape(-1).copy()).cuda()
+    cands = hesp.cands_tensor(8, 2048, np.arange(C, dtype=np.int64) * nb)
+    ws = hesp.alloc_workspace_kept(8, 2, C)
+    nt0 = torch.empty(C, dtype=torch.int64, device="cuda")
+    bst, _ = hesp.dag_build_kept(cands, lv, C, 8, 2, ws, ntasks=nt0)
+    for key in ("cfg1a", "cfg1b", "cfg2"):
+        plat = hesp.Platform(W.PLATFORMS[key])
+        ms, st, _ = hesp.simulate_batch_reuse(plat, cands, lv, C, 8, 2, ws)
+        ms2, st2, _ = hesp.simulate_batch(plat, cands, lv, C, 8, 2, hesp.alloc_workspace(plat, 8, 2, C))
+        torch.cuda.synchronize()
+        assert torch.equal(st, st2) and torch.equal(ms, ms2), key
+    bst = bst.cpu().numpy()
+    assert bst[5] == -1 and (np.delete(bst, 5) == 0).all()
