@@ -210,19 +210,16 @@ __device__ __forceinline__ uint64_t warp_max_u64(uint64_t k) {
     return ((uint64_t)hmax << 32) | lmax;
 }
 
-// Per-processor FIFO of tasks in flight, threaded through the tasks.  For a
-// task in flight: its successor in the FIFO and that successor's finish time,
-// and the range of its own successor list, all read together when it
-// completes.  Record q also holds slot q of the FCFS wait queue of F-P / R-P
-// (every task joins that queue once).
+// Per-processor FIFO of tasks in flight, threaded through the tasks: for a
+// task in flight, its successor in the FIFO and that successor's finish time,
+// read together (16 bytes) when it completes.  Record q also holds slot q of
+// the FCFS wait queue of F-P / R-P (every task joins that queue once).
 struct __align__(16) Link {
     int32_t next;
-    int32_t e0, e1;  // successor list succ[e0 .. e1)
-    int32_t pad;
-    int64_t nfin;
     int32_t rq;  // wait-queue slot
-    int32_t pad2;
+    int64_t nfin;
 };
+static_assert(sizeof(Link) == 16, "one 16-byte load per completion");
 
 struct KArgs {
     const hesp_cand *cands;
@@ -327,21 +324,18 @@ struct Counts {
     }
 };
 
-// Schedule task j at time t: data-ready time per memory, the processor
+// Schedule task j (descriptor d) at time t: data-ready time per memory, the processor
 // choice `sel` (ties to the lowest id), commit of the coherence state (the
 // caching policy `cache`), append to the chosen processor's FIFO.  Under
 // F-P / R-P the caller guarantees a processor idle at t.  Clears `ok` on an
 // internal inconsistency.
 template <int M, int NS, bool FIFO, bool REC>
-__device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, const KArgs &a, int Lc, int lb_b,
+__device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, char *base, const KArgs &a, int Lc, int lb_b,
                                                  int lane, const int64_t *s_exec, const int8_t *s_pmem,
                                                  const int8_t *s_ptype, const int pm[NS], const int pt[NS],
                                                  const bool pv[NS], int64_t avail[NS], int head[NS], int tail[NS],
                                                  int64_t hfin[NS], int64_t &mk, bool &ok, int64_t sched_base,
                                                  int sel, uint64_t rp_seed, int cache, bool links) {
-    const uint64_t d = at<uint64_t>(base, a.ar.off_desc)[j];
-    const int32_t *const succoff = at<int32_t>(base, a.ar.off_succoff);
-    const int se0 = succoff[j], se1 = succoff[j + 1];  // kept with the task while it is in flight
     const int op = (int)(d & 3);
     const int lvl = (int)((d >> 2) & 7);
     const int nr = nreg_of(op);
@@ -571,12 +565,13 @@ __device__ __forceinline__ int64_t schedule_task(int j, int64_t t, char *base, c
                     link[tail[q]].next = j;
                     link[tail[q]].nfin = eft;
                 }
-                int4 lj;
-                lj.x = -1;
-                lj.y = se0;
-                lj.z = se1;
-                lj.w = 0;
-                *reinterpret_cast<int4 *>(&link[j]) = lj;
+                if (sel >= HESP_SELECT_FP) {
+                    link[j].next = -1;  // record j's wait-queue slot stays
+                } else {
+                    // the whole record, so that reading it never needs DRAM
+                    // for bytes that were never written
+                    *reinterpret_cast<int4 *>(&link[j]) = make_int4(-1, 0, 0, 0);
+                }
                 tail[q] = j;
             }
         }
@@ -853,13 +848,6 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     T = hd->T;
                     E = hd->E;
                     for (int64_t j = lane; j < T; j += 32) pending[j] = pend0[j];
-                    // warm L2 with the DAG the event loop reads
-                    const char *d0 = (const char *)desc;
-                    for (int64_t q = (int64_t)lane * 128; q < 8 * T; q += 32 * 128)
-                        asm volatile("prefetch.global.L2 [%0];" ::"l"(d0 + q));
-                    const char *s0 = (const char *)at<int32_t>(base, a.ar.off_succ);
-                    for (int64_t q = (int64_t)lane * 128; q < 4 * E; q += 32 * 128)
-                        asm volatile("prefetch.global.L2 [%0];" ::"l"(s0 + q));
                 }
             }
             __syncwarp();
@@ -1009,7 +997,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                             }
                         if (!__any_sync(FULL, any)) tj = (int64_t)warp_min_u64(mn);
                     }
-                    const int64_t fj = schedule_task<M, NS, false, GEN>(j, tj, base, a, Lc, lb_b, lane, s_exec, s_pmem,
+                    const int64_t fj = schedule_task<M, NS, false, GEN>(j, desc[j], tj, base, a, Lc, lb_b, lane, s_exec, s_pmem,
                                                                    s_ptype, pm, pt, pv, avail, head, tail, hfin, mk,
                                                                    ok, sched_base, sel, rp_seed, cache, links);
                     const int e0 = succoff[j], e1 = succoff[j + 1];
@@ -1048,6 +1036,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                 tail[s] = -1;
             }
             const int64_t sched_base = a.sched_off ? a.sched_off[c] : -1;
+            const int32_t *const succoff = at<int32_t>(base, a.ar.off_succoff);
             const int32_t *const succ = at<int32_t>(base, a.ar.off_succ);
             Link *const link = at<Link>(base, a.ar.off_link);
             int qh = 0, qt = 0;  // F-P / R-P wait queue: link[qh .. qt).rq
@@ -1060,6 +1049,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
             // one time, or a long successor list) or, when a single task
             // completed and released at most 32 successors, in the lanes (dj).
             int dj = INT_MAX;
+            uint64_t djd = 0;  // descriptor of task dj, loaded when it is released
             bool direct = false;
             for (;;) {
                 // schedule every released task in ascending id
@@ -1067,13 +1057,15 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     for (;;) {
                         const int j = __reduce_min_sync(FULL, dj);
                         if (j == INT_MAX) break;
+                        const unsigned own = __ballot_sync(FULL, dj == j);
+                        const uint64_t dsc = __shfl_sync(FULL, djd, __ffs(own) - 1);
                         if (dj == j) dj = INT_MAX;
                         if (waits) {
                             if (lane == 0) link[qt].rq = j;
                             ++qt;
                             continue;
                         }
-                        schedule_task<M, NS, true, GEN>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
+                        schedule_task<M, NS, true, GEN>(j, dsc, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
                                                    avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache, links);
                         ++scheduled;
                     }
@@ -1100,7 +1092,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                                     ++qt;
                                     continue;
                                 }
-                                schedule_task<M, NS, true, GEN>(jb + bit, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype,
+                                schedule_task<M, NS, true, GEN>(jb + bit, desc[jb + bit], t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype,
                                                            pm, pt, pv, avail, head, tail, hfin, mk, ok, sched_base,
                                                            sel, rp_seed, cache, links);
                                 ++scheduled;
@@ -1120,7 +1112,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                         if (!__any_sync(FULL, any)) break;
                         const int j = link[qh].rq;
                         ++qh;
-                        schedule_task<M, NS, true, GEN>(j, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
+                        schedule_task<M, NS, true, GEN>(j, desc[j], t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
                                                    avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache, links);
                         ++scheduled;
                     }
@@ -1150,13 +1142,13 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                         const int src = __ffs(cm) - 1;
                         cm &= cm - 1;
                         const int i = __shfl_sync(FULL, head[s], src);
-                        int4 l0 = make_int4(0, 0, 0, 0);
-                        int64_t lnfin = 0;
-                        if (lane == src) {
-                            l0 = *reinterpret_cast<const int4 *>(&link[i]);
-                            lnfin = link[i].nfin;
-                        }
-                        const int e0 = __shfl_sync(FULL, l0.y, src), e1 = __shfl_sync(FULL, l0.z, src);
+                        // lane src: the FIFO record; lanes 0, 1: the successor range
+                        Link l0;
+                        l0.next = 0;
+                        l0.nfin = 0;
+                        if (lane == src) l0 = link[i];
+                        const int eq = lane < 2 ? succoff[i + lane] : 0;
+                        const int e0 = __shfl_sync(FULL, eq, 0), e1 = __shfl_sync(FULL, eq, 1);
                         if (ncomp == 1 && e1 - e0 <= 32) {
                             // the only completion: its released successors wait in the lanes
                             const int e = e0 + lane;
@@ -1164,7 +1156,10 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                                 const int sj = succ[e];
                                 const int pvv = (int)pending[sj] - 1;
                                 pending[sj] = (uint16_t)pvv;
-                                if (pvv == 0) dj = sj;
+                                if (pvv == 0) {
+                                    dj = sj;
+                                    djd = desc[sj];
+                                }
                             }
                             direct = true;
                         } else {
@@ -1183,9 +1178,9 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                             whi = max(whi, __reduce_max_sync(FULL, hi));
                         }
                         if (lane == src) {
-                            head[s] = l0.x;
-                            hfin[s] = l0.x >= 0 ? lnfin : kInf;
-                            if (l0.x < 0) tail[s] = -1;
+                            head[s] = l0.next;
+                            hfin[s] = l0.next >= 0 ? l0.nfin : kInf;
+                            if (l0.next < 0) tail[s] = -1;
                         }
                         __syncwarp();
                     }
