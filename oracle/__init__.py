@@ -116,6 +116,13 @@ def lib():
         L.or_simulate_levels.restype = i32
         L.or_simulate_levels.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i32, i32,
                                          vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
+        L.or_deps_side.restype = i64
+        L.or_deps_side.argtypes = [i32, i64, vp, i64, i64, i32, i64, i64, vp, vp, vp]
+        L.or_factors_to_code.restype = i64
+        L.or_factors_to_code.argtypes = [i32, vp, vp, i64]
+        L.or_simulate_factors.restype = i32
+        L.or_simulate_factors.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i32,
+                                          vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
         L.or_simulate_many.restype = i32
         L.or_simulate_many.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i64, vp, vp, vp]
         _lib = L
@@ -239,6 +246,66 @@ def deps(n: int, b: int, code, mode: int, atom_level: int = 0):
         if E < 0:
             raise ValueError("deps failed (%d)" % E)
         return po[:T + 1].copy(), pv[:E].copy(), int(war.value)
+
+
+def factors_to_code(n: int, factors) -> np.ndarray:
+    """Split code of one-level k-way partitions (Sec. 2.1, partition
+    parameter p = 1 / factors[t] for base task t)."""
+    fv = np.ascontiguousarray(factors, np.int8)
+    cap = int(sum(1 + int(f) ** 3 for f in fv)) + 1
+    code = np.zeros(cap, np.int8)
+    k = lib().or_factors_to_code(n, fv.ctypes.data, code.ctypes.data, cap)
+    if k < 0:
+        raise ValueError("bad factors (%d)" % k)
+    return code[:k].copy()
+
+
+def lcm_of(factors) -> int:
+    L = 1
+    for f in np.asarray(factors, np.int64).reshape(-1):
+        L = L * int(f) // int(np.gcd(L, int(f)))
+    return L
+
+
+def deps_side(n: int, b: int, code, atom_side: int):
+    """Atom last-writer predecessor lists with atoms of side atom_side:
+    (pred_off[T+1], preds[E], war_edges)."""
+    code = np.ascontiguousarray(code, np.int8)
+    cap_t = _cap_for_code(code)
+    T = len(expand(n, b, code)["op"])
+    cap_e = 1 << 16
+    while True:
+        po = np.zeros(cap_t + 1, np.int64)
+        pv = np.zeros(cap_e, np.int32)
+        war = ctypes.c_int32(0)
+        E = lib().or_deps_side(n, b, code.ctypes.data, len(code), cap_t, 1, atom_side, cap_e,
+                               po.ctypes.data, pv.ctypes.data, ctypes.addressof(war))
+        if E == -2 and cap_e < (1 << 30):
+            cap_e *= 8
+            continue
+        if E < 0:
+            raise ValueError("deps failed (%d)" % E)
+        return po[:T + 1].copy(), pv[:E].copy(), int(war.value)
+
+
+def simulate_factors(pl: Platform, n: int, b: int, factors, dep_mode: int = 1, schedule: bool = True):
+    """One candidate of one-level k-way partitions: factors[t] per base task
+    (Fig. 1 order); atoms of side b / lcm(factors)."""
+    fv = np.ascontiguousarray(factors, np.int8)
+    cap = int(sum(int(f) ** 3 for f in fv)) + 1
+    proc = np.zeros(cap, np.int16) if schedule else None
+    start = np.zeros(cap, np.int64) if schedule else None
+    fin = np.zeros(cap, np.int64) if schedule else None
+    order = np.zeros(cap, np.int32) if schedule else None
+    issue = np.zeros(cap, np.int64) if schedule else None
+    st = Stats()
+    rc = lib().or_simulate_factors(ctypes.byref(pl), n, b, fv.ctypes.data, dep_mode,
+                                   proc.ctypes.data if schedule else None,
+                                   start.ctypes.data if schedule else None,
+                                   fin.ctypes.data if schedule else None,
+                                   order.ctypes.data if schedule else None,
+                                   issue.ctypes.data if schedule else None, ctypes.byref(st))
+    return _result(rc, st, proc, start, fin, order, issue)
 
 
 def simulate_code(pl: Platform, n: int, b: int, code, atom_level: int, dep_mode: int = 1,

@@ -158,9 +158,10 @@ static int dag_push(or_dag *d, const or_task *t) {
     return OR_OK;
 }
 
-static or_region quad(or_region r, int p, int q) {
+/* Block (p, q) of region r cut into k x k square blocks. */
+static or_region part(or_region r, int64_t k, int64_t p, int64_t q) {
     or_region o;
-    int64_t h = r.sz / 2;
+    int64_t h = r.sz / k;
     o.r0 = r.r0 + p * h;
     o.c0 = r.c0 + q * h;
     o.sz = h;
@@ -170,18 +171,28 @@ static or_region quad(or_region r, int p, int q) {
 static int emit(or_dag *d, const int8_t *code, int64_t code_len, int64_t *pos,
                 int32_t op, int32_t depth, int32_t base, or_region a, or_region b, or_region c);
 
-/* Emit a task, or, when the split tree says so, the tasks of its 2x2 blocked
+/* Emit a task, or, when the split tree says so, the tasks of its blocked
  * algorithm in their program order (each of them again subject to the tree).
+ * Sec. 2.1: a partitioner is the task's blocked algorithm with a partition
+ * parameter p; the new tasks work on blocks of p times the task's block
+ * size.  A split code value s >= 1 takes p = 1 / (s + 1): the task's blocks
+ * are cut into k x k blocks, k = s + 1 (k = 2 is the 2x2 partition of
+ * Fig. 3; k = 3 gives the non-dyadic tilings of Fig. 4).
  * Region arguments: chol(A=a); trsm(T=a, B=b); syrk(A=a, C=b); gemm(A=a, B=b, C=c).
  *
- *   chol(A):   chol(A00); trsm(A00 -> A01); syrk(A01 -> A11); chol(A11)
- *   trsm(T,B): B := T^-T B, T upper triangular
- *              trsm(T00->B00); trsm(T00->B01);
- *              gemm(T01,B00->B10); gemm(T01,B01->B11);
- *              trsm(T11->B10); trsm(T11->B11)
- *   syrk(A,C): C -= A^T A on the upper part of C; for k = 0, 1:
- *              gemm(Ak0,Ak1->C01); syrk(Ak0->C00); syrk(Ak1->C11)
- *   gemm(A,B,C): C -= A^T B; for k, for i, for j: gemm(Aki,Bkj->Cij)
+ *   chol(A):   the loop of Fig. 1 on the k x k blocks of A:
+ *              for p: chol(App); for q > p: trsm(App -> Apq);
+ *                     for i > p: { for q > i: gemm(Api, Apq -> Aiq); syrk(Api -> Aii) }
+ *   trsm(T,B): B := T^-T B, T upper triangular, one block row at a time:
+ *              for p: { for c: trsm(Tpp -> Bpc);
+ *                       for i > p: for c: gemm(Tpi, Bpc -> Bic) }
+ *   syrk(A,C): C -= A^T A on the upper part of C, in the inner order of Fig. 1:
+ *              for p: for i: { for j > i: gemm(Api, Apj -> Cij); syrk(Api -> Cii) }
+ *   gemm(A,B,C): C -= A^T B: for p, for i, for j: gemm(Api, Bpj -> Cij)
+ * For k = 2 these are, in order: chol(A00) trsm(A00->A01) syrk(A01->A11)
+ * chol(A11); trsm(T00->B00) trsm(T00->B01) gemm(T01,B00->B10)
+ * gemm(T01,B01->B11) trsm(T11->B10) trsm(T11->B11); per p: gemm(Ap0,Ap1->C01)
+ * syrk(Ap0->C00) syrk(Ap1->C11); and the eight gemms in p, i, j order.
  */
 static int emit(or_dag *d, const int8_t *code, int64_t code_len, int64_t *pos,
                 int32_t op, int32_t depth, int32_t base, or_region a, or_region b, or_region c) {
@@ -210,36 +221,56 @@ static int emit(or_dag *d, const int8_t *code, int64_t code_len, int64_t *pos,
         }
         return dag_push(d, &t);
     }
-    if (a.sz % 2 != 0) return OR_ERR_ARG;
+    int64_t k = (int64_t)split + 1;
+    if (split < 0 || a.sz % k != 0) return OR_ERR_ARG;
     or_region z = {0, 0, 0};
     int nd = depth + 1;
     switch (op) {
     case OP_CHOL:
-        if ((rc = emit(d, code, code_len, pos, OP_CHOL, nd, base, quad(a, 0, 0), z, z))) return rc;
-        if ((rc = emit(d, code, code_len, pos, OP_TRSM, nd, base, quad(a, 0, 0), quad(a, 0, 1), z))) return rc;
-        if ((rc = emit(d, code, code_len, pos, OP_SYRK, nd, base, quad(a, 0, 1), quad(a, 1, 1), z))) return rc;
-        if ((rc = emit(d, code, code_len, pos, OP_CHOL, nd, base, quad(a, 1, 1), z, z))) return rc;
-        break;
-    case OP_TRSM:
-        if ((rc = emit(d, code, code_len, pos, OP_TRSM, nd, base, quad(a, 0, 0), quad(b, 0, 0), z))) return rc;
-        if ((rc = emit(d, code, code_len, pos, OP_TRSM, nd, base, quad(a, 0, 0), quad(b, 0, 1), z))) return rc;
-        if ((rc = emit(d, code, code_len, pos, OP_GEMM, nd, base, quad(a, 0, 1), quad(b, 0, 0), quad(b, 1, 0)))) return rc;
-        if ((rc = emit(d, code, code_len, pos, OP_GEMM, nd, base, quad(a, 0, 1), quad(b, 0, 1), quad(b, 1, 1)))) return rc;
-        if ((rc = emit(d, code, code_len, pos, OP_TRSM, nd, base, quad(a, 1, 1), quad(b, 1, 0), z))) return rc;
-        if ((rc = emit(d, code, code_len, pos, OP_TRSM, nd, base, quad(a, 1, 1), quad(b, 1, 1), z))) return rc;
-        break;
-    case OP_SYRK:
-        for (int k = 0; k < 2; k++) {
-            if ((rc = emit(d, code, code_len, pos, OP_GEMM, nd, base, quad(a, k, 0), quad(a, k, 1), quad(b, 0, 1)))) return rc;
-            if ((rc = emit(d, code, code_len, pos, OP_SYRK, nd, base, quad(a, k, 0), quad(b, 0, 0), z))) return rc;
-            if ((rc = emit(d, code, code_len, pos, OP_SYRK, nd, base, quad(a, k, 1), quad(b, 1, 1), z))) return rc;
+        for (int64_t p = 0; p < k; p++) {
+            if ((rc = emit(d, code, code_len, pos, OP_CHOL, nd, base, part(a, k, p, p), z, z))) return rc;
+            for (int64_t q = p + 1; q < k; q++)
+                if ((rc = emit(d, code, code_len, pos, OP_TRSM, nd, base, part(a, k, p, p), part(a, k, p, q), z)))
+                    return rc;
+            for (int64_t i = p + 1; i < k; i++) {
+                for (int64_t q = i + 1; q < k; q++)
+                    if ((rc = emit(d, code, code_len, pos, OP_GEMM, nd, base, part(a, k, p, i), part(a, k, p, q),
+                                   part(a, k, i, q))))
+                        return rc;
+                if ((rc = emit(d, code, code_len, pos, OP_SYRK, nd, base, part(a, k, p, i), part(a, k, i, i), z)))
+                    return rc;
+            }
         }
         break;
+    case OP_TRSM:
+        for (int64_t p = 0; p < k; p++) {
+            for (int64_t cc = 0; cc < k; cc++)
+                if ((rc = emit(d, code, code_len, pos, OP_TRSM, nd, base, part(a, k, p, p), part(b, k, p, cc), z)))
+                    return rc;
+            for (int64_t i = p + 1; i < k; i++)
+                for (int64_t cc = 0; cc < k; cc++)
+                    if ((rc = emit(d, code, code_len, pos, OP_GEMM, nd, base, part(a, k, p, i), part(b, k, p, cc),
+                                   part(b, k, i, cc))))
+                        return rc;
+        }
+        break;
+    case OP_SYRK:
+        for (int64_t p = 0; p < k; p++)
+            for (int64_t i = 0; i < k; i++) {
+                for (int64_t j = i + 1; j < k; j++)
+                    if ((rc = emit(d, code, code_len, pos, OP_GEMM, nd, base, part(a, k, p, i), part(a, k, p, j),
+                                   part(b, k, i, j))))
+                        return rc;
+                if ((rc = emit(d, code, code_len, pos, OP_SYRK, nd, base, part(a, k, p, i), part(b, k, i, i), z)))
+                    return rc;
+            }
+        break;
     case OP_GEMM:
-        for (int k = 0; k < 2; k++)
-            for (int i = 0; i < 2; i++)
-                for (int j = 0; j < 2; j++)
-                    if ((rc = emit(d, code, code_len, pos, OP_GEMM, nd, base, quad(a, k, i), quad(b, k, j), quad(c, i, j))))
+        for (int64_t p = 0; p < k; p++)
+            for (int64_t i = 0; i < k; i++)
+                for (int64_t j = 0; j < k; j++)
+                    if ((rc = emit(d, code, code_len, pos, OP_GEMM, nd, base, part(a, k, p, i), part(b, k, p, j),
+                                   part(c, k, i, j))))
                         return rc;
         break;
     default:
@@ -402,8 +433,9 @@ static int depends(const or_task *i, const or_task *j) {
 /* Dependences via atoms                                               */
 /* ------------------------------------------------------------------ */
 
-/* The matrix is cut into square atoms of side a = b / 2^atom_level; every
- * region of the DAG is a union of atoms when atom_level >= the deepest split.
+/* The matrix is cut into square atoms of side a (b / 2^atom_level for the
+ * dyadic partitions, b / lcm of the factors for the one-level k-way ones);
+ * every region of the DAG must be a union of atoms.
  * For task j, in creation order, and every atom x of its regions:
  *   RaW / WaW: j depends on the last writer of x;
  *   WaR: if j writes x, j depends on every reader of x since its last write.
@@ -560,11 +592,12 @@ static int make_dag(int32_t n, int64_t b, const int8_t *code, int64_t code_len, 
     return rc;
 }
 
-static int check_atoms(const or_dag *d, int64_t b, int32_t atom_level, atom_grid *g, int32_t n) {
-    if (atom_level < 0 || atom_level > 20) return OR_ERR_ARG;
-    if (b % ((int64_t)1 << atom_level) != 0) return OR_ERR_ARG;
-    g->a = b >> atom_level;
-    g->grid = (int64_t)n << atom_level;
+/* Atoms of side `side` elements: every region of the DAG must be a union of
+ * them (side divides b and every region's offsets and size). */
+static int check_atoms(const or_dag *d, int64_t b, int64_t side, atom_grid *g, int32_t n) {
+    if (side < 1 || b % side != 0) return OR_ERR_ARG;
+    g->a = side;
+    g->grid = (int64_t)n * (b / side);
     for (int32_t j = 0; j < d->n; j++)
         for (int r = 0; r < d->t[j].nreg; r++) {
             or_region x = d->t[j].reg[r];
@@ -574,10 +607,10 @@ static int check_atoms(const or_dag *d, int64_t b, int32_t atom_level, atom_grid
 }
 
 /* Dependence lists for a split code. mode 0: all pairs (definition);
- * mode 1: atoms of side b / 2^atom_level.  Output: pred_off[T+1], preds[cap_e].
+ * mode 1: atoms of side atom_side.  Output: pred_off[T+1], preds[cap_e].
  * Returns the edge count, or a negative error. war_out: WaR edges found. */
-int64_t or_deps(int32_t n, int64_t b, const int8_t *code, int64_t code_len, int64_t cap_t, int32_t mode,
-                int32_t atom_level, int64_t cap_e, int64_t *pred_off, int32_t *preds, int32_t *war_out) {
+int64_t or_deps_side(int32_t n, int64_t b, const int8_t *code, int64_t code_len, int64_t cap_t, int32_t mode,
+                     int64_t atom_side, int64_t cap_e, int64_t *pred_off, int32_t *preds, int32_t *war_out) {
     or_dag d;
     int rc = make_dag(n, b, code, code_len, cap_t, &d);
     if (rc) return rc;
@@ -588,7 +621,7 @@ int64_t or_deps(int32_t n, int64_t b, const int8_t *code, int64_t code_len, int6
         rc = allpairs_deps(&d, &po, &pv);
     } else {
         atom_grid g;
-        rc = check_atoms(&d, b, atom_level, &g, n);
+        rc = check_atoms(&d, b, atom_side, &g, n);
         if (!rc) rc = atom_deps(&d, &g, &po, &pv, &war);
     }
     if (rc) { free(d.t); return rc; }
@@ -601,6 +634,14 @@ int64_t or_deps(int32_t n, int64_t b, const int8_t *code, int64_t code_len, int6
     free(po);
     free(pv);
     return ne;
+}
+
+/* or_deps with atoms of side b / 2^atom_level. */
+int64_t or_deps(int32_t n, int64_t b, const int8_t *code, int64_t code_len, int64_t cap_t, int32_t mode,
+                int32_t atom_level, int64_t cap_e, int64_t *pred_off, int32_t *preds, int32_t *war_out) {
+    if (mode != 0 && (atom_level < 0 || atom_level > 20 || b % ((int64_t)1 << atom_level) != 0)) return OR_ERR_ARG;
+    return or_deps_side(n, b, code, code_len, cap_t, mode, mode == 0 ? 1 : b >> atom_level, cap_e, pred_off, preds,
+                        war_out);
 }
 
 /* ------------------------------------------------------------------ */
@@ -809,7 +850,7 @@ static int by_crit_desc(const void *a, const void *b) {
 
 /* Simulate one candidate.
  *   code/code_len: split tree (preorder), see or_levels_to_code
- *   atom_level:    atom side = b / 2^atom_level (>= deepest split)
+ *   atom_side:     atom side in elements (divides every region)
  *   dep_mode:      0 = all-pairs dependences, 1 = atom last-writer
  * Optional outputs (NULL to skip), per task in creation order:
  *   proc_out, start_out, finish_out, issue_out (the time at which the task
@@ -851,10 +892,10 @@ static int by_crit_desc(const void *a, const void *b) {
  *     when mem(p*) is not the host, only in host memory from finish +
  *     xfer(block) (else as WB).
  *   - the makespan is the largest finish time. */
-int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *code, int64_t code_len,
-                    int64_t cap_t, int32_t atom_level, int32_t dep_mode, int16_t *proc_out,
-                    int64_t *start_out, int64_t *finish_out, int32_t *order_out, int64_t *issue_out,
-                    or_stats *st) {
+int32_t or_simulate_side(const or_platform *pl, int32_t n, int64_t b, const int8_t *code, int64_t code_len,
+                         int64_t cap_t, int64_t atom_side, int32_t dep_mode, int16_t *proc_out,
+                         int64_t *start_out, int64_t *finish_out, int32_t *order_out, int64_t *issue_out,
+                         or_stats *st) {
     if (!pl || pl->n_mem < 1 || pl->n_mem > OR_MAX_MEMS || pl->n_procs < 1 || pl->n_procs > OR_MAX_PROCS)
         return OR_ERR_ARG;
     if (pl->n_mem > 1 && pl->bw_bytes_per_ns < 1) return OR_ERR_ARG;
@@ -870,7 +911,7 @@ int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *c
     int rc = make_dag(n, b, code, code_len, cap_t, &d);
     if (rc) return rc;
     atom_grid g;
-    rc = check_atoms(&d, b, atom_level, &g, n);
+    rc = check_atoms(&d, b, atom_side, &g, n);
     if (rc) { free(d.t); return rc; }
     int64_t *pred_off = NULL;
     int32_t *preds = NULL;
@@ -1073,6 +1114,17 @@ out:
     return rc;
 }
 
+/* or_simulate_side with atoms of side b / 2^atom_level (atom_level >= the
+ * deepest split of a dyadic partition). */
+int32_t or_simulate(const or_platform *pl, int32_t n, int64_t b, const int8_t *code, int64_t code_len,
+                    int64_t cap_t, int32_t atom_level, int32_t dep_mode, int16_t *proc_out,
+                    int64_t *start_out, int64_t *finish_out, int32_t *order_out, int64_t *issue_out,
+                    or_stats *st) {
+    if (atom_level < 0 || atom_level > 20 || b % ((int64_t)1 << atom_level) != 0) return OR_ERR_ARG;
+    return or_simulate_side(pl, n, b, code, code_len, cap_t, b >> atom_level, dep_mode, proc_out, start_out,
+                            finish_out, order_out, issue_out, st);
+}
+
 /* Convenience: one candidate given one split level per base task; the atom
  * level is the largest split level unless atom_level >= 0 is given. */
 int32_t or_simulate_levels(const or_platform *pl, int32_t n, int64_t b, const int8_t *levels, int32_t atom_level,
@@ -1103,6 +1155,93 @@ int32_t or_simulate_levels(const or_platform *pl, int32_t n, int64_t b, const in
     if (len < 0) { free(code); return (int32_t)len; }
     int32_t rc = or_simulate(pl, n, b, code, len, ntask, atom_level, dep_mode, proc_out, start_out, finish_out,
                              order_out, issue_out, st);
+    free(code);
+    return rc;
+}
+
+/* Number of tasks a k-way partition of a task of type op creates, by
+ * enumerating the loops of emit(). */
+static int64_t part_count(int32_t op, int64_t k) {
+    int64_t c = 0;
+    if (op == OP_CHOL) {
+        for (int64_t p = 0; p < k; p++) {
+            c += 1;
+            for (int64_t q = p + 1; q < k; q++) c += 1;
+            for (int64_t i = p + 1; i < k; i++) {
+                for (int64_t q = i + 1; q < k; q++) c += 1;
+                c += 1;
+            }
+        }
+    } else if (op == OP_TRSM) {
+        for (int64_t p = 0; p < k; p++) {
+            c += k;
+            for (int64_t i = p + 1; i < k; i++) c += k;
+        }
+    } else if (op == OP_SYRK) {
+        for (int64_t p = 0; p < k; p++)
+            for (int64_t i = 0; i < k; i++) c += (k - 1 - i) + 1;
+    } else {
+        c = k * k * k;
+    }
+    return c;
+}
+
+/* Split code of a one-level partition per base task: base task t is cut
+ * with partition parameter p = 1 / factors[t] (factor 1 keeps it); its new
+ * tasks are not partitioned again.  Returns the code length or an error. */
+int64_t or_factors_to_code(int32_t n, const int8_t *factors, int8_t *code, int64_t cap) {
+    int64_t nb = or_base_count(n);
+    int32_t *ops = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+    if (!ops) return OR_ERR_CAPACITY;
+    or_base_ops(n, ops);
+    int64_t pos = 0;
+    for (int64_t t = 0; t < nb; t++) {
+        int32_t f = factors[t];
+        if (f < 1 || f > 64) { free(ops); return OR_ERR_ARG; }
+        if (pos >= cap) { free(ops); return OR_ERR_CAPACITY; }
+        code[pos++] = (int8_t)(f - 1);
+        if (f > 1) {
+            int64_t kids = part_count(ops[t], f);
+            if (pos + kids > cap) { free(ops); return OR_ERR_CAPACITY; }
+            for (int64_t q = 0; q < kids; q++) code[pos++] = 0;
+        }
+    }
+    free(ops);
+    return pos;
+}
+
+static int64_t gcd64(int64_t x, int64_t y) {
+    while (y) { int64_t r = x % y; x = y; y = r; }
+    return x;
+}
+
+/* One candidate of one-level k-way partitions (factors[t] per base task).
+ * The atoms are the common refinement of every tiling: side b / L, L the
+ * least common multiple of the factors (b must be a multiple of L). */
+int32_t or_simulate_factors(const or_platform *pl, int32_t n, int64_t b, const int8_t *factors, int32_t dep_mode,
+                            int16_t *proc_out, int64_t *start_out, int64_t *finish_out, int32_t *order_out,
+                            int64_t *issue_out, or_stats *st) {
+    if (n < 1 || b < 1) return OR_ERR_ARG;
+    int64_t nb = or_base_count(n);
+    int32_t *ops = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+    if (!ops) return OR_ERR_CAPACITY;
+    or_base_ops(n, ops);
+    int64_t L = 1, ntask = 0;
+    for (int64_t t = 0; t < nb; t++) {
+        if (factors[t] < 1 || factors[t] > 64) { free(ops); return OR_ERR_ARG; }
+        L = L / gcd64(L, factors[t]) * factors[t];
+        ntask += factors[t] > 1 ? part_count(ops[t], factors[t]) : 1;
+        if (L > b) { free(ops); return OR_ERR_ARG; }
+    }
+    free(ops);
+    if (b % L != 0) return OR_ERR_ARG;
+    int64_t cap = ntask + nb;
+    int8_t *code = (int8_t *)malloc((size_t)cap);
+    if (!code) return OR_ERR_CAPACITY;
+    int64_t len = or_factors_to_code(n, factors, code, cap);
+    if (len < 0) { free(code); return (int32_t)len; }
+    int32_t rc = or_simulate_side(pl, n, b, code, len, ntask, b / L, dep_mode, proc_out, start_out, finish_out,
+                                  order_out, issue_out, st);
     free(code);
     return rc;
 }
