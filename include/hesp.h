@@ -49,6 +49,7 @@ const char *hesp_status_string(int status);
 #define HESP_MAX_LEVEL 4  /* split levels per base task: 0..4 */
 #define HESP_MAX_TILES 64 /* tiles per matrix side */
 #define HESP_MAX_LOG2_BLOCK 20 /* block sizes are powers of two up to 2^20 */
+#define HESP_MAX_FACTOR 4  /* partition factors k (p = 1/k) of hesp_simulate_factors: 1..4 */
 
 /* Operations of the blocked Cholesky factorization (Sec. 1.1, Fig. 1). */
 #define HESP_OP_CHOL 0
@@ -236,6 +237,46 @@ int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands_dev, cons
                         int64_t *makespan_dev, int32_t *status_dev, int64_t *ntasks_dev, const int64_t *sched_offsets_dev,
                         int16_t *proc_dev, int64_t *start_dev, int64_t *finish_dev, void *workspace_dev,
                         size_t workspace_bytes, void *stream);
+
+/* General partition parameter (Sec. 2.1, "Iterative solver": a partition
+ * cuts a task's blocks of size d into blocks of size p d, p in (0, 1]; Fig. 4:
+ * partially overlapping blocks of two tilings of one block).  Each base task
+ * t of the Fig. 1 loop is cut once with p = 1 / k, k = factors[t] in
+ * 1 .. max_factor (k = 1 keeps it): it is replaced by its k-way blocked
+ * algorithm, whose tasks are not cut again --
+ *   chol(A):   the Fig. 1 loop on the k x k blocks of A;
+ *   trsm(T,B): B := T^-T B, for p: { for c: trsm(Tpp -> Bpc);
+ *              for i > p: for c: gemm(Tpi, Bpc -> Bic) };
+ *   syrk(A,C): for p: for i: { for j > i: gemm(Api, Apj -> Cij); syrk(Api -> Cii) };
+ *   gemm(A,B,C): for p, i, j: gemm(Api, Bpj -> Cij).
+ * k = 2 is the 2x2 partition of hesp_simulate_batch at level 1 (the same
+ * tasks in the same order); mixing k = 2 and 3 on one tile gives the
+ * non-dyadic tilings of Fig. 4.  Dependences and coherence are tracked on
+ * the common refinement of all the tilings: atoms of side b / L, L the least
+ * common multiple of the candidate's factors (b must be a multiple of L).
+ * Task times: exec(op, type, b / k) from the platform's table where b / k is
+ * a power of two (so hesp_platform_set_exec_table applies), else from the
+ * performance model of hesp_ptype.  The simulation itself (policies,
+ * caching, links, event loop, outputs) is that of hesp_simulate_batch.
+ *
+ * Inputs (device): cands_dev[n_cand] (n_tiles <= max_tiles; b must equal
+ * the argument b, else the candidate gets HESP_ERR_ARG), factors_dev (int8,
+ * one factor per base task, addressed through level_offset).  max_factor
+ * (1 .. HESP_MAX_FACTOR) and task_cap bound every candidate and must match
+ * the workspace sizing (hesp_sim_workspace_size_factors; the arena holds up
+ * to 16 dependence edges per task, more give HESP_ERR_CAPACITY).  Outputs
+ * and the optional schedule as for hesp_simulate_batch (the schedule's
+ * sizes: the task counts of the k-way partitions, e.g. from ntasks_dev of a
+ * first call).  Returns HESP_ERR_UNSUPPORTED for max_factor or max_tiles
+ * outside the limits, HESP_ERR_ARG for bad pointers or sizes; asynchronous
+ * on `stream`. */
+int hesp_sim_workspace_size_factors(const hesp_platform *p, int32_t max_tiles, int32_t max_factor, int64_t task_cap,
+                                    int64_t n_cand, size_t *bytes_out);
+int hesp_simulate_factors(const hesp_platform *p, const hesp_cand *cands_dev, const int8_t *factors_dev,
+                          int64_t n_cand, int32_t max_tiles, int32_t max_factor, int32_t b, int64_t task_cap,
+                          int64_t *makespan_dev, int32_t *status_dev, int64_t *ntasks_dev,
+                          const int64_t *sched_offsets_dev, int16_t *proc_dev, int64_t *start_dev,
+                          int64_t *finish_dev, void *workspace_dev, size_t workspace_bytes, void *stream);
 
 /* Table 1 metrics (Sec. 3) of simulated candidates, one value per candidate:
  *   busy_dev[c]      = sum over its tasks of finish - start (the processors'

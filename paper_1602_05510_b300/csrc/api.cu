@@ -26,6 +26,8 @@ int64_t regions_uniform(int64_t n, int level) {
 
 static int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
 
+Arena arena_offsets(Arena a, int32_t n_mem);
+
 Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem, int64_t task_cap) {
     Arena a;
     memset(&a, 0, sizeof a);
@@ -36,6 +38,11 @@ Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem, int64_t ta
     a.Ecap = task_cap > 0 && 4 * a.Tcap < eb ? 4 * a.Tcap : eb;
     a.Acap = ((int64_t)max_tiles * (max_tiles + 1) / 2) << (2 * max_level);
     a.Kcap = (3LL << (2 * max_level)) + 1;
+    return arena_offsets(a, n_mem);
+}
+
+// Offsets of the arena areas for the capacities in a.
+Arena arena_offsets(Arena a, int32_t n_mem) {
     const int64_t mp = n_mem <= 1 ? 0 : (n_mem == 2 ? 2 : 4);  // int64 words of coherence state per atom
     const int64_t link_bytes = 32 * a.Tcap > 8 * a.Ecap ? 32 * a.Tcap : 8 * a.Ecap;
     int64_t o = 0;
@@ -56,6 +63,39 @@ Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem, int64_t ta
     a.off_hdr = o; o = align256(o + 64);            // keep / reuse: the candidate's header
     a.slot_bytes = o;
     return a;
+}
+
+// Least common multiple of 1 .. max_factor: atoms per tile side in factor mode.
+int32_t factor_lcm(int32_t max_factor) {
+    int32_t L = 1;
+    for (int32_t f = 2; f <= max_factor; ++f) {
+        int32_t x = L, y = f;
+        while (y) {
+            const int32_t r = x % y;
+            x = y;
+            y = r;
+        }
+        L = L / x * f;
+    }
+    return L;
+}
+
+// Arena of one-level k-way partitions with factors up to max_factor: the
+// tasks of every base task cut max_factor ways, atoms of side b / lcm(1 ..
+// max_factor), edges up to 16 per task (a larger DAG reports
+// HESP_ERR_CAPACITY).
+Arena make_arena_factors(int32_t max_tiles, int32_t max_factor, int32_t n_mem, int64_t task_cap) {
+    Arena a;
+    memset(&a, 0, sizeof a);
+    const int64_t n = max_tiles, k = max_factor;
+    const int64_t tb = n * (k * (k + 1) * (k + 2) / 6) + n * (n - 1) * (k * k * (k + 1) / 2) +
+                       n * (n - 1) * (n - 2) / 6 * (k * k * k);
+    a.Tcap = task_cap > 0 && task_cap < tb ? task_cap : tb;
+    a.Ecap = 16 * a.Tcap;
+    const int64_t L = factor_lcm(max_factor);
+    a.Acap = n * (n + 1) / 2 * L * L;
+    a.Kcap = 3 * L * L + 1;
+    return arena_offsets(a, n_mem);
 }
 
 static DevPlatform dev_platform(const hesp_platform *p) {
@@ -96,6 +136,50 @@ static DevPlatform dev_platform(const hesp_platform *p) {
     return d;
 }
 
+// Task time of (op, type) on a bs x bs block: ceil(flops / rate) with
+// flops = c bs^3 / 3 and rate = peak eff/100 bs^2 / (bs^2 + h^2), i.e.
+// ceil(c bs (bs^2 + h^2) 100 / (3 peak eff)); -1 if above 2^56.
+static int64_t model_exec(const hesp_ptype &ty, int op, int64_t bs) {
+    static const int64_t coef[4] = {1, 3, 3, 6};
+    const unsigned __int128 num =
+        (unsigned __int128)coef[op] * (unsigned __int128)bs * ((unsigned __int128)bs * bs + (unsigned __int128)ty.h * ty.h) * 100u;
+    const unsigned __int128 den = (unsigned __int128)3 * (unsigned __int128)ty.peak_gflops * (unsigned __int128)ty.eff_pct[op];
+    const unsigned __int128 q = (num + den - 1) / den;
+    if (q >= ((unsigned __int128)1 << 56)) return -1;
+    return (int64_t)q;
+}
+
+
+// Factor mode: exec and wsum indexed by the factor k (1 .. max_factor) for
+// blocks of b / k: the platform's table where b / k is a power of two (so
+// that measured-model overrides apply), else the performance model; -1
+// where b / k is not an integer.
+static DevPlatform dev_platform_factors(const hesp_platform *p, int32_t b, int32_t max_factor) {
+    DevPlatform d = dev_platform(p);
+    for (int op = 0; op < 4; ++op) {
+        for (int t = 0; t < HESP_MAX_TYPES; ++t)
+            for (int k = 1; k <= max_factor; ++k) {
+                int64_t e = -1;
+                if (t < p->n_types && b % k == 0) {
+                    const int64_t bs = b / k;
+                    int l = 0;
+                    while ((1LL << l) < bs) ++l;
+                    e = (1LL << l) == bs && l < HESP_LB ? p->exec[op][t][l] : model_exec(p->types[t], op, bs);
+                }
+                d.exec[(op * HESP_MAX_TYPES + t) * HESP_LB + k] = e;
+            }
+        for (int k = 1; k <= max_factor; ++k) {
+            int64_t s = 0;
+            for (int i = 0; i < p->n_procs && s >= 0; ++i) {
+                const int64_t e = d.exec[(op * HESP_MAX_TYPES + p->procs[i].type) * HESP_LB + k];
+                s = (e < 0 || s + e >= (1LL << 40)) ? -1 : s + e;
+            }
+            d.wsum[op * HESP_LB + k] = s;
+        }
+    }
+    return d;
+}
+
 // Resident warps of the simulation kernel on the current device.
 int sim_slots_for(const hesp_platform *p, const Arena &ar, int64_t *resident_warps) {
     int dev = 0;
@@ -128,19 +212,6 @@ const char *hesp_status_string(int s) {
     case HESP_ERR_UNSUPPORTED: return "HESP_ERR_UNSUPPORTED";
     default: return "HESP_ERR_UNKNOWN";
     }
-}
-
-// Task time of (op, type) on a 2^lb block: ceil(flops / rate) with
-// flops = c bs^3 / 3 and rate = peak eff/100 bs^2 / (bs^2 + h^2), i.e.
-// ceil(c bs (bs^2 + h^2) 100 / (3 peak eff)); -1 if above 2^56.
-static int64_t model_exec(const hesp_ptype &ty, int op, int64_t bs) {
-    static const int64_t coef[4] = {1, 3, 3, 6};
-    const unsigned __int128 num =
-        (unsigned __int128)coef[op] * (unsigned __int128)bs * ((unsigned __int128)bs * bs + (unsigned __int128)ty.h * ty.h) * 100u;
-    const unsigned __int128 den = (unsigned __int128)3 * (unsigned __int128)ty.peak_gflops * (unsigned __int128)ty.eff_pct[op];
-    const unsigned __int128 q = (num + den - 1) / den;
-    if (q >= ((unsigned __int128)1 << 56)) return -1;
-    return (int64_t)q;
 }
 
 int hesp_platform_create(const hesp_platform_desc *d, hesp_platform **out) {
@@ -384,7 +455,7 @@ int simulate_common(const hesp_platform *p, const hesp_cand *cands, const int8_t
     if (slots > n_cand) slots = n_cand;
     const DevPlatform dp = dev_platform(p);
     return launch_sim(p, dp, ar, slots, cands, levels, n_cand, max_tiles, max_level, makespan, status, ntasks,
-                      sched_off, sproc, sstart, sfinish, crit, 0, 0, (char *)ws, (cudaStream_t)stream);
+                      sched_off, sproc, sstart, sfinish, crit, 0, 0, 0, 0, (char *)ws, (cudaStream_t)stream);
 }
 
 // Layout signature of keep / reuse arenas: their layout fields, mixed.
@@ -419,7 +490,7 @@ int simulate_kept(const hesp_platform *p, const hesp_cand *cands, const int8_t *
     const DevPlatform dp = dev_platform(p);
     return launch_sim(p, dp, ar, warps, cands, levels, n_cand, max_tiles, max_level, makespan, status, ntasks,
                       nullptr, nullptr, nullptr, nullptr, nullptr, dag_mode, layout_signature(ar, max_tiles, max_level),
-                      (char *)ws, (cudaStream_t)stream);
+                      0, 0, (char *)ws, (cudaStream_t)stream);
 }
 
 }  // namespace
@@ -431,6 +502,48 @@ int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands, const in
                         size_t ws_bytes, void *stream) {
     return simulate_common(p, cands, levels, n_cand, max_tiles, max_level, task_cap, makespan, status, ntasks,
                            sched_off, sproc, sstart, sfinish, nullptr, ws, ws_bytes, stream);
+}
+
+int hesp_sim_workspace_size_factors(const hesp_platform *p, int32_t max_tiles, int32_t max_factor, int64_t task_cap,
+                                    int64_t n_cand, size_t *bytes_out) {
+    if (!p || !bytes_out || n_cand < 0 || task_cap < 0) return HESP_ERR_ARG;
+    if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_factor < 1 || max_factor > HESP_MAX_FACTOR)
+        return HESP_ERR_UNSUPPORTED;
+    const Arena ar = make_arena_factors(max_tiles, max_factor, p->n_mem, task_cap);
+    int64_t resident = 0;
+    const int rc = sim_slots_for(p, ar, &resident);
+    if (rc) return rc;
+    int64_t slots = n_cand < resident ? n_cand : resident;
+    if (slots < 1) slots = 1;
+    *bytes_out = (size_t)(kWsHeaderBytes + slots * ar.slot_bytes);
+    return HESP_OK;
+}
+
+int hesp_simulate_factors(const hesp_platform *p, const hesp_cand *cands, const int8_t *factors, int64_t n_cand,
+                          int32_t max_tiles, int32_t max_factor, int32_t b, int64_t task_cap, int64_t *makespan,
+                          int32_t *status, int64_t *ntasks, const int64_t *sched_off, int16_t *sproc, int64_t *sstart,
+                          int64_t *sfinish, void *ws, size_t ws_bytes, void *stream) {
+    if (!p || n_cand < 0 || task_cap < 0) return HESP_ERR_ARG;
+    if (n_cand == 0) return HESP_OK;
+    if (!cands || !factors || !makespan || !status || !ws || b < 1) return HESP_ERR_ARG;
+    if (((uintptr_t)ws & 255) != 0) return HESP_ERR_ARG;
+    const bool any_s = sched_off || sproc || sstart || sfinish;
+    const bool all_s = sched_off && sproc && sstart && sfinish;
+    if (any_s && !all_s) return HESP_ERR_ARG;
+    if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_factor < 1 || max_factor > HESP_MAX_FACTOR ||
+        b > (1 << HESP_MAX_LOG2_BLOCK))
+        return HESP_ERR_UNSUPPORTED;
+    const Arena ar = make_arena_factors(max_tiles, max_factor, p->n_mem, task_cap);
+    if ((int64_t)ws_bytes < kWsHeaderBytes + ar.slot_bytes) return HESP_ERR_ARG;
+    int64_t resident = 0;
+    int rc = sim_slots_for(p, ar, &resident);
+    if (rc) return rc;
+    int64_t slots = ((int64_t)ws_bytes - kWsHeaderBytes) / ar.slot_bytes;
+    if (slots > resident) slots = resident;
+    if (slots > n_cand) slots = n_cand;
+    const DevPlatform dp = dev_platform_factors(p, b, max_factor);
+    return launch_sim(p, dp, ar, slots, cands, factors, n_cand, max_tiles, max_factor, makespan, status, ntasks,
+                      sched_off, sproc, sstart, sfinish, nullptr, 0, 0, 1, b, (char *)ws, (cudaStream_t)stream);
 }
 
 int hesp_schedule_metrics(const hesp_cand *cands, const int8_t *levels, int64_t n_cand, const int64_t *sched_off,

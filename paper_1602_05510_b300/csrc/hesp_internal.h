@@ -99,12 +99,14 @@ constexpr int64_t kWsHeaderBytes = 256;
 int64_t tasks_uniform(int64_t n, int level);  // tasks when every base task is split `level` times
 int64_t regions_uniform(int64_t n, int level); // sum over those tasks of their region count
 Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem, int64_t task_cap);
+Arena make_arena_factors(int32_t max_tiles, int32_t max_factor, int32_t n_mem, int64_t task_cap);
 
 int sim_slots_for(const hesp_platform *p, const Arena &ar, int64_t *resident_warps);  // device resident warps
 int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, int64_t n_slots,
                const hesp_cand *cands, const int8_t *levels, int64_t n_cand, int32_t max_tiles, int32_t max_level,
                int64_t *makespan, int32_t *status, int64_t *ntasks, const int64_t *sched_off, int16_t *sproc,
-               int64_t *sstart, int64_t *sfinish, int8_t *crit, int dag_mode, uint64_t layout_sig, char *ws,
+               int64_t *sstart, int64_t *sfinish, int8_t *crit, int dag_mode, uint64_t layout_sig, int fmode,
+               int32_t fm_b, char *ws,
                cudaStream_t stream);
 int sim_kernel_occupancy(int n_mem, int n_procs, int64_t Tcap, int *blocks_per_sm, int *threads_per_block);
 int launch_build(const Arena &ar, const hesp_cand *cands, const int8_t *levels, int64_t n_cand, int32_t max_tiles,

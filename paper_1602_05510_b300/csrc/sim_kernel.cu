@@ -185,6 +185,140 @@ __device__ __forceinline__ uint32_t desc_atom(uint64_t d, int r) {
     return (uint32_t)((d >> (5 + 19 * r)) & 0x7FFFFu);
 }
 
+// ---- one-level k-way partitions (Sec. 2.1: partition parameter p = 1 / k).
+// A base task cut with factor k is replaced by its k-way blocked algorithm
+// (chol: the Fig. 1 loop on k x k blocks; trsm, syrk, gemm: their block-row
+// algorithms); mixed factors give non-dyadic tilings (Fig. 4).  Atoms are
+// the common refinement of every tiling: a tile holds fL x fL atoms, fL the
+// least common multiple of the candidate's factors, numbered row by row; a
+// block of a k-way task is a w x w square of them, w = fL / k.
+
+// Tasks of a base task of each op cut k ways.
+__device__ __forceinline__ int fcount(int op, int k) {
+    return op == kOpChol ? k * (k + 1) * (k + 2) / 6 : (op == kOpGemm ? k * k * k : k * k * (k + 1) / 2);
+}
+
+__device__ __forceinline__ uint32_t atom_index_f(int I, int J, int r, int c, int fL, int n) {
+    const uint32_t tile = (uint32_t)(I * n - (I * (I - 1)) / 2 + (J - I));
+    return tile * (uint32_t)(fL * fL) + (uint32_t)(r * fL + c);
+}
+
+// Descriptor of sub-task q of base task (op, K, I, J) cut k ways: op | k
+// (in the level field) | first atom of each region.  Each region is block
+// (br, bc) of one of the base task's tiles (tile index tr).
+__device__ uint64_t decode_sub_f(int op, int K, int I, int J, int k, int q, int fL, int n) {
+    int TR[3] = {0, 0, 0}, TC[3] = {0, 0, 0};
+    if (op == kOpChol) {
+        TR[0] = K; TC[0] = K;
+    } else if (op == kOpTrsm) {
+        TR[0] = K; TC[0] = K; TR[1] = K; TC[1] = J;
+    } else if (op == kOpSyrk) {
+        TR[0] = K; TC[0] = I; TR[1] = I; TC[1] = I;
+    } else {
+        TR[0] = K; TC[0] = I; TR[1] = K; TC[1] = J; TR[2] = I; TC[2] = J;
+    }
+    int sop = op;
+    int tr[3] = {0, 1, 2}, br[3] = {0, 0, 0}, bc[3] = {0, 0, 0};
+    int rem = q;
+    if (k > 1 && op == kOpChol) {
+        // for p: chol(App); for c > p: trsm(App -> Apc);
+        //        for i > p: { for c > i: gemm(Api, Apc -> Aic); syrk(Api -> Aii) }
+        tr[0] = tr[1] = tr[2] = 0;
+        for (int p = 0; p < k; ++p) {
+            if (rem == 0) { sop = kOpChol; br[0] = bc[0] = p; break; }
+            rem -= 1;
+            if (rem < k - 1 - p) { sop = kOpTrsm; br[0] = bc[0] = p; br[1] = p; bc[1] = p + 1 + rem; break; }
+            rem -= k - 1 - p;
+            bool done = false;
+            for (int i = p + 1; i < k && !done; ++i) {
+                const int ng = k - 1 - i;
+                if (rem < ng) {
+                    sop = kOpGemm;
+                    br[0] = p; bc[0] = i; br[1] = p; bc[1] = i + 1 + rem; br[2] = i; bc[2] = i + 1 + rem;
+                    done = true;
+                } else if (rem == ng) {
+                    sop = kOpSyrk;
+                    br[0] = p; bc[0] = i; br[1] = i; bc[1] = i;
+                    done = true;
+                } else {
+                    rem -= ng + 1;
+                }
+            }
+            if (done) break;
+        }
+    } else if (k > 1 && op == kOpTrsm) {
+        // for p: { for c: trsm(Tpp -> Bpc); for i > p: for c: gemm(Tpi, Bpc -> Bic) }
+        for (int p = 0; p < k; ++p) {
+            if (rem < k) { sop = kOpTrsm; br[0] = bc[0] = p; br[1] = p; bc[1] = rem; break; }
+            rem -= k;
+            const int ng = (k - 1 - p) * k;
+            if (rem < ng) {
+                const int i = p + 1 + rem / k, c = rem % k;
+                sop = kOpGemm;
+                tr[0] = 0; tr[1] = 1; tr[2] = 1;
+                br[0] = p; bc[0] = i; br[1] = p; bc[1] = c; br[2] = i; bc[2] = c;
+                break;
+            }
+            rem -= ng;
+        }
+    } else if (k > 1 && op == kOpSyrk) {
+        // for p: for i: { for j > i: gemm(Api, Apj -> Cij); syrk(Api -> Cii) }
+        bool done = false;
+        for (int p = 0; p < k && !done; ++p)
+            for (int i = 0; i < k && !done; ++i) {
+                const int ng = k - 1 - i;
+                if (rem < ng) {
+                    sop = kOpGemm;
+                    tr[0] = 0; tr[1] = 0; tr[2] = 1;
+                    br[0] = p; bc[0] = i; br[1] = p; bc[1] = i + 1 + rem; br[2] = i; bc[2] = i + 1 + rem;
+                    done = true;
+                } else if (rem == ng) {
+                    sop = kOpSyrk;
+                    br[0] = p; bc[0] = i; br[1] = i; bc[1] = i;
+                    done = true;
+                } else {
+                    rem -= ng + 1;
+                }
+            }
+    } else if (k > 1) {
+        // gemm: for p, i, j: gemm(Api, Bpj -> Cij)
+        const int p = q / (k * k), i = (q / k) % k, j = q % k;
+        br[0] = p; bc[0] = i; br[1] = p; bc[1] = j; br[2] = i; bc[2] = j;
+    }
+    const int w = fL / k;
+    const int nr = nreg_of(sop);
+    uint64_t at[3] = {0, 0, 0};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        if (r < nr) {
+            const int t = tr[r];
+            const int tI = t == 0 ? TR[0] : (t == 1 ? TR[1] : TR[2]);
+            const int tJ = t == 0 ? TC[0] : (t == 1 ? TC[1] : TC[2]);
+            at[r] = atom_index_f(tI, tJ, br[r] * w, bc[r] * w, fL, n);
+        }
+    }
+    return (uint64_t)sop | ((uint64_t)k << 2) | (at[0] << 5) | (at[1] << 24) | (at[2] << 43);
+}
+
+// Atom i (region-major) of a task's regions, and its region r.  Dyadic: a
+// region is a contiguous run of 4^(Lc - lvl) = 1 << sh atoms (Z order);
+// factor mode (fm): a w x w square of the tile's fL x fL atoms.
+__device__ __forceinline__ uint32_t task_atom(uint64_t d, int i, int sh, int w, int fL, bool fm, int &r) {
+    if (!fm) {
+        r = i >> sh;
+        return desc_atom(d, r) + (uint32_t)(i & ((1 << sh) - 1));
+    }
+    const int w2 = w * w;
+    r = i / w2;
+    const int q = i - r * w2;
+    const int row = q / w;
+    return desc_atom(d, r) + (uint32_t)(row * fL + (q - row * w));
+}
+
+// Index of a task's time in the exec tables: log2 of its block (dyadic), or
+// its factor k (factor mode, tables laid out per k for the launch's b).
+__device__ __forceinline__ int exec_idx(int lb_b, int lvl, bool fm) { return fm ? lvl : lb_b - lvl; }
+
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -241,6 +375,10 @@ struct KArgs {
     Arena ar;
     int64_t n_slots;
     int32_t bm_smem_words;  // > 0: the released-task bitmap lives in shared memory
+    // 1: the levels array holds one partition factor k per base task (one-level
+    // k-way partitions, every candidate of block size fm_b; max_level is the
+    // largest factor); 0: dyadic split levels
+    int32_t fmode, fm_b;
 };
 
 template <typename T>
@@ -331,7 +469,7 @@ struct Counts {
 // internal inconsistency.
 template <int M, int NS, bool FIFO, bool REC>
 __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, char *base, const KArgs &a, int Lc, int lb_b,
-                                                 int lane, const int64_t *s_exec, const int8_t *s_pmem,
+                                                 int fL, int lane, const int64_t *s_exec, const int8_t *s_pmem,
                                                  const int8_t *s_ptype, const int pm[NS], const int pt[NS],
                                                  const bool pv[NS], int64_t avail[NS], int head[NS], int tail[NS],
                                                  int64_t hfin[NS], int64_t &mk, bool &ok, int64_t sched_base,
@@ -339,9 +477,12 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
     const int op = (int)(d & 3);
     const int lvl = (int)((d >> 2) & 7);
     const int nr = nreg_of(op);
-    const int sh = 2 * (Lc - lvl);
-    const int tot = nr << sh;
-    const int lb = lb_b - lvl;
+    const bool fm = REC && fL > 0;          // factor mode: lvl is the factor k
+    const int wf = fm ? fL / lvl : 0;       // block side in atoms (factor mode)
+    const int sh = fm ? 0 : 2 * (Lc - lvl);
+    const int na = fm ? wf * wf : 1 << sh;  // atoms per region
+    const int tot = nr * na;
+    const int lb = exec_idx(lb_b, lvl, fm);
     constexpr int MP = AtomState<M>::MP;
     int64_t *vfrom = at<int64_t>(base, a.ar.off_vfrom);
     // transfer time of k atoms: one table, or (links) one per ordered pair
@@ -377,7 +518,8 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
         for (int i0 = 0; i0 < tot; i0 += 32) {
             const int i = i0 + lane;
             if (i < tot) {
-                const uint32_t x = desc_atom(d, i >> sh) + (uint32_t)(i & ((1 << sh) - 1));
+                int rr;
+                const uint32_t x = task_atom(d, i, sh, wf, fL, fm, rr);
                 AtomState<M> st;
                 st.load(vfrom + (int64_t)x * MP);
                 const int src = st.fetch_source(t, cache);
@@ -504,8 +646,8 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
         for (int i0 = 0; i0 < tot; i0 += 32) {
             const int i = i0 + lane;
             if (i < tot) {
-                const int r = i >> sh;
-                const uint32_t x = desc_atom(d, r) + (uint32_t)(i & ((1 << sh) - 1));
+                int r;
+                const uint32_t x = task_atom(d, i, sh, wf, fL, fm, r);
                 int64_t *px = vfrom + (int64_t)x * MP;
                 if (r == nr - 1) {
                     // written block, every other copy invalidated: WB valid in
@@ -514,7 +656,7 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
                     // in host memory, from finish + xfer(block)
                     const bool acc = ms != 0 && cache != HESP_CACHE_WB;
                     const int64_t v_ms = (cache == HESP_CACHE_WA && ms != 0) ? -1 : eft;
-                    const int64_t v_host = acc ? eft + xtab(ms, 0)[1 << sh] : -1;
+                    const int64_t v_host = acc ? eft + xtab(ms, 0)[na] : -1;
                     longlong2 w0, w1;
                     w0.x = ms == 0 ? v_ms : v_host;
                     w0.y = ms == 1 ? v_ms : -1;
@@ -608,6 +750,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
+    const bool fm = GEN && a.fmode != 0;  // one-level k-way partitions
     const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (slot >= a.n_slots) return;  // whole warp
     char *const slot_base = a.ws + slot * a.ar.slot_bytes;
@@ -642,15 +785,18 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
         int64_t T = 0;
         int64_t mk = 0;
 
-        const bool bad_nb = n < 1 || n > a.max_tiles || b < 1 || (b & (b - 1)) != 0 || b > (1 << HESP_MAX_LOG2_BLOCK);
+        const bool bad_nb = n < 1 || n > a.max_tiles || b < 1 || (!fm && (b & (b - 1)) != 0) ||
+                            b > (1 << HESP_MAX_LOG2_BLOCK);
         const int64_t nb = bad_nb ? 0 : (int64_t)n * (n + 1) * (n + 2) / 6;
         int lmax = 0;
+        unsigned fmask = 0;  // factor mode: the factors present
         bool badl = false;
         uint64_t lvh = 0;  // (keep / reuse) hash of the levels: sum of (l + 1) (t + 1) gamma
         for (int64_t t0 = lane; t0 < nb; t0 += 32) {
             const int l = a.levels[loff + t0];
             lmax = max(lmax, l);
-            badl |= (l < 0 || l > a.max_level);
+            badl |= (l < (fm ? 1 : 0) || l > a.max_level);
+            if (fm && l >= 1 && l <= 8) fmask |= 1u << l;
             lvh += (uint64_t)(l + 1) * ((uint64_t)(t0 + 1) * kGamma);
         }
         if (a.dag_mode) {
@@ -660,20 +806,40 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
         }
         lmax = __reduce_max_sync(FULL, lmax);
         badl = __any_sync(FULL, badl);
-        const int Lc = lmax;
+        // factor mode: a tile holds fL x fL atoms, fL = lcm of the factors
+        int fL = 0;
+        if (fm) {
+            fmask = __reduce_or_sync(FULL, fmask);
+            fL = 1;
+            for (int f = 2; f <= 8; ++f)
+                if ((fmask >> f) & 1u) {
+                    int x = fL, y = f;
+                    while (y) {
+                        const int r = x % y;
+                        x = y;
+                        y = r;
+                    }
+                    fL = fL / x * f;
+                }
+        }
+        const int Lc = fm ? 0 : lmax;
         const int lb_b = bad_nb ? 0 : 31 - __clz(b);
         if (bad_nb || badl || (b >> Lc) < 1) status = HESP_ERR_ARG;
+        if (fm && status == HESP_OK && (b != a.fm_b || b % fL != 0)) status = HESP_ERR_ARG;
 
-        const int64_t A = (int64_t)n * (n + 1) / 2 << (2 * Lc);
+        const int64_t A = fm ? (int64_t)n * (n + 1) / 2 * fL * fL : (int64_t)n * (n + 1) / 2 << (2 * Lc);
         if (status == HESP_OK && (A > a.ar.Acap || A >= (1 << 19))) status = HESP_ERR_CAPACITY;
         // task times used by this candidate must be representable
         if (!BUILD && status == HESP_OK) {
             bool bad = false;
-            for (int e = lane; e < 4 * HESP_MAX_TYPES * (Lc + 1); e += 32) {
-                const int op = e / (HESP_MAX_TYPES * (Lc + 1));
-                const int rem = e % (HESP_MAX_TYPES * (Lc + 1));
-                const int ty = rem / (Lc + 1), l = rem % (Lc + 1);
-                if (ty < pl.n_types && s_exec[(op * HESP_MAX_TYPES + ty) * HESP_LB + lb_b - l] < 0) bad = true;
+            const int nl = fm ? 9 : Lc + 1;  // levels 0..Lc, or factors 1..8
+            for (int e = lane; e < 4 * HESP_MAX_TYPES * nl; e += 32) {
+                const int op = e / (HESP_MAX_TYPES * nl);
+                const int rem = e % (HESP_MAX_TYPES * nl);
+                const int ty = rem / nl, l = rem % nl;
+                const bool used = !fm || ((fmask >> l) & 1u) != 0;
+                if (used && ty < pl.n_types && s_exec[(op * HESP_MAX_TYPES + ty) * HESP_LB + exec_idx(lb_b, l, fm)] < 0)
+                    bad = true;
             }
             if (__any_sync(FULL, bad)) status = HESP_ERR_ARG;
         }
@@ -689,7 +855,8 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                 if (t < nb) {
                     int op, K, I, J;
                     decode_base(n, t, op, K, I, J);
-                    cnt = c_cnt[op][a.levels[loff + t]];
+                    const int l = a.levels[loff + t];
+                    cnt = fm ? fcount(op, l) : c_cnt[op][l];
                 }
                 tcount += __reduce_add_sync(FULL, (unsigned)cnt);
             }
@@ -705,7 +872,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                 if (t < nb) {
                     decode_base(n, t, op, K, I, J);
                     l = a.levels[loff + t];
-                    cnt = c_cnt[op][l];
+                    cnt = fm ? fcount(op, l) : c_cnt[op][l];
                 }
                 const int incl = warp_incl_scan(cnt, lane);
                 const int excl = incl - cnt;
@@ -726,7 +893,9 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     const int oI = __shfl_sync(FULL, I, owner);
                     const int oJ = __shfl_sync(FULL, J, owner);
                     const int ol = __shfl_sync(FULL, l, owner);
-                    if (g < total) desc[off + g] = decode_sub(oop, oK, oI, oJ, ol, q, Lc, n);
+                    if (g < total)
+                        desc[off + g] = fm ? decode_sub_f(oop, oK, oI, oJ, ol, q, fL, n)
+                                           : decode_sub(oop, oK, oI, oJ, ol, q, Lc, n);
                 }
                 off += total;
             }
@@ -756,9 +925,10 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                 const int op = (int)(d & 3);
                 const int lvl = (int)((d >> 2) & 7);
                 const int nr = nreg_of(op);
-                const int sh = 2 * (Lc - lvl);
-                const int na = 1 << sh;
-                const int tot = nr << sh;
+                const int wf = fm ? fL / lvl : 0;
+                const int sh = fm ? 0 : 2 * (Lc - lvl);
+                const int na = fm ? wf * wf : 1 << sh;
+                const int tot = nr * na;
                 // a task whose atoms fit one round is deduplicated inside the
                 // warp; larger ones also use the per-task mark across rounds
                 const bool multi = tot > 32;
@@ -766,7 +936,8 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                 for (int i0 = 0; i0 < tot; i0 += 32) {
                     const int i = i0 + lane;
                     int w = -1;
-                    if (i < tot) w = lw[desc_atom(d, i >> sh) + (uint32_t)(i & (na - 1))];
+                    int rr;
+                    if (i < tot) w = lw[task_atom(d, i, sh, wf, fL, fm, rr)];
                     const unsigned grp = __match_any_sync(FULL, w);
                     bool isnew = lane == __ffs(grp) - 1 && w >= 0;
                     if (multi && isnew) {
@@ -787,8 +958,10 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                 }
                 if (lane == 0) pending[j] = (uint16_t)cnt;
                 E += cnt;
-                const uint32_t xw = desc_atom(d, nr - 1);
-                for (int i = lane; i < na; i += 32) lw[xw + i] = j;
+                for (int i = lane; i < na; i += 32) {
+                    int rr;
+                    lw[task_atom(d, (nr - 1) * na + i, sh, wf, fL, fm, rr)] = j;
+                }
                 __syncwarp();
             }
             if (E > a.ar.Ecap) status = HESP_ERR_CAPACITY;
@@ -872,8 +1045,9 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                 // transfer time of k atoms (k * (b >> Lc)^2 elements): one
                 // table, or (links) one per ordered pair of memories
                 int64_t *const xt = at<int64_t>(base, a.ar.off_xt);
-                const int64_t ae = (int64_t)(b >> Lc) * (int64_t)(b >> Lc);
-                const int kmax = 3 << (2 * Lc);
+                const int64_t as = fm ? (int64_t)(b / fL) : (int64_t)(b >> Lc);
+                const int64_t ae = as * as;
+                const int kmax = fm ? 3 * fL * fL : 3 << (2 * Lc);
                 for (int k = lane; k <= kmax; k += 32) {
                     const int64_t bytes = (int64_t)k * ae * pl.bpe;
                     xt[k] = k == 0 ? 0 : pl.lat + (bytes + pl.bw - 1) / pl.bw;
@@ -920,7 +1094,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     uint64_t mx = 0;
                     for (int e = e0 + lane; e < e1; e += 32) mx = max(mx, (uint64_t)crit[succ[e]]);
                     mx = warp_max_u64(mx);
-                    const int64_t w = s_wsum[(int)(d & 3) * HESP_LB + lb_b - (int)((d >> 2) & 7)];
+                    const int64_t w = s_wsum[(int)(d & 3) * HESP_LB + exec_idx(lb_b, (int)((d >> 2) & 7), fm)];
                     const int64_t cj = (int64_t)mx + w;
                     okp = okp && w > 0 && cj < (1ll << 41);
                     if (lane == 0) crit[j] = cj;
@@ -997,7 +1171,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                             }
                         if (!__any_sync(FULL, any)) tj = (int64_t)warp_min_u64(mn);
                     }
-                    const int64_t fj = schedule_task<M, NS, false, GEN>(j, desc[j], tj, base, a, Lc, lb_b, lane, s_exec, s_pmem,
+                    const int64_t fj = schedule_task<M, NS, false, GEN>(j, desc[j], tj, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem,
                                                                    s_ptype, pm, pt, pv, avail, head, tail, hfin, mk,
                                                                    ok, sched_base, sel, rp_seed, cache, links);
                     const int e0 = succoff[j], e1 = succoff[j + 1];
@@ -1065,7 +1239,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                             ++qt;
                             continue;
                         }
-                        schedule_task<M, NS, true, GEN>(j, dsc, t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
+                        schedule_task<M, NS, true, GEN>(j, dsc, t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
                                                    avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache, links);
                         ++scheduled;
                     }
@@ -1092,7 +1266,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                                     ++qt;
                                     continue;
                                 }
-                                schedule_task<M, NS, true, GEN>(jb + bit, desc[jb + bit], t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype,
+                                schedule_task<M, NS, true, GEN>(jb + bit, desc[jb + bit], t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype,
                                                            pm, pt, pv, avail, head, tail, hfin, mk, ok, sched_base,
                                                            sel, rp_seed, cache, links);
                                 ++scheduled;
@@ -1112,7 +1286,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                         if (!__any_sync(FULL, any)) break;
                         const int j = link[qh].rq;
                         ++qh;
-                        schedule_task<M, NS, true, GEN>(j, desc[j], t, base, a, Lc, lb_b, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
+                        schedule_task<M, NS, true, GEN>(j, desc[j], t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
                                                    avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache, links);
                         ++scheduled;
                     }
@@ -1202,8 +1376,8 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
             int64_t *const up = down + T;
             auto dur = [&](int64_t j) -> int64_t {
                 const uint64_t d = desc[j];
-                return s_exec[((int)(d & 3) * HESP_MAX_TYPES + s_ptype[prc[j]]) * HESP_LB + lb_b -
-                              (int)((d >> 2) & 7)];
+                return s_exec[((int)(d & 3) * HESP_MAX_TYPES + s_ptype[prc[j]]) * HESP_LB +
+                              exec_idx(lb_b, (int)((d >> 2) & 7), fm)];
             };
             // longest path from each task to a sink (creation order is topological)
             for (int64_t j = T - 1; j >= 0; --j) {
@@ -1235,7 +1409,8 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                 if (t < nb) {
                     int op, K, I, J;
                     decode_base(n, t, op, K, I, J);
-                    cnt = c_cnt[op][a.levels[loff + t]];
+                    const int l = a.levels[loff + t];
+                    cnt = fm ? fcount(op, l) : c_cnt[op][l];
                 }
                 const int incl = warp_incl_scan(cnt, lane);
                 if (t < nb) {
@@ -1397,7 +1572,8 @@ int sim_kernel_occupancy(int n_mem, int n_procs, int64_t Tcap, int *blocks_per_s
 int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, int64_t n_slots,
                const hesp_cand *cands, const int8_t *levels, int64_t n_cand, int32_t max_tiles, int32_t max_level,
                int64_t *makespan, int32_t *status, int64_t *ntasks, const int64_t *sched_off, int16_t *sproc,
-               int64_t *sstart, int64_t *sfinish, int8_t *crit, int dag_mode, uint64_t layout_sig, char *ws,
+               int64_t *sstart, int64_t *sfinish, int8_t *crit, int dag_mode, uint64_t layout_sig, int fmode,
+               int32_t fm_b, char *ws,
                cudaStream_t stream) {
     KArgs a;
     a.cands = cands;
@@ -1415,6 +1591,8 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
     a.crit = crit;
     a.dag_mode = dag_mode;
     a.layout_sig = layout_sig;
+    a.fmode = fmode;
+    a.fm_b = fm_b;
     a.ar = ar;
     a.n_slots = n_slots;
     a.ws = ws + kWsHeaderBytes;
@@ -1427,7 +1605,7 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
     const bool two = p->n_procs > 32;
     const unsigned ub = (unsigned)blocks;
     const bool gen = p->order != HESP_ORDER_FCFS || p->select != HESP_SELECT_EFT || p->cache != HESP_CACHE_WB ||
-                     p->use_links || crit != nullptr;
+                     p->use_links || crit != nullptr || fmode != 0;
     switch (p->n_mem) {
     case 1: two ? launch_one<1, 2>(gen, ub, threads, smem, stream, dp, a, ctr)
                 : launch_one<1, 1>(gen, ub, threads, smem, stream, dp, a, ctr); break;

@@ -18,10 +18,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhesp.so")
 
 HESP_OK = 0
+HESP_ERR_ARG, HESP_ERR_CAPACITY, HESP_ERR_UNSUPPORTED = -1, -2, -6
 STATUS_NAMES = {0: "HESP_OK", -1: "HESP_ERR_ARG", -2: "HESP_ERR_CAPACITY", -3: "HESP_ERR_CUDA",
                 -4: "HESP_ERR_TIMEOUT", -5: "HESP_ERR_STATE", -6: "HESP_ERR_UNSUPPORTED"}
 GEN_EXHAUSTIVE, GEN_UNIFORM = 0, 1
 MAX_LEVEL, MAX_TILES, MAX_PROCS, MAX_MEMS, MAX_TYPES = 4, 64, 64, 4, 4
+MAX_FACTOR = 4  # partition factors k (p = 1/k) of simulate_factors
 
 # Every symbol include/hesp.h declares (checked by the CPU tests).
 EXPORTS = (
@@ -38,6 +40,7 @@ EXPORTS = (
     "hesp_graph_launch", "hesp_graph_destroy", "hesp_platform_set_tuning", "hesp_platform_get_tuning",
     "hesp_sim_autotune", "hesp_sort_cands_workspace_size", "hesp_sort_cands_by_size", "hesp_platform_set_policy",
     "hesp_simulate_critical", "hesp_solver_moves", "hesp_solver_pick", "hesp_schedule_metrics",
+    "hesp_sim_workspace_size_factors", "hesp_simulate_factors",
     "hesp_sim_workspace_size_kept", "hesp_simulate_batch_keep", "hesp_simulate_batch_reuse",
     "hesp_platform_set_cache", "hesp_surrogate_save", "hesp_surrogate_load", "hesp_platform_set_link",
     "hesp_dag_build_kept",
@@ -103,6 +106,9 @@ def lib():
         L.hesp_simulate_batch.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         L.hesp_simulate_batch_noalloc.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.hesp_simulate_critical.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, sz, vp]
+        L.hesp_sim_workspace_size_factors.argtypes = [vp, i32, i32, i64, i64, ctypes.POINTER(sz)]
+        L.hesp_simulate_factors.argtypes = [vp, vp, vp, i64, i32, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, sz,
+                                            vp]
         L.hesp_sim_workspace_size_kept.argtypes = [i32, i32, i64, i64, ctypes.POINTER(sz)]
         L.hesp_simulate_batch_keep.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, sz, vp]
         L.hesp_dag_build_kept.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp, vp, sz, vp]
@@ -299,6 +305,36 @@ def simulate_batch(platform: Platform, cands, levels, n_cand, max_tiles, max_lev
                                     _ptr(makespan), _ptr(status), _ptr(ntasks), _ptr(so), _ptr(sp), _ptr(ss),
                                     _ptr(sf), _ptr(workspace), workspace.numel(), _stream(stream)),
           "hesp_simulate_batch")
+    return makespan, status, ntasks
+
+
+def alloc_workspace_factors(platform: Platform, max_tiles, max_factor, n_cand, task_cap=0):
+    """Workspace of simulate_factors for up to n_cand concurrent candidates."""
+    import torch
+    n = ctypes.c_size_t()
+    check(lib().hesp_sim_workspace_size_factors(platform.h, max_tiles, max_factor, task_cap, n_cand, ctypes.byref(n)),
+          "hesp_sim_workspace_size_factors")
+    return torch.empty(n.value, dtype=torch.uint8, device="cuda")
+
+
+def simulate_factors(platform: Platform, cands, factors, n_cand, max_tiles, max_factor, b, workspace,
+                     makespan=None, status=None, ntasks=None, schedule=None, stream=None, task_cap=0):
+    """hesp_simulate_factors: one partition factor k (p = 1/k) per base task,
+    every candidate of block size b.  Arguments and results as
+    simulate_batch, with `factors` (int8 device tensor) in place of levels."""
+    import torch
+    dev = factors.device
+    if makespan is None:
+        makespan = torch.empty(n_cand, dtype=torch.int64, device=dev)
+    if status is None:
+        status = torch.empty(n_cand, dtype=torch.int32, device=dev)
+    so = sp = ss = sf = None
+    if schedule is not None:
+        so, sp, ss, sf = schedule
+    check(lib().hesp_simulate_factors(platform.h, _ptr(cands), _ptr(factors), n_cand, max_tiles, max_factor, b,
+                                      task_cap, _ptr(makespan), _ptr(status), _ptr(ntasks), _ptr(so), _ptr(sp),
+                                      _ptr(ss), _ptr(sf), _ptr(workspace), workspace.numel(), _stream(stream)),
+          "hesp_simulate_factors")
     return makespan, status, ntasks
 
 

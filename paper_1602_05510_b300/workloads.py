@@ -147,6 +147,16 @@ def uniform_levels(seed: int, first: int, count: int, n_base: int, n_levels: int
     return draw(counter_u64(seed, c, t), n_levels).astype(np.int8)
 
 
+def uniform_factors(seed: int, first: int, count: int, n_base: int, max_factor: int) -> np.ndarray:
+    """Partition factors k (p = 1/k) per base task: 1 + draw(max_factor) of
+    output k = t of candidate first + c."""
+    return (uniform_levels(seed, first, count, n_base, max_factor) + 1).astype(np.int8)
+
+
+# Non-dyadic workload: 8 x 8 tiles of b = 3072 = 12 * 256 (so that every mix
+# of factors 1..4 tiles a block exactly), factors uniform in {1, 2, 3, 4}.
+FACTOR_N, FACTOR_B, FACTOR_MAX = 8, 3072, 4
+
 B_CHOICES = (512, 1024, 2048)
 
 
