@@ -569,6 +569,62 @@ def run_uneven(args):
     print(json.dumps(line))
 
 
+def run_factors(args):
+    """General partition parameter (one-level k-way partitions, p = 1/k):
+    65,536 candidates of 8 x 8 tiles of b = 3072 with factors uniform in
+    {1, 2, 3, 4} (non-dyadic tilings wherever 3 meets 2 or 4), simulated on
+    both platforms of the default workload; inputs resident on the device, a
+    256 MB buffer written between steps."""
+    import torch
+
+    from paper_1602_05510_b300 import build, hesp
+
+    build.build()
+    n, b, K = W.FACTOR_N, W.FACTOR_B, W.FACTOR_MAX
+    C = args.candidates
+    nb = W.base_count(n)
+    f = torch.from_numpy(W.uniform_factors(9, 0, C, nb, K).reshape(-1).copy()).cuda()
+    cands = hesp.cands_tensor(n, b, np.arange(C, dtype=np.int64) * nb)
+    plats = [hesp.Platform(W.PLATFORMS[k]) for k in PLATS]
+    wss = [hesp.alloc_workspace_factors(p, n, K, C) for p in plats]
+    ms = [torch.empty(C, dtype=torch.int64, device="cuda") for _ in plats]
+    st = [torch.empty(C, dtype=torch.int32, device="cuda") for _ in plats]
+    nt = [torch.empty(C, dtype=torch.int64, device="cuda") for _ in plats]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        for i, p in enumerate(plats):
+            hesp.simulate_factors(p, cands, f, C, n, K, b, wss[i], makespan=ms[i], status=st[i], ntasks=nt[i])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t_k = [0.0 for _ in plats]
+    for it in range(args.steps):
+        flush.fill_(it & 255)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(plats) + 1)]
+        ev[0].record()
+        for i, p in enumerate(plats):
+            hesp.simulate_factors(p, cands, f, C, n, K, b, wss[i], makespan=ms[i], status=st[i], ntasks=nt[i])
+            ev[i + 1].record()
+        torch.cuda.synchronize()
+        for i in range(len(plats)):
+            t_k[i] += ev[i].elapsed_time(ev[i + 1]) / 1e3
+    ok = all(bool((x == 0).all().item()) for x in st)
+    events = sum(int(x.sum().item()) for x in nt)
+    t = sum(t_k)
+    line = {"metric": METRIC, "value": events * args.steps / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "int64", "data": "synthetic",
+            "workload": "non-dyadic partitions: N=24576 Cholesky, b=3072 (8x8 tiles, 120 base tasks), one "
+                        "partition factor k in {1,2,3,4} (p = 1/k) per base task, %d candidates, atoms of "
+                        "b / lcm(factors), simulated on 12 CPU + 1 GPU-type and on 4 big + 4 LITTLE" % C,
+            "ms_per_step": 1e3 * t / args.steps, "all_ok": ok, "task_events_per_step": events,
+            "candidates_per_s": C * len(plats) * args.steps / t,
+            "kernel_ms_per_step": {k: 1e3 * x / args.steps for k, x in zip(PLATS, t_k)},
+            "l2": "256 MB buffer written between timed steps"}
+    print(json.dumps(line))
+
+
 def run_exhaustive(args):
     """The exhaustive search of the 3 x 3-tile problem (N = 3072, b = 1024):
     all 1,024 partitions (each base task split once or not), generated,
@@ -774,7 +830,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=256)
     ap.add_argument("--candidates", type=int, default=N_CAND,
                     help="candidates per step (default: the workload's 65,536; smaller only for profiling)")
-    ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search", "uneven", "solver", "table1", "exhaustive"],
+    ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search", "uneven", "solver", "table1", "exhaustive",
+                             "factors"],
                     help="random: the default benchmark line; surrogate: label/train/rank/re-score "
                          "pipeline; search: surrogate-guided vs random search")
     ap.add_argument("--labels", type=int, default=1 << 20)
@@ -801,6 +858,8 @@ def main():
         return run_solver(args)
     if args.workload == "table1":
         return run_table1(args)
+    if args.workload == "factors":
+        return run_factors(args)
     if args.workload == "exhaustive":
         return run_exhaustive(args)
     if args.impl == "reference":
