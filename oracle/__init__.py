@@ -78,12 +78,14 @@ class Platform(ctypes.Structure):
         ("use_links", ctypes.c_int32),
         ("link_lat", (ctypes.c_int64 * MAX_MEMS) * MAX_MEMS),
         ("link_bw", (ctypes.c_int64 * MAX_MEMS) * MAX_MEMS),
+        ("cap_bytes", ctypes.c_int64 * MAX_MEMS),
     ]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in
-                ("makespan", "n_tasks", "n_events", "n_transfers", "xfer_elems", "atom_visits")]
+                ("makespan", "n_tasks", "n_events", "n_transfers", "xfer_elems", "atom_visits", "evicted",
+                 "written_back")]
 
 
 def _p(a, ct):
@@ -135,13 +137,14 @@ CACHE_WB, CACHE_WT, CACHE_WA = 0, 1, 2
 
 
 def make_platform(desc, order: int = ORDER_FCFS, select: int = SELECT_EFT, rp_seed: int = 0,
-                  cache: int = CACHE_WB, links=None) -> Platform:
+                  cache: int = CACHE_WB, links=None, capacity=None) -> Platform:
     """Oracle platform from a plain description (a dict or an object with the
     fields of ``paper_1602_05510_b300.workloads.PlatformSpec``), with the
     task order (FCFS / PL), the processor selection (EFT-P / EIT-P / F-P /
-    R-P), the seed of R-P's draws, the caching policy (WB / WT / WA) and,
-    optionally, per-link costs {(src, dst): (latency_ns, bytes_per_ns)} (the
-    other pairs keep the platform's scalars)."""
+    R-P), the seed of R-P's draws, the caching policy (WB / WT / WA),
+    optionally per-link costs {(src, dst): (latency_ns, bytes_per_ns)} (the
+    other pairs keep the platform's scalars) and finite capacities of
+    accelerator memories {mem: bytes}."""
     g = (lambda k: desc[k]) if isinstance(desc, dict) else (lambda k: getattr(desc, k))
     pl = Platform()
     pl.n_mem = g("n_mem")
@@ -174,6 +177,8 @@ def make_platform(desc, order: int = ORDER_FCFS, select: int = SELECT_EFT, rp_se
                 lat, bw = links.get((s_, d_), (pl.xfer_latency_ns, pl.bw_bytes_per_ns))
                 pl.link_lat[s_][d_] = lat
                 pl.link_bw[s_][d_] = bw
+    for m, nbytes in (capacity or {}).items():
+        pl.cap_bytes[m] = nbytes
     return pl
 
 
@@ -331,7 +336,7 @@ def _result(rc, st, proc, start, fin, order, issue):
     T = int(st.n_tasks)
     out = dict(status=int(rc), makespan=int(st.makespan), n_tasks=T, n_events=int(st.n_events),
                n_transfers=int(st.n_transfers), xfer_elems=int(st.xfer_elems),
-               atom_visits=int(st.atom_visits))
+               atom_visits=int(st.atom_visits), evicted=int(st.evicted), written_back=int(st.written_back))
     if proc is not None:
         out.update(proc=proc[:T].copy(), start=start[:T].copy(), finish=fin[:T].copy(),
                    order=order[:T].copy(), issue=issue[:T].copy())

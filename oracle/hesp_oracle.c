@@ -84,6 +84,9 @@ typedef struct {
     int32_t use_links;
     int64_t link_lat[OR_MAX_MEMS][OR_MAX_MEMS];
     int64_t link_bw[OR_MAX_MEMS][OR_MAX_MEMS];
+    /* finite memory spaces (Sec. 2): capacity of each accelerator memory in
+     * bytes, 0 = unbounded; host memory (0) is always unbounded */
+    int64_t cap_bytes[OR_MAX_MEMS];
 } or_platform;
 
 /* A square data region in element coordinates of the full matrix. */
@@ -655,6 +658,8 @@ typedef struct {
     int64_t n_transfers;  /* messages issued */
     int64_t xfer_elems;   /* elements moved */
     int64_t atom_visits;  /* sum over tasks of atoms in their regions */
+    int64_t evicted;      /* atoms evicted from finite memories */
+    int64_t written_back; /* of those, atoms written back to host memory */
 } or_stats;
 
 /* State of one simulation, shared by the task-order loops below. */
@@ -671,6 +676,10 @@ typedef struct {
     int32_t *axw;
     int32_t *src;
     or_stats *st;
+    int64_t *use;                     /* per atom x memory: latest finish of a task that used it there */
+    int8_t bounded[OR_MAX_MEMS];      /* finite memory */
+    int64_t cap_atoms[OR_MAX_MEMS];   /* its capacity in atoms (whole atoms only) */
+    uint8_t *wb;                      /* per atom: written back by the current eviction */
     int16_t *proc_out;
     int64_t *start_out, *finish_out;
     int32_t *order_out;
@@ -761,6 +770,32 @@ static int schedule_task(sched_state *S, int32_t j, int64_t t) {
             }
         }
     }
+    /* Finite memories (reading of Sec. 2, which names finite-size memory
+     * spaces but no policy): a bounded memory m can take task j at t when the
+     * atoms j lacks there fit in its free space plus what it may evict --
+     * atoms valid in m that j does not use and that no task in flight on m
+     * still uses (use[x][m] <= t).  Processors of memories that cannot take j
+     * are not candidates. */
+    int feasible[OR_MAX_MEMS];
+    int64_t need[OR_MAX_MEMS], room[OR_MAX_MEMS];
+    int any_bounded = 0;
+    for (int m = 0; m < M; m++) {
+        feasible[m] = 1;
+        need[m] = room[m] = 0;
+        if (!S->mem_used[m] || !S->bounded[m]) continue;
+        any_bounded = 1;
+        for (int64_t e = 0; e < na; e++) need[m] += !valid[ax[e] * M + m];
+        int64_t occ = 0, evictable = 0;
+        for (int64_t x = 0; x < g->grid * g->grid; x++) {
+            if (!valid[x * M + m]) continue;
+            occ++;
+            int mine = 0;
+            for (int64_t e = 0; e < na && !mine; e++) mine = ax[e] == x;
+            if (!mine && S->use[x * M + m] <= t) evictable++;
+        }
+        room[m] = S->cap_atoms[m] - occ;
+        feasible[m] = need[m] <= room[m] + evictable;
+    }
     /* processor selection, ties to the lowest id:
      *   EFT-P: the earliest finish time max(t, avail, DRT) + exec;
      *   EIT-P: the processor that becomes idle first, max(t, avail);
@@ -778,6 +813,7 @@ static int schedule_task(sched_state *S, int32_t j, int64_t t) {
     int64_t best_key = 0, best_eft = 0, best_exec = 0;
     for (int p = 0; p < P; p++) {
         if (pl->select >= 2 && S->avail[p] > t) continue;
+        if (!feasible[pl->proc_mem[p]]) continue;
         int64_t ready = t;
         if (S->avail[p] > ready) ready = S->avail[p];
         int64_t idle = ready;
@@ -792,7 +828,46 @@ static int schedule_task(sched_state *S, int32_t j, int64_t t) {
         idle_seen++;
         if (best < 0 || key < best_key) { best = p; best_key = key; best_eft = eft; best_exec = ex; }
     }
+    if (best < 0) return OR_ERR_CAPACITY; /* no memory can take the task */
     int ms = pl->proc_mem[best];
+    /* eviction from a bounded memory: the least recently used evictable atom
+     * first (smallest use[x][ms], ties to the lower atom index) until the
+     * missing atoms fit; an evicted atom valid in no other memory is written
+     * back to host memory, all of them in one message issued at t, valid in
+     * host memory from its arrival */
+    if (any_bounded && S->bounded[ms] && need[ms] > room[ms]) {
+        int64_t k = need[ms] - room[ms], n_wb = 0;
+        for (int64_t q = 0; q < k; q++) {
+            int64_t victim = -1;
+            for (int64_t x = 0; x < g->grid * g->grid; x++) {
+                if (!valid[x * M + ms] || S->use[x * M + ms] > t) continue;
+                int mine = 0;
+                for (int64_t e = 0; e < na && !mine; e++) mine = ax[e] == x;
+                if (mine) continue;
+                if (victim < 0 || S->use[x * M + ms] < S->use[victim * M + ms]) victim = x;
+            }
+            if (victim < 0) return OR_ERR_STATE;
+            int elsewhere = 0;
+            for (int m = 0; m < M; m++)
+                if (m != ms && valid[victim * M + m]) elsewhere = 1;
+            valid[victim * M + ms] = 0;
+            if (!elsewhere) {
+                S->wb[victim] = 1;
+                n_wb++;
+            }
+            S->st->evicted++;
+        }
+        if (n_wb > 0) {
+            int64_t arrive_host = t + or_xfer_pair_ns(pl, ms, 0, n_wb * atom_elems);
+            for (int64_t x = 0; x < g->grid * g->grid; x++)
+                if (S->wb[x]) {
+                    S->wb[x] = 0;
+                    valid[x * M + 0] = 1;
+                    vfrom[x * M + 0] = arrive_host;
+                }
+            S->st->written_back += n_wb;
+        }
+    }
     /* commit: transfers, then write-back invalidation of written atoms */
     int64_t elems_from2[OR_MAX_MEMS];
     for (int sm = 0; sm < M; sm++) elems_from2[sm] = 0;
@@ -828,6 +903,8 @@ static int schedule_task(sched_state *S, int32_t j, int64_t t) {
             vfrom[x * M + 0] = through;
         }
     }
+    for (int64_t e = 0; e < na; e++)
+        if (S->use[ax[e] * M + ms] < best_eft) S->use[ax[e] * M + ms] = best_eft;
     S->avail[best] = best_eft;
     S->finish_j = best_eft;
     if (S->proc_out) S->proc_out[j] = (int16_t)best;
@@ -907,6 +984,14 @@ int32_t or_simulate_side(const or_platform *pl, int32_t n, int64_t b, const int8
         if (pl->proc_mem[p] < 0 || pl->proc_mem[p] >= pl->n_mem || pl->proc_type[p] < 0 ||
             pl->proc_type[p] >= pl->n_types)
             return OR_ERR_ARG;
+    /* finite memories: accelerators only, with EFT-P or EIT-P (F-P and R-P
+     * would also need a rule for idle processors whose memory is full) */
+    int bounded = 0;
+    for (int m = 0; m < pl->n_mem; m++) {
+        if (pl->cap_bytes[m] < 0 || (m == 0 && pl->cap_bytes[m] != 0)) return OR_ERR_ARG;
+        if (pl->cap_bytes[m] > 0) bounded = 1;
+    }
+    if (bounded && pl->select >= 2) return OR_ERR_ARG;
     or_dag d;
     int rc = make_dag(n, b, code, code_len, cap_t, &d);
     if (rc) return rc;
@@ -938,6 +1023,8 @@ int32_t or_simulate_side(const or_platform *pl, int32_t n, int64_t b, const int8
     int32_t *fifo = (int32_t *)malloc(sizeof(int32_t) * (size_t)(T + 1)); /* FCFS queue */
     uint8_t *valid = (uint8_t *)calloc((size_t)(natoms * M), 1);
     int64_t *vfrom = (int64_t *)calloc((size_t)(natoms * M), sizeof(int64_t));
+    int64_t *use = (int64_t *)malloc(sizeof(int64_t) * (size_t)(natoms * M));
+    uint8_t *wbm = (uint8_t *)calloc((size_t)natoms, 1);
     int64_t maxatoms = 0;
     for (int32_t j = 0; j < T; j++) {
         int64_t s = d.t[j].bs / g.a;
@@ -951,7 +1038,7 @@ int32_t or_simulate_side(const or_platform *pl, int32_t n, int64_t b, const int8
     or_stats s;
     memset(&s, 0, sizeof s);
     if (!succ_off || !succ || !fill || !pending || !finish || !state || !released || !valid || !vfrom || !ax ||
-        !axw || !src || !inflight || !fifo) {
+        !axw || !src || !inflight || !fifo || !use || !wbm) {
         rc = OR_ERR_CAPACITY;
         goto out;
     }
@@ -969,6 +1056,7 @@ int32_t or_simulate_side(const or_platform *pl, int32_t n, int64_t b, const int8
         valid[x * M + 0] = 1;
         vfrom[x * M + 0] = 0;
     }
+    for (int64_t x = 0; x < natoms * M; x++) use[x] = -1;
     for (int p = 0; p < P; p++) avail[p] = 0;
     memset(mem_used, 0, sizeof mem_used);
     for (int p = 0; p < P; p++) mem_used[pl->proc_mem[p]] = 1;
@@ -993,6 +1081,13 @@ int32_t or_simulate_side(const or_platform *pl, int32_t n, int64_t b, const int8
     S.order_out = order_out;
     S.issue_out = issue_out;
     S.n_sched = 0;
+    S.use = use;
+    S.wb = wbm;
+    for (int m = 0; m < OR_MAX_MEMS; m++) {
+        int64_t ab = g.a * g.a * pl->bytes_per_elem;
+        S.bounded[m] = m < M && pl->cap_bytes[m] > 0;
+        S.cap_atoms[m] = S.bounded[m] ? pl->cap_bytes[m] / ab : 0;
+    }
     const int waits = pl->select >= 2; /* F-P, R-P: idle processors only */
     int32_t n_done = 0;
     if (pl->order == 1) {
@@ -1108,6 +1203,8 @@ out:
     free(fifo);
     free(valid);
     free(vfrom);
+    free(use);
+    free(wbm);
     free(ax);
     free(axw);
     free(src);
