@@ -154,6 +154,27 @@ int hesp_platform_set_cache(hesp_platform *p, int32_t cache);
  * carry any number of messages at once (no contention).  ERR_ARG for src ==
  * dst, a memory out of range, latency < 0 or bandwidth < 1. */
 int hesp_platform_set_link(hesp_platform *p, int32_t src, int32_t dst, int64_t latency_ns, int64_t bw_bytes_per_ns);
+
+/* Finite memory spaces (Sec. 2: a platform of "finite-size memory spaces";
+ * the paper gives no eviction policy, so this is a reading).  Memory `mem`
+ * (an accelerator memory, 1 .. n_mem - 1; host memory is unbounded) holds at
+ * most `bytes` bytes of data, counted in whole atoms (the blocks of side
+ * b / 2^L of a candidate whose deepest split level is L); 0 = unbounded (the
+ * default).  When task j is scheduled at time t, a finite memory m can take
+ * it when the atoms j lacks in m fit in m's free space plus the atoms m may
+ * evict -- valid in m, not used by j, and not used by a task in flight on a
+ * processor of m (the latest finish of a task that used the atom there is
+ * <= t); processors of memories that cannot take j are not candidates, and
+ * a task no memory can take gives its candidate HESP_ERR_CAPACITY.  On the
+ * chosen memory, atoms are evicted least recently used first (that latest
+ * finish, ties to the lower atom index) until j's atoms fit; evicted atoms
+ * valid in no other memory are written back to host memory, in one message
+ * issued at t, and are valid there from its arrival.  Supported with EFT-P
+ * and EIT-P (hesp_simulate_batch returns HESP_ERR_ARG under F-P / R-P) and
+ * dyadic partitions (hesp_simulate_factors returns HESP_ERR_UNSUPPORTED);
+ * every task order and caching policy.  Returns HESP_ERR_ARG for a bad
+ * memory or a negative size. */
+int hesp_platform_set_capacity(hesp_platform *p, int32_t mem, int64_t bytes);
 /* Host queries of the models, as used by the simulator. */
 int hesp_platform_exec_ns(const hesp_platform *p, int32_t op, int32_t type, int64_t block, int64_t *ns_out);
 int hesp_platform_xfer_ns(const hesp_platform *p, int64_t elems, int64_t *ns_out);

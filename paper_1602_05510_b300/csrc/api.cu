@@ -61,6 +61,7 @@ Arena arena_offsets(Arena a, int32_t n_mem) {
     a.off_hist = o; o = align256(o + 4 * 256);  // radix histogram of the priority-list sort
     a.off_pend0 = o; o = align256(o + 2 * a.Tcap);  // keep / reuse: the DAG's initial pending counts
     a.off_hdr = o; o = align256(o + 64);            // keep / reuse: the candidate's header
+    a.off_use = o; o = align256(o + 8 * a.Acap * mp);  // finite memories: last use per atom and memory
     a.slot_bytes = o;
     return a;
 }
@@ -116,6 +117,8 @@ static DevPlatform dev_platform(const hesp_platform *p) {
     d.rp_seed = p->rp_seed;
     d.cache = p->cache;
     d.use_links = p->use_links;
+    d.use_cap = p->use_cap;
+    for (int m = 0; m < HESP_MAX_MEMS; ++m) d.cap_bytes[m] = p->cap_bytes[m];
     for (int s = 0; s < HESP_MAX_MEMS; ++s)
         for (int t = 0; t < HESP_MAX_MEMS; ++t) {
             d.link_lat[s * HESP_MAX_MEMS + t] = p->use_links ? p->link_lat[s][t] : p->xfer_latency_ns;
@@ -294,6 +297,15 @@ int hesp_platform_set_link(hesp_platform *p, int32_t src, int32_t dst, int64_t l
     return HESP_OK;
 }
 
+int hesp_platform_set_capacity(hesp_platform *p, int32_t mem, int64_t bytes) {
+    if (!p || mem < 1 || mem >= p->n_mem || bytes < 0) return HESP_ERR_ARG;
+    p->cap_bytes[mem] = bytes;
+    p->use_cap = 0;
+    for (int m = 1; m < p->n_mem; ++m)
+        if (p->cap_bytes[m] > 0) p->use_cap = 1;
+    return HESP_OK;
+}
+
 int hesp_platform_set_cache(hesp_platform *p, int32_t cache) {
     if (!p || cache < HESP_CACHE_WB || cache > HESP_CACHE_WA) return HESP_ERR_ARG;
     p->cache = cache;
@@ -445,6 +457,7 @@ int simulate_common(const hesp_platform *p, const hesp_cand *cands, const int8_t
     if (any_s && !all_s) return HESP_ERR_ARG;
     if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_level < 0 || max_level > HESP_MAX_LEVEL)
         return HESP_ERR_UNSUPPORTED;
+    if (p->use_cap && p->select >= HESP_SELECT_FP) return HESP_ERR_ARG;  // finite memories: EFT-P / EIT-P
     const Arena ar = make_arena(max_tiles, max_level, p->n_mem, task_cap);
     if ((int64_t)ws_bytes < kWsHeaderBytes + ar.slot_bytes) return HESP_ERR_ARG;
     int64_t resident = 0;
@@ -480,6 +493,7 @@ int simulate_kept(const hesp_platform *p, const hesp_cand *cands, const int8_t *
     if (((uintptr_t)ws & 255) != 0) return HESP_ERR_ARG;
     if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_level < 0 || max_level > HESP_MAX_LEVEL)
         return HESP_ERR_UNSUPPORTED;
+    if (p->use_cap && p->select >= HESP_SELECT_FP) return HESP_ERR_ARG;  // finite memories: EFT-P / EIT-P
     const Arena ar = make_arena(max_tiles, max_level, HESP_MAX_MEMS, task_cap);
     if ((int64_t)ws_bytes < kWsHeaderBytes || ((int64_t)ws_bytes - kWsHeaderBytes) / ar.slot_bytes < n_cand)
         return HESP_ERR_ARG;
@@ -526,6 +540,7 @@ int hesp_simulate_factors(const hesp_platform *p, const hesp_cand *cands, const 
     if (!p || n_cand < 0 || task_cap < 0) return HESP_ERR_ARG;
     if (n_cand == 0) return HESP_OK;
     if (!cands || !factors || !makespan || !status || !ws || b < 1) return HESP_ERR_ARG;
+    if (p->use_cap) return HESP_ERR_UNSUPPORTED;  // finite memories: dyadic partitions only
     if (((uintptr_t)ws & 255) != 0) return HESP_ERR_ARG;
     const bool any_s = sched_off || sproc || sstart || sfinish;
     const bool all_s = sched_off && sproc && sstart && sfinish;

@@ -29,6 +29,9 @@ struct hesp_platform {
     // link_lat[s][d] + ceil(bytes / link_bw[s][d]) ns
     int32_t use_links;
     int64_t link_lat[HESP_MAX_MEMS][HESP_MAX_MEMS], link_bw[HESP_MAX_MEMS][HESP_MAX_MEMS];
+    // finite accelerator memories: capacity in bytes per memory (0 = unbounded)
+    int32_t use_cap;
+    int64_t cap_bytes[HESP_MAX_MEMS];
 };
 
 struct hesp_dag {
@@ -65,6 +68,8 @@ struct DevPlatform {
     uint64_t rp_seed;       // R-P: seed of the per-task draws
     int32_t cache, use_links;  // caching policy (0 WB, 1 WT, 2 WA); per-link transfer costs
     int64_t link_lat[HESP_MAX_MEMS * HESP_MAX_MEMS], link_bw[HESP_MAX_MEMS * HESP_MAX_MEMS];
+    int32_t use_cap, pad2;  // finite accelerator memories
+    int64_t cap_bytes[HESP_MAX_MEMS];
     int64_t exec[4 * HESP_MAX_TYPES * HESP_LB];
     int64_t wsum[4 * HESP_LB];  // task time summed over all processors, per (op, log2 block); -1 if any is -1
     int8_t proc_mem[HESP_MAX_PROCS];
@@ -85,7 +90,7 @@ struct Arena {
     // link area and the per-task marks in the successor offsets: neither is
     // in use at the same time as what it shares memory with.
     int64_t off_desc, off_pending, off_link, off_next, off_succoff, off_succ, off_epred, off_esucc, off_lw,
-        off_vfrom, off_bitmap, off_xt, off_hist, off_pend0, off_hdr;
+        off_vfrom, off_bitmap, off_xt, off_hist, off_pend0, off_hdr, off_use;
 };
 
 // Header at the start of the workspace.

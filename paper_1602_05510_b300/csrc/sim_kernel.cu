@@ -85,6 +85,22 @@ __device__ __forceinline__ uint32_t atom_index(int R, int C, int Lc, int n) {
     return (tile << (2 * Lc)) | z;
 }
 
+// Row-major position in the matrix (atom row * atoms per side + atom
+// column) of dyadic atom x: the order finite memories break LRU ties in.
+__device__ uint32_t rowmajor_of(uint32_t x, int Lc, int n) {
+    const uint32_t tile = x >> (2 * Lc), z = x & ((1u << (2 * Lc)) - 1u);
+    uint32_t r = 0, c = 0;
+    for (int k = 0; k < Lc; ++k) {
+        c |= ((z >> (2 * k)) & 1u) << k;
+        r |= ((z >> (2 * k + 1)) & 1u) << k;
+    }
+    int I = 0;
+    while (I + 1 < n && (uint32_t)((I + 1) * n - ((I + 1) * I) / 2) <= tile) ++I;
+    const int J = (int)(tile - (uint32_t)(I * n - (I * (I - 1)) / 2)) + I;
+    const uint32_t side = (uint32_t)n << Lc;
+    return (((uint32_t)I << Lc) + r) * side + ((uint32_t)J << Lc) + c;
+}
+
 // Decode base task t of the Fig. 1 loop on n tiles.
 __device__ void decode_base(int n, int64_t t, int &op, int &K, int &I, int &J) {
     int k = 0;
@@ -429,10 +445,11 @@ struct AtomState {
         return src;
     }
     // the source of a fetch at t: the lowest memory with a copy usable at t,
-    // else (write-through / write-around only) the copy usable first
-    __device__ __forceinline__ int fetch_source(int64_t t, int cache) const {
+    // else (when copies may be in flight to their only holder: write-through,
+    // write-around, write-backs of evictions) the copy usable first
+    __device__ __forceinline__ int fetch_source(int64_t t, bool fallback) const {
         const int s = source(t);
-        return (s < 0 && cache != HESP_CACHE_WB) ? earliest() : s;
+        return (s < 0 && fallback) ? earliest() : s;
     }
 };
 
@@ -462,18 +479,31 @@ struct Counts {
     }
 };
 
+// Finite accelerator memories of one candidate (Sec. 2 "finite-size memory
+// spaces"; the eviction rule is a reading, the paper gives none): bit m of
+// `bounded` marks a finite memory that holds processors, cap[m] its
+// capacity in atoms; use[x * MP + m] (arena) = the latest finish of a task
+// that used atom x on a processor of memory m (-1: none).
+struct CapState {
+    unsigned bounded;
+    int nA;  // atoms of the candidate
+    int64_t cap[HESP_MAX_MEMS];
+};
+
 // Schedule task j (descriptor d) at time t: data-ready time per memory, the processor
 // choice `sel` (ties to the lowest id), commit of the coherence state (the
 // caching policy `cache`), append to the chosen processor's FIFO.  Under
 // F-P / R-P the caller guarantees a processor idle at t.  Clears `ok` on an
-// internal inconsistency.
+// internal inconsistency; sets `capfail` when no memory can take the task
+// (finite memories, cs.bounded != 0: dyadic partitions, EFT-P / EIT-P).
 template <int M, int NS, bool FIFO, bool REC>
 __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, char *base, const KArgs &a, int Lc, int lb_b,
                                                  int fL, int lane, const int64_t *s_exec, const int8_t *s_pmem,
                                                  const int8_t *s_ptype, const int pm[NS], const int pt[NS],
                                                  const bool pv[NS], int64_t avail[NS], int head[NS], int tail[NS],
                                                  int64_t hfin[NS], int64_t &mk, bool &ok, int64_t sched_base,
-                                                 int sel, uint64_t rp_seed, int cache, bool links) {
+                                                 int sel, uint64_t rp_seed, int cache, bool links, const CapState &cs,
+                                                 bool &capfail) {
     const int op = (int)(d & 3);
     const int lvl = (int)((d >> 2) & 7);
     const int nr = nreg_of(op);
@@ -491,6 +521,11 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
     auto xtab = [&](int s, int d) -> const int64_t * {
         return links ? xt + (int64_t)(s * HESP_MAX_MEMS + d) * a.ar.Kcap : xt;
     };
+    // finite memories in use; then, as under WT / WA, a copy may be valid
+    // only in flight (a write-back), so a message departs when the last of
+    // its data is usable at the source
+    const bool capped = REC && M > 1 && cs.bounded != 0;
+    const bool fb = cache != HESP_CACHE_WB || capped;
 
     int64_t drt_off[M];
     Counts<M> cnt;
@@ -522,9 +557,9 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
                 const uint32_t x = task_atom(d, i, sh, wf, fL, fm, rr);
                 AtomState<M> st;
                 st.load(vfrom + (int64_t)x * MP);
-                const int src = st.fetch_source(t, cache);
+                const int src = st.fetch_source(t, fb);
                 Lead slead = 0;  // lead of the source copy over t
-                if (cache != HESP_CACHE_WB && src >= 0) {
+                if (fb && src >= 0) {
 #pragma unroll
                     for (int q = 0; q < M; ++q)
                         if (q == src && st.v[q] > t) {
@@ -548,7 +583,7 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
                     } else {
                         ok &= src >= 0;
                         cnt.add(m, src);
-                        if (cache != HESP_CACHE_WB) {
+                        if (fb) {
 #pragma unroll
                             for (int q = 0; q < M; ++q)
                                 if (q == src) dlead[m][q] = max(dlead[m][q], slead);
@@ -559,7 +594,7 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
         }
 #pragma unroll
         for (int k = 0; k < Counts<M>::NW; ++k) cnt.w[k] = __reduce_add_sync(FULL, cnt.w[k]);
-        if (cache != HESP_CACHE_WB) {
+        if (fb) {
 #pragma unroll
             for (int m = 0; m < M; ++m)
 #pragma unroll
@@ -576,9 +611,45 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
             for (int s = 0; s < M; ++s) {
                 if (s == m) continue;
                 const unsigned c = cnt.get(m, s);
-                if (c > 0) off = max(off, (cache != HESP_CACHE_WB ? (int64_t)dlead[m][s] : 0) + xtab(s, m)[c]);
+                if (c > 0) off = max(off, (fb ? (int64_t)dlead[m][s] : 0) + xtab(s, m)[c]);
             }
             drt_off[m] = off;
+        }
+    }
+    // Finite memories: memory m can take j when the atoms j lacks there fit
+    // in its free space plus the atoms it may evict (valid there, not used by
+    // j, no task in flight there still using them: use <= t).
+    int64_t *const use = at<int64_t>(base, a.ar.off_use);
+    unsigned feas = ~0u;  // bit m: memory m can take j
+    int64_t need[M], room[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) need[m] = room[m] = 0;
+    auto in_task = [&](uint32_t x) -> bool {
+        bool in = false;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            if (r < nr && x - desc_atom(d, r) < (uint32_t)na) in = true;
+        return in;
+    };
+    if (capped) {
+#pragma unroll
+        for (int m = 1; m < M; ++m) {
+            if (!((cs.bounded >> m) & 1u)) continue;
+            unsigned nd = 0;
+#pragma unroll
+            for (int s = 0; s < M; ++s)
+                if (s != m) nd += cnt.get(m, s);
+            need[m] = nd;
+            unsigned occ = 0, evictable = 0;
+            for (int x = lane; x < cs.nA; x += 32) {
+                if (vfrom[(int64_t)x * MP + m] < 0) continue;
+                ++occ;
+                if (use[(int64_t)x * MP + m] <= t && !in_task((uint32_t)x)) ++evictable;
+            }
+            occ = __reduce_add_sync(FULL, occ);
+            evictable = __reduce_add_sync(FULL, evictable);
+            room[m] = cs.cap[m] - (int64_t)occ;
+            if (need[m] > room[m] + (int64_t)evictable) feas &= ~(1u << m);
         }
     }
     // Processor choice, key = value << 6 | proc (ties to the lowest id):
@@ -605,7 +676,7 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         emine[s] = 0;
-        const bool cand = pv[s] && (sel < HESP_SELECT_FP || avail[s] <= t);
+        const bool cand = pv[s] && (sel < HESP_SELECT_FP || avail[s] <= t) && ((feas >> pm[s]) & 1u);
         if (cand) {
             const int64_t ex = s_exec[(op * HESP_MAX_TYPES + pt[s]) * HESP_LB + lb];
             int64_t ready = max(t, avail[s]);
@@ -631,6 +702,10 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
     key = warp_min_u64(key);
     const bool none = sel >= HESP_SELECT_FP && key == ~0ull;  // no idle processor: the caller's error
     ok &= !none;
+    if (capped && key == ~0ull) {  // no memory can take j
+        capfail = true;
+        key = 0;
+    }
     const int pbest = none ? 0 : (int)(key & 63);
     int64_t eft = (int64_t)(key >> 6);
     if (sel != HESP_SELECT_EFT) {
@@ -642,6 +717,58 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
     }
     const int ms = s_pmem[pbest];
 
+    // Eviction from a finite memory: the least recently used evictable atom
+    // (smallest use, ties to the lower atom) until j's missing atoms fit; an
+    // evicted atom valid in no other memory goes back to host memory, all
+    // in one message issued at t (marked -2 until its arrival is known).
+    if (capped && !capfail && ((cs.bounded >> ms) & 1u) && need[ms] > room[ms]) {
+        const int64_t k = need[ms] - room[ms];
+        for (int64_t q = 0; q < k; ++q) {
+            uint64_t best = ~0ull;
+            for (int x = lane; x < cs.nA; x += 32) {
+                if (vfrom[(int64_t)x * MP + ms] < 0) continue;
+                const int64_t u = use[(int64_t)x * MP + ms];
+                if (u <= t && !in_task((uint32_t)x)) best = min(best, (uint64_t)u);
+            }
+            best = warp_min_u64(best);
+            if (best == ~0ull) {
+                ok = false;
+                break;
+            }
+            const int32_t *const rmk = at<int32_t>(base, a.ar.off_lw);
+            int vk = INT_MAX;  // lowest row-major key among the tied atoms
+            for (int x = lane; x < cs.nA; x += 32) {
+                if (vfrom[(int64_t)x * MP + ms] < 0) continue;
+                if ((uint64_t)use[(int64_t)x * MP + ms] == best && !in_task((uint32_t)x)) vk = min(vk, rmk[x]);
+            }
+            vk = __reduce_min_sync(FULL, vk);
+            int vx = INT_MAX;
+            for (int x = lane; x < cs.nA; x += 32)
+                if (rmk[x] == vk) vx = x;
+            vx = __reduce_min_sync(FULL, vx);
+            if (lane == 0) {
+                int64_t *pv2 = vfrom + (int64_t)vx * MP;
+                bool elsewhere = false;
+#pragma unroll
+                for (int m = 0; m < M; ++m)
+                    if (m != ms && pv2[m] >= 0) elsewhere = true;
+                pv2[ms] = -1;
+                if (!elsewhere) pv2[0] = -2;
+            }
+            __syncwarp();
+        }
+        // write-backs: the atoms marked -2 in host memory
+        unsigned nw = 0;
+        for (int x = lane; x < cs.nA; x += 32) nw += vfrom[(int64_t)x * MP] == -2;
+        const int n_wb = (int)__reduce_add_sync(FULL, nw);
+        if (n_wb > 0) {
+            const int64_t arrive = t + xtab(ms, 0)[n_wb];
+            for (int x = lane; x < cs.nA; x += 32)
+                if (vfrom[(int64_t)x * MP] == -2) vfrom[(int64_t)x * MP] = arrive;
+        }
+        __syncwarp();
+    }
+
     if (M > 1) {
         for (int i0 = 0; i0 < tot; i0 += 32) {
             const int i = i0 + lane;
@@ -649,6 +776,10 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
                 int r;
                 const uint32_t x = task_atom(d, i, sh, wf, fL, fm, r);
                 int64_t *px = vfrom + (int64_t)x * MP;
+                if (capped) {
+                    int64_t *pu = use + (int64_t)x * MP + ms;
+                    if (*pu < eft) *pu = eft;
+                }
                 if (r == nr - 1) {
                     // written block, every other copy invalidated: WB valid in
                     // the chosen memory from the finish; WT also in host memory
@@ -675,7 +806,7 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
                         if (m == ms) vm = st.v[m];
                     if (vm < 0) {
                         // fetched: valid in the chosen memory from its message's arrival
-                        const int src = st.fetch_source(t, cache);
+                        const int src = st.fetch_source(t, fb);
                         unsigned c = 0;
                         int64_t lead = 0;
 #pragma unroll
@@ -1066,6 +1197,32 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     }
                 }
             }
+            // finite accelerator memories (general instantiation, dyadic partitions)
+            CapState cs;
+            cs.bounded = 0;
+            cs.nA = (int)A;
+            bool capfail = false;
+            if (GEN && M > 1 && pl.use_cap && !fm) {
+                unsigned mm = 0;  // memories holding processors
+#pragma unroll
+                for (int s = 0; s < NS; ++s)
+                    if (pv[s]) mm |= 1u << pm[s];
+                mm = __reduce_or_sync(FULL, mm);
+                const int64_t as = (int64_t)(b >> Lc);
+                const int64_t abytes = as * as * pl.bpe;
+#pragma unroll
+                for (int m = 0; m < HESP_MAX_MEMS; ++m) {
+                    cs.cap[m] = m < M && pl.cap_bytes[m] > 0 ? pl.cap_bytes[m] / abytes : 0;
+                    if (m > 0 && m < M && pl.cap_bytes[m] > 0 && ((mm >> m) & 1u)) cs.bounded |= 1u << m;
+                }
+                int64_t *const use = at<int64_t>(base, a.ar.off_use);
+                for (int64_t x = lane; x < A * MP; x += 32) use[x] = -1;
+                // LRU ties go to the lower row-major atom; the keys live in
+                // the last-writer area, free after the dependence phase
+                int32_t *const rmk = at<int32_t>(base, a.ar.off_lw);
+                for (int64_t x = lane; x < A; x += 32) rmk[x] = (int32_t)rowmajor_of((uint32_t)x, Lc, n);
+                __syncwarp();
+            }
             // GEN = false: the FCFS + EFT-P + write-back instantiation; GEN =
             // true: every policy, chosen at run time from the platform.
             const int sel = GEN ? pl.select : HESP_SELECT_EFT;
@@ -1173,7 +1330,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     }
                     const int64_t fj = schedule_task<M, NS, false, GEN>(j, desc[j], tj, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem,
                                                                    s_ptype, pm, pt, pv, avail, head, tail, hfin, mk,
-                                                                   ok, sched_base, sel, rp_seed, cache, links);
+                                                                   ok, sched_base, sel, rp_seed, cache, links, cs, capfail);
                     const int e0 = succoff[j], e1 = succoff[j + 1];
                     for (int e = e0 + lane; e < e1; e += 32) {
                         const int sj = succ[e];
@@ -1182,6 +1339,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     __syncwarp();
                 }
                 if (!__all_sync(FULL, ok && okp)) status = HESP_ERR_STATE;
+                if (capfail) status = HESP_ERR_CAPACITY;
             } else {
             const int W = (int)((T + 31) >> 5);
             int wlo = INT_MAX, whi = -1;
@@ -1240,7 +1398,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                             continue;
                         }
                         schedule_task<M, NS, true, GEN>(j, dsc, t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
-                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache, links);
+                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache, links, cs, capfail);
                         ++scheduled;
                     }
                     direct = false;
@@ -1268,7 +1426,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                                 }
                                 schedule_task<M, NS, true, GEN>(jb + bit, desc[jb + bit], t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype,
                                                            pm, pt, pv, avail, head, tail, hfin, mk, ok, sched_base,
-                                                           sel, rp_seed, cache, links);
+                                                           sel, rp_seed, cache, links, cs, capfail);
                                 ++scheduled;
                             }
                         }
@@ -1287,7 +1445,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                         const int j = link[qh].rq;
                         ++qh;
                         schedule_task<M, NS, true, GEN>(j, desc[j], t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
-                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache, links);
+                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache, links, cs, capfail);
                         ++scheduled;
                     }
                 }
@@ -1362,6 +1520,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
             }
             if (!__all_sync(FULL, ok)) status = HESP_ERR_STATE;
             if (status == HESP_OK && scheduled != T) status = HESP_ERR_STATE;
+            if (capfail) status = HESP_ERR_CAPACITY;
             }
         }
 
@@ -1605,7 +1764,7 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
     const bool two = p->n_procs > 32;
     const unsigned ub = (unsigned)blocks;
     const bool gen = p->order != HESP_ORDER_FCFS || p->select != HESP_SELECT_EFT || p->cache != HESP_CACHE_WB ||
-                     p->use_links || crit != nullptr || fmode != 0;
+                     p->use_links || crit != nullptr || fmode != 0 || p->use_cap;
     switch (p->n_mem) {
     case 1: two ? launch_one<1, 2>(gen, ub, threads, smem, stream, dp, a, ctr)
                 : launch_one<1, 1>(gen, ub, threads, smem, stream, dp, a, ctr); break;

@@ -40,7 +40,7 @@ EXPORTS = (
     "hesp_graph_launch", "hesp_graph_destroy", "hesp_platform_set_tuning", "hesp_platform_get_tuning",
     "hesp_sim_autotune", "hesp_sort_cands_workspace_size", "hesp_sort_cands_by_size", "hesp_platform_set_policy",
     "hesp_simulate_critical", "hesp_solver_moves", "hesp_solver_pick", "hesp_schedule_metrics",
-    "hesp_sim_workspace_size_factors", "hesp_simulate_factors",
+    "hesp_sim_workspace_size_factors", "hesp_simulate_factors", "hesp_platform_set_capacity",
     "hesp_sim_workspace_size_kept", "hesp_simulate_batch_keep", "hesp_simulate_batch_reuse",
     "hesp_platform_set_cache", "hesp_surrogate_save", "hesp_surrogate_load", "hesp_platform_set_link",
     "hesp_dag_build_kept",
@@ -106,6 +106,7 @@ def lib():
         L.hesp_simulate_batch.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         L.hesp_simulate_batch_noalloc.argtypes = [vp, vp, vp, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.hesp_simulate_critical.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, sz, vp]
+        L.hesp_platform_set_capacity.argtypes = [vp, i32, i64]
         L.hesp_sim_workspace_size_factors.argtypes = [vp, i32, i32, i64, i64, ctypes.POINTER(sz)]
         L.hesp_simulate_factors.argtypes = [vp, vp, vp, i64, i32, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, sz,
                                             vp]
@@ -182,9 +183,11 @@ def _stream(stream):
 
 class Platform:
     """A simulated platform (hesp_platform handle) built from a
-    ``workloads.PlatformSpec``."""
+    ``workloads.PlatformSpec``, with its task order, processor selection,
+    R-P seed, caching policy, optional per-link costs {(src, dst):
+    (latency_ns, bytes_per_ns)} and optional finite memories {mem: bytes}."""
 
-    def __init__(self, spec, order=0, select=0, rp_seed=0, cache=0, links=None):
+    def __init__(self, spec, order=0, select=0, rp_seed=0, cache=0, links=None, capacity=None):
         self.spec = spec
         L = lib()
         types = (_PType * len(spec.types))()
@@ -206,6 +209,8 @@ class Platform:
         check(L.hesp_platform_set_cache(h, cache), "hesp_platform_set_cache")
         for (s_, d_), (lat, bw) in sorted((links or {}).items()):
             check(L.hesp_platform_set_link(h, s_, d_, lat, bw), "hesp_platform_set_link")
+        for m, nbytes in sorted((capacity or {}).items()):
+            check(L.hesp_platform_set_capacity(h, m, nbytes), "hesp_platform_set_capacity")
 
     @property
     def n_mem(self):
