@@ -309,8 +309,8 @@ def run_gpu(args):
 # for the kernel source they were taken on: DRAM bytes per 4,096 candidates on the
 # CPU+GPU platform (scaled to a launch by candidates; traffic grows in proportion)
 # and the share of issue slots busy.
-SIM_NCU = {"source_sha1_12": "fd7ba30af648", "dram_bytes_per_4096": 1.360899e9 + 1.227563e9,
-           "issue_active_pct": 60.41, "warps_per_sm": 25.7, "alu_pipe_pct": 50.3}
+SIM_NCU = {"source_sha1_12": "474a8c57dc3c", "dram_bytes_per_4096": 0.531109e9 + 0.327541e9,
+           "issue_active_pct": 62.76, "warps_per_sm": 25.4, "alu_pipe_pct": 56.1}
 
 
 def sim_source_matches():
@@ -323,8 +323,10 @@ def sim_source_matches():
 
 
 def roofline(plats, t_kern, K, task_events_rank, clk, peaks):
-    """Dominant kernel: the simulation kernel on the CPU+GPU platform.  It is
-    bound by integer/control issue, not by HBM or tensor cores; `achieved`
+    """Dominant kernel: the simulation kernel on the CPU+GPU platform (the
+    event loop with coherence, from the DAGs the build launch kept; 54 % of a
+    step).  It is bound by integer/control issue, not by HBM or tensor cores;
+    `achieved`
     counts the algorithmic int64 operations of the simulation per task-event
     (EFT evaluation 4 P, data-ready times M A_j, coherence commit A_j) and the
     peak is the SM integer issue rate at the maximum SM clock (148 SMs x 128
@@ -338,7 +340,7 @@ def roofline(plats, t_kern, K, task_events_rank, clk, peaks):
     achieved = alg * ev_a / t / 1e12 if t > 0 and alg else None
     fresh = sim_source_matches()
     C = N_CAND
-    return {"bound": "alu", "kernel": "sim_kernel<M=2> (cpu12_gpu1)", "achieved": achieved, "peak": peak,
+    return {"bound": "alu", "kernel": "sim_kernel<M=2> reuse (cpu12_gpu1)", "achieved": achieved, "peak": peak,
             "unit": "T int64-op/s", "frac": achieved / peak if achieved else None,
             "peak_source": "derived: 148 SMs x 128 INT32 lanes x %.0f MHz / 2 (sm_max_mhz of MEASURED_PEAKS)" % sm_max,
             "kernel_ms": 1e3 * t,
@@ -625,6 +627,51 @@ def run_factors(args):
     print(json.dumps(line))
 
 
+def run_capacity(args):
+    """Finite accelerator memories: the default workload's 65,536 candidates
+    (8 x 8 tiles, b = 2048, levels {0, 1, 2}) on 12 CPU + 1 GPU-type
+    processor whose memory holds 256 MB (8 tiles of the 64 the matrix
+    needs): LRU eviction with write-back, simulated exactly."""
+    import torch
+
+    from paper_1602_05510_b300 import build, hesp
+
+    build.build()
+    C = args.candidates
+    nb = W.base_count(N_TILES)
+    plat = hesp.Platform(W.PLATFORMS["cfg1a"], capacity={1: 256 << 20})
+    cands = torch.empty(C * 16, dtype=torch.uint8, device="cuda")
+    levels = torch.empty(C * nb, dtype=torch.int8, device="cuda")
+    hesp.generate_candidates(hesp.GEN_UNIFORM, WORKLOAD.seed, 0, C, N_TILES, B, N_LEVELS, levels, cands)
+    ws = hesp.alloc_workspace(plat, N_TILES, MAX_LEVEL, C)
+    ms = torch.empty(C, dtype=torch.int64, device="cuda")
+    st = torch.empty(C, dtype=torch.int32, device="cuda")
+    nt = torch.empty(C, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        hesp.simulate_batch(plat, cands, levels, C, N_TILES, MAX_LEVEL, ws, makespan=ms, status=st, ntasks=nt)
+    torch.cuda.synchronize()
+    t = 0.0
+    for it in range(args.steps):
+        flush.fill_(it & 255)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        hesp.simulate_batch(plat, cands, levels, C, N_TILES, MAX_LEVEL, ws, makespan=ms, status=st, ntasks=nt)
+        e.record()
+        torch.cuda.synchronize()
+        t += a.elapsed_time(e) / 1e3
+    events = int(nt.sum().item())
+    line = {"metric": METRIC, "value": events * args.steps / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "int64", "data": "synthetic",
+            "workload": "finite GPU memory: N=16384 Cholesky, b=2048 (8x8 tiles), levels uniform {0,1,2}, "
+                        "%d candidates on 12 CPU + 1 GPU-type with 256 MB of GPU memory (LRU eviction, "
+                        "write-back)" % C,
+            "ms_per_step": 1e3 * t / args.steps, "all_ok": bool((st == 0).all().item()),
+            "task_events_per_step": events, "candidates_per_s": C * args.steps / t,
+            "mean_makespan_ns": float(ms.double().mean().item()), "l2": "256 MB buffer written between timed steps"}
+    print(json.dumps(line))
+
+
 def run_exhaustive(args):
     """The exhaustive search of the 3 x 3-tile problem (N = 3072, b = 1024):
     all 1,024 partitions (each base task split once or not), generated,
@@ -831,7 +878,7 @@ def main():
     ap.add_argument("--candidates", type=int, default=N_CAND,
                     help="candidates per step (default: the workload's 65,536; smaller only for profiling)")
     ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search", "uneven", "solver", "table1", "exhaustive",
-                             "factors"],
+                             "factors", "capacity"],
                     help="random: the default benchmark line; surrogate: label/train/rank/re-score "
                          "pipeline; search: surrogate-guided vs random search")
     ap.add_argument("--labels", type=int, default=1 << 20)
@@ -858,6 +905,8 @@ def main():
         return run_solver(args)
     if args.workload == "table1":
         return run_table1(args)
+    if args.workload == "capacity":
+        return run_capacity(args)
     if args.workload == "factors":
         return run_factors(args)
     if args.workload == "exhaustive":
