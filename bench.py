@@ -394,6 +394,22 @@ def cpu_baseline(sample):
                       "thread-chunk over %d host threads, %.1f s" % (sample, ev, cores, dt)}
 
 
+def cpu_baseline_each(sim_one, count, label):
+    """The oracle timed on the host cores over `count` candidates of a
+    general-path workload: sim_one(c) simulates candidate c and returns its
+    task count (ctypes releases the GIL, so Python threads run in parallel)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        ev = sum(ex.map(sim_one, range(count)))
+    dt = time.perf_counter() - t0
+    return {"value": ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d candidates of the same workload (%s, %d task-events) over %d host threads, %.1f s"
+                      % (count, label, ev, cores, dt)}
+
+
 # ---------------------------------------------------------- reference arm
 
 
@@ -624,6 +640,16 @@ def run_factors(args):
             "candidates_per_s": C * len(plats) * args.steps / t,
             "kernel_ms_per_step": {k: 1e3 * x / args.steps for k, x in zip(PLATS, t_k)},
             "l2": "256 MB buffer written between timed steps"}
+    if args.cpu_baseline:
+        import oracle as O
+
+        fh = W.uniform_factors(9, 0, 8192, nb, K)
+        pls = [O.make_platform(W.PLATFORMS[k]) for k in PLATS]
+
+        def one(c):
+            return sum(O.simulate_factors(pl, n, b, fh[c], schedule=False)["n_tasks"] for pl in pls)
+
+        line["cpu_baseline"] = cpu_baseline_each(one, 8192, "both platforms")
     print(json.dumps(line))
 
 
@@ -669,6 +695,16 @@ def run_capacity(args):
             "ms_per_step": 1e3 * t / args.steps, "all_ok": bool((st == 0).all().item()),
             "task_events_per_step": events, "candidates_per_s": C * args.steps / t,
             "mean_makespan_ns": float(ms.double().mean().item()), "l2": "256 MB buffer written between timed steps"}
+    if args.cpu_baseline:
+        import oracle as O
+
+        lh = W.workload_levels("cfg1", 0, 8192)
+        pl = O.make_platform(W.PLATFORMS["cfg1a"], capacity={1: 256 << 20})
+
+        def one(c):
+            return O.simulate(pl, N_TILES, B, lh[c], schedule=False)["n_tasks"]
+
+        line["cpu_baseline"] = cpu_baseline_each(one, 8192, "12 CPU + 1 GPU-type, 256 MB GPU memory")
     print(json.dumps(line))
 
 
