@@ -488,6 +488,7 @@ struct CapState {
     unsigned bounded;
     int nA;  // atoms of the candidate
     int64_t cap[HESP_MAX_MEMS];
+    int64_t occ[HESP_MAX_MEMS];  // atoms valid there now (kept exact at every commit)
 };
 
 // Schedule task j (descriptor d) at time t: data-ready time per memory, the processor
@@ -496,13 +497,13 @@ struct CapState {
 // F-P / R-P the caller guarantees a processor idle at t.  Clears `ok` on an
 // internal inconsistency; sets `capfail` when no memory can take the task
 // (finite memories, cs.bounded != 0: dyadic partitions, EFT-P / EIT-P).
-template <int M, int NS, bool FIFO, bool REC>
+template <int M, int NS, bool FIFO, bool REC, bool CAP>
 __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, char *base, const KArgs &a, int Lc, int lb_b,
                                                  int fL, int lane, const int64_t *s_exec, const int8_t *s_pmem,
                                                  const int8_t *s_ptype, const int pm[NS], const int pt[NS],
                                                  const bool pv[NS], int64_t avail[NS], int head[NS], int tail[NS],
                                                  int64_t hfin[NS], int64_t &mk, bool &ok, int64_t sched_base,
-                                                 int sel, uint64_t rp_seed, int cache, bool links, const CapState &cs,
+                                                 int sel, uint64_t rp_seed, int cache, bool links, CapState &cs,
                                                  bool &capfail) {
     const int op = (int)(d & 3);
     const int lvl = (int)((d >> 2) & 7);
@@ -524,7 +525,7 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
     // finite memories in use; then, as under WT / WA, a copy may be valid
     // only in flight (a write-back), so a message departs when the last of
     // its data is usable at the source
-    const bool capped = REC && M > 1 && cs.bounded != 0;
+    const bool capped = CAP && M > 1 && cs.bounded != 0;
     const bool fb = cache != HESP_CACHE_WB || capped;
 
     int64_t drt_off[M];
@@ -545,6 +546,10 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
     for (int m = 0; m < M; ++m)
 #pragma unroll
         for (int s = 0; s < M; ++s) dlead[m][s] = 0;
+    // finite memories: written atoms valid per memory before the commit
+    unsigned wvalid[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) wvalid[m] = 0;
     if (M > 1) {
         // latest lead of a valid copy per memory
         Lead amax[M];
@@ -557,6 +562,10 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
                 const uint32_t x = task_atom(d, i, sh, wf, fL, fm, rr);
                 AtomState<M> st;
                 st.load(vfrom + (int64_t)x * MP);
+                if (capped && rr == nr - 1) {
+#pragma unroll
+                    for (int m = 1; m < M; ++m) wvalid[m] += st.v[m] >= 0;
+                }
                 const int src = st.fetch_source(t, fb);
                 Lead slead = 0;  // lead of the source copy over t
                 if (fb && src >= 0) {
@@ -634,22 +643,25 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
     if (capped) {
 #pragma unroll
         for (int m = 1; m < M; ++m) {
+            wvalid[m] = __reduce_add_sync(FULL, wvalid[m]);
             if (!((cs.bounded >> m) & 1u)) continue;
             unsigned nd = 0;
 #pragma unroll
             for (int s = 0; s < M; ++s)
                 if (s != m) nd += cnt.get(m, s);
             need[m] = nd;
-            unsigned occ = 0, evictable = 0;
-            for (int x = lane; x < cs.nA; x += 32) {
-                if (vfrom[(int64_t)x * MP + m] < 0) continue;
-                ++occ;
-                if (use[(int64_t)x * MP + m] <= t && !in_task((uint32_t)x)) ++evictable;
+            room[m] = cs.cap[m] - cs.occ[m];
+            if (need[m] <= room[m]) continue;
+            // count evictable atoms until there are enough
+            const int64_t want = need[m] - room[m];
+            int64_t got = 0;
+            for (int x0 = 0; x0 < cs.nA && got < want; x0 += 32) {
+                const int x = x0 + lane;
+                const bool e = x < cs.nA && vfrom[(int64_t)x * MP + m] >= 0 &&
+                               use[(int64_t)x * MP + m] <= t && !in_task((uint32_t)x);
+                got += __popc(__ballot_sync(FULL, e));
             }
-            occ = __reduce_add_sync(FULL, occ);
-            evictable = __reduce_add_sync(FULL, evictable);
-            room[m] = cs.cap[m] - (int64_t)occ;
-            if (need[m] > room[m] + (int64_t)evictable) feas &= ~(1u << m);
+            if (got < want) feas &= ~(1u << m);
         }
     }
     // Processor choice, key = value << 6 | proc (ties to the lowest id):
@@ -723,29 +735,29 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
     // in one message issued at t (marked -2 until its arrival is known).
     if (capped && !capfail && ((cs.bounded >> ms) & 1u) && need[ms] > room[ms]) {
         const int64_t k = need[ms] - room[ms];
+        const int32_t *const rmk = at<int32_t>(base, a.ar.off_lw);
         for (int64_t q = 0; q < k; ++q) {
-            uint64_t best = ~0ull;
+            // one pass: each lane's least (use, row-major key), then the warp's
+            uint64_t bu = ~0ull;
+            int bk = INT_MAX, bx = INT_MAX;
             for (int x = lane; x < cs.nA; x += 32) {
                 if (vfrom[(int64_t)x * MP + ms] < 0) continue;
                 const int64_t u = use[(int64_t)x * MP + ms];
-                if (u <= t && !in_task((uint32_t)x)) best = min(best, (uint64_t)u);
+                if (u > t || in_task((uint32_t)x)) continue;
+                const int key = rmk[x];
+                if ((uint64_t)u < bu || ((uint64_t)u == bu && key < bk)) {
+                    bu = (uint64_t)u;
+                    bk = key;
+                    bx = x;
+                }
             }
-            best = warp_min_u64(best);
+            const uint64_t best = warp_min_u64(bu);
             if (best == ~0ull) {
                 ok = false;
                 break;
             }
-            const int32_t *const rmk = at<int32_t>(base, a.ar.off_lw);
-            int vk = INT_MAX;  // lowest row-major key among the tied atoms
-            for (int x = lane; x < cs.nA; x += 32) {
-                if (vfrom[(int64_t)x * MP + ms] < 0) continue;
-                if ((uint64_t)use[(int64_t)x * MP + ms] == best && !in_task((uint32_t)x)) vk = min(vk, rmk[x]);
-            }
-            vk = __reduce_min_sync(FULL, vk);
-            int vx = INT_MAX;
-            for (int x = lane; x < cs.nA; x += 32)
-                if (rmk[x] == vk) vx = x;
-            vx = __reduce_min_sync(FULL, vx);
+            const int vk = __reduce_min_sync(FULL, bu == best ? bk : INT_MAX);
+            const int vx = __reduce_min_sync(FULL, (bu == best && bk == vk) ? bx : INT_MAX);
             if (lane == 0) {
                 int64_t *pv2 = vfrom + (int64_t)vx * MP;
                 bool elsewhere = false;
@@ -757,6 +769,7 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
             }
             __syncwarp();
         }
+        cs.occ[ms] -= k;
         // write-backs: the atoms marked -2 in host memory
         unsigned nw = 0;
         for (int x = lane; x < cs.nA; x += 32) nw += vfrom[(int64_t)x * MP] == -2;
@@ -857,6 +870,17 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
         a.sstart[sched_base + j] = eft - s_exec[(op * HESP_MAX_TYPES + s_ptype[pbest]) * HESP_LB + lb];
         a.sfinish[sched_base + j] = eft;
     }
+    if (capped && !capfail) {
+        // occupancy after the commit: j's missing atoms arrived in ms; its
+        // written block left every other memory (and ms too under WA)
+        if ((cs.bounded >> ms) & 1u) {
+            cs.occ[ms] += need[ms];
+            if (cache == HESP_CACHE_WA && ms != 0) cs.occ[ms] -= na;
+        }
+#pragma unroll
+        for (int m = 1; m < M; ++m)
+            if (m != ms && ((cs.bounded >> m) & 1u)) cs.occ[m] -= wvalid[m];
+    }
     mk = max(mk, eft);
     __syncwarp();
     return eft;
@@ -864,7 +888,9 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
 
 // BUILD: expand and analyse each candidate's DAG and keep it (a keep launch
 // without the simulation; platform independent, so one instantiation).
-template <int M, int NS, bool GEN, bool BUILD = false>
+// CAP: the general instantiation with finite memories (kept apart so that
+// the other general launches carry none of its registers).
+template <int M, int NS, bool GEN, bool BUILD = false, bool CAP = false>
 __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl, KArgs a,
                                                                  unsigned long long *work_counter) {
     __shared__ int64_t s_exec[4 * HESP_MAX_TYPES * HESP_LB];
@@ -1202,7 +1228,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
             cs.bounded = 0;
             cs.nA = (int)A;
             bool capfail = false;
-            if (GEN && M > 1 && pl.use_cap && !fm) {
+            if (CAP && M > 1 && pl.use_cap && !fm) {
                 unsigned mm = 0;  // memories holding processors
 #pragma unroll
                 for (int s = 0; s < NS; ++s)
@@ -1212,6 +1238,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                 const int64_t abytes = as * as * pl.bpe;
 #pragma unroll
                 for (int m = 0; m < HESP_MAX_MEMS; ++m) {
+                    cs.occ[m] = 0;  // every atom starts in host memory only
                     cs.cap[m] = m < M && pl.cap_bytes[m] > 0 ? pl.cap_bytes[m] / abytes : 0;
                     if (m > 0 && m < M && pl.cap_bytes[m] > 0 && ((mm >> m) & 1u)) cs.bounded |= 1u << m;
                 }
@@ -1328,7 +1355,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                             }
                         if (!__any_sync(FULL, any)) tj = (int64_t)warp_min_u64(mn);
                     }
-                    const int64_t fj = schedule_task<M, NS, false, GEN>(j, desc[j], tj, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem,
+                    const int64_t fj = schedule_task<M, NS, false, GEN, CAP>(j, desc[j], tj, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem,
                                                                    s_ptype, pm, pt, pv, avail, head, tail, hfin, mk,
                                                                    ok, sched_base, sel, rp_seed, cache, links, cs, capfail);
                     const int e0 = succoff[j], e1 = succoff[j + 1];
@@ -1397,7 +1424,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                             ++qt;
                             continue;
                         }
-                        schedule_task<M, NS, true, GEN>(j, dsc, t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
+                        schedule_task<M, NS, true, GEN, CAP>(j, dsc, t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
                                                    avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache, links, cs, capfail);
                         ++scheduled;
                     }
@@ -1424,7 +1451,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                                     ++qt;
                                     continue;
                                 }
-                                schedule_task<M, NS, true, GEN>(jb + bit, desc[jb + bit], t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype,
+                                schedule_task<M, NS, true, GEN, CAP>(jb + bit, desc[jb + bit], t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype,
                                                            pm, pt, pv, avail, head, tail, hfin, mk, ok, sched_base,
                                                            sel, rp_seed, cache, links, cs, capfail);
                                 ++scheduled;
@@ -1444,7 +1471,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                         if (!__any_sync(FULL, any)) break;
                         const int j = link[qh].rq;
                         ++qh;
-                        schedule_task<M, NS, true, GEN>(j, desc[j], t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
+                        schedule_task<M, NS, true, GEN, CAP>(j, desc[j], t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
                                                    avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache, links, cs, capfail);
                         ++scheduled;
                     }
@@ -1601,12 +1628,16 @@ template <int M, int NS>
 void set_smem_attr(size_t smem) {
     cudaFuncSetAttribute(sim_kernel<M, NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(sim_kernel<M, NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (M > 1)
+        cudaFuncSetAttribute(sim_kernel<M, NS, true, false, (M > 1)>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
 }
 
 template <int M, int NS>
-void launch_one(bool gen, unsigned blocks, int threads, size_t smem, cudaStream_t stream, const DevPlatform &dp,
-                const KArgs &a, unsigned long long *ctr) {
-    if (gen) sim_kernel<M, NS, true><<<blocks, threads, smem, stream>>>(dp, a, ctr);
+void launch_one(bool gen, bool cap, unsigned blocks, int threads, size_t smem, cudaStream_t stream,
+                const DevPlatform &dp, const KArgs &a, unsigned long long *ctr) {
+    if (cap && M > 1) sim_kernel<M, NS, true, false, (M > 1)><<<blocks, threads, smem, stream>>>(dp, a, ctr);
+    else if (gen) sim_kernel<M, NS, true><<<blocks, threads, smem, stream>>>(dp, a, ctr);
     else sim_kernel<M, NS, false><<<blocks, threads, smem, stream>>>(dp, a, ctr);
 }
 
@@ -1765,15 +1796,16 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
     const unsigned ub = (unsigned)blocks;
     const bool gen = p->order != HESP_ORDER_FCFS || p->select != HESP_SELECT_EFT || p->cache != HESP_CACHE_WB ||
                      p->use_links || crit != nullptr || fmode != 0 || p->use_cap;
+    const bool cap = p->use_cap && fmode == 0;
     switch (p->n_mem) {
-    case 1: two ? launch_one<1, 2>(gen, ub, threads, smem, stream, dp, a, ctr)
-                : launch_one<1, 1>(gen, ub, threads, smem, stream, dp, a, ctr); break;
-    case 2: two ? launch_one<2, 2>(gen, ub, threads, smem, stream, dp, a, ctr)
-                : launch_one<2, 1>(gen, ub, threads, smem, stream, dp, a, ctr); break;
-    case 3: two ? launch_one<3, 2>(gen, ub, threads, smem, stream, dp, a, ctr)
-                : launch_one<3, 1>(gen, ub, threads, smem, stream, dp, a, ctr); break;
-    case 4: two ? launch_one<4, 2>(gen, ub, threads, smem, stream, dp, a, ctr)
-                : launch_one<4, 1>(gen, ub, threads, smem, stream, dp, a, ctr); break;
+    case 1: two ? launch_one<1, 2>(gen, cap, ub, threads, smem, stream, dp, a, ctr)
+                : launch_one<1, 1>(gen, cap, ub, threads, smem, stream, dp, a, ctr); break;
+    case 2: two ? launch_one<2, 2>(gen, cap, ub, threads, smem, stream, dp, a, ctr)
+                : launch_one<2, 1>(gen, cap, ub, threads, smem, stream, dp, a, ctr); break;
+    case 3: two ? launch_one<3, 2>(gen, cap, ub, threads, smem, stream, dp, a, ctr)
+                : launch_one<3, 1>(gen, cap, ub, threads, smem, stream, dp, a, ctr); break;
+    case 4: two ? launch_one<4, 2>(gen, cap, ub, threads, smem, stream, dp, a, ctr)
+                : launch_one<4, 1>(gen, cap, ub, threads, smem, stream, dp, a, ctr); break;
     default:
         return HESP_ERR_ARG;
     }
