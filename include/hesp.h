@@ -288,7 +288,9 @@ int hesp_simulate_batch(const hesp_platform *p, const hesp_cand *cands_dev, cons
  * to 16 dependence edges per task, more give HESP_ERR_CAPACITY).  Outputs
  * and the optional schedule as for hesp_simulate_batch (the schedule's
  * sizes: the task counts of the k-way partitions, e.g. from ntasks_dev of a
- * first call).  Returns HESP_ERR_UNSUPPORTED for max_factor or max_tiles
+ * first call).  crit_dev (nullable, int8, addressed like factors_dev):
+ * the critical-path flags of hesp_simulate_critical, per base task, for the
+ * iterative solver over factors.  Returns HESP_ERR_UNSUPPORTED for max_factor or max_tiles
  * outside the limits, HESP_ERR_ARG for bad pointers or sizes; asynchronous
  * on `stream`. */
 int hesp_sim_workspace_size_factors(const hesp_platform *p, int32_t max_tiles, int32_t max_factor, int64_t task_cap,
@@ -297,7 +299,8 @@ int hesp_simulate_factors(const hesp_platform *p, const hesp_cand *cands_dev, co
                           int64_t n_cand, int32_t max_tiles, int32_t max_factor, int32_t b, int64_t task_cap,
                           int64_t *makespan_dev, int32_t *status_dev, int64_t *ntasks_dev,
                           const int64_t *sched_offsets_dev, int16_t *proc_dev, int64_t *start_dev,
-                          int64_t *finish_dev, void *workspace_dev, size_t workspace_bytes, void *stream);
+                          int64_t *finish_dev, int8_t *crit_dev, void *workspace_dev, size_t workspace_bytes,
+                          void *stream);
 
 /* Table 1 metrics (Sec. 3) of simulated candidates, one value per candidate:
  *   busy_dev[c]      = sum over its tasks of finish - start (the processors'
@@ -399,6 +402,17 @@ int hesp_simulate_critical(const hesp_platform *p, const hesp_cand *cands_dev, c
  * ERR_UNSUPPORTED for n_base > 32767.  Asynchronous on `stream`. */
 int hesp_solver_moves(const int8_t *levels_dev, int32_t n_base, int32_t n_levels, int32_t mode,
                       const int8_t *crit_dev, int32_t *moves_dev, int64_t *count_dev, int8_t *rows_dev, void *stream);
+
+/* hesp_solver_moves over any value range [lo, hi] (0 <= lo <= hi <= 127):
+ * the partition factors k of hesp_simulate_factors (lo = 1, hi = max_factor:
+ * Sec. 2.1, the partition parameter p = 1/k of a task is made finer, k + 1,
+ * or coarser, k - 1, down to merging the cluster back at k = 1).  A finer
+ * move for each selected base task below hi, a coarser one for each base
+ * task above lo; Shallow selects the base tasks at the minimal value.
+ * hesp_solver_moves is this call with lo = 0, hi = n_levels - 1. */
+int hesp_solver_moves_range(const int8_t *values_dev, int32_t n_base, int32_t lo, int32_t hi, int32_t mode,
+                            const int8_t *crit_dev, int32_t *moves_dev, int64_t *count_dev, int8_t *rows_dev,
+                            void *stream);
 
 /* Partition stage, step (2): score the *count_dev moves from their simulated
  * makespan_dev / status_dev (index r = row r of hesp_solver_moves) against

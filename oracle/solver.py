@@ -29,6 +29,12 @@ cluster of depth l), so a move changes one base task's level by one:
   and takes the first kept move (in increasing k) whose running score sum
   exceeds r, i.e. each with probability score / S.
 * No kept move: the partition is a local optimum and the solver stops.
+
+With factors=True the partition is one partition factor k per base task
+(one-level k-way partitions, the partition parameter p = 1/k of Sec. 2.1):
+a finer move k + 1 for each selected base task below the largest factor, a
+coarser move k - 1 for every base task above 1 (k = 1 merges the cluster
+back); Shallow selects the base tasks with the smallest factor.
 """
 from __future__ import annotations
 
@@ -37,7 +43,7 @@ from typing import List, Optional
 
 import numpy as np
 
-from . import deps, expand, levels_to_code, simulate
+from . import deps, deps_side, expand, factors_to_code, lcm_of, levels_to_code, simulate, simulate_factors
 
 MODE_ALL, MODE_CP, MODE_SHALLOW = 0, 1, 2
 PICK_HARD, PICK_SOFT = 0, 1
@@ -54,17 +60,17 @@ def _sm64(seed: int, c: int, k: int) -> int:
     return z ^ (z >> 31)
 
 
-def critical_bases(pl, n: int, b: int, levels) -> tuple:
+def critical_bases(pl, n: int, b: int, levels, factors: bool = False) -> tuple:
     """Schedule stage: simulate the partition and flag, per base task,
     whether one of its tasks lies on the critical path.  Returns
     (flags int8[n_base], makespan)."""
     lv = np.ascontiguousarray(levels, np.int8)
-    r = simulate(pl, n, b, lv)
+    r = simulate_factors(pl, n, b, lv) if factors else simulate(pl, n, b, lv)
     if r["status"] != 0:
         raise ValueError("simulation failed (%d)" % r["status"])
-    code = levels_to_code(n, lv)
+    code = factors_to_code(n, lv) if factors else levels_to_code(n, lv)
     d = expand(n, b, code)
-    po, pv, _ = deps(n, b, code, 1, int(lv.max()))
+    po, pv, _ = deps_side(n, b, code, b // lcm_of(lv)) if factors else deps(n, b, code, 1, int(lv.max()))
     T = r["n_tasks"]
     dur = [int(r["finish"][j] - r["start"][j]) for j in range(T)]
     preds = [[int(pv[e]) for e in range(po[j], po[j + 1])] for j in range(T)]
@@ -86,8 +92,10 @@ def critical_bases(pl, n: int, b: int, levels) -> tuple:
     return flags, r["makespan"]
 
 
-def neighbours(levels, n_levels: int, mode: int, crit=None):
-    """Stage (1): the moves (k, moved levels) in increasing k."""
+def neighbours(levels, n_levels: int, mode: int, crit=None, factors: bool = False):
+    """Stage (1): the moves (k, moved levels) in increasing k.  Values lie in
+    0 .. n_levels - 1 (levels) or 1 .. n_levels (factors)."""
+    lo, hi = (1, n_levels) if factors else (0, n_levels - 1)
     lv = [int(x) for x in levels]
     nb = len(lv)
     if mode == MODE_ALL:
@@ -101,11 +109,11 @@ def neighbours(levels, n_levels: int, mode: int, crit=None):
         raise ValueError(mode)
     out = []
     for t in range(nb):
-        if t in sel and lv[t] < n_levels - 1:
+        if t in sel and lv[t] < hi:
             w = list(lv)
             w[t] += 1
             out.append((2 * t, np.array(w, np.int8)))
-        if lv[t] > 0:
+        if lv[t] > lo:
             w = list(lv)
             w[t] -= 1
             out.append((2 * t + 1, np.array(w, np.int8)))
@@ -139,18 +147,19 @@ class Step:
     chosen: Optional[int] = None  # move code k, or None at a local optimum
 
 
-def solve(pl, n: int, b: int, levels0, n_levels: int, mode: int, how: int, seed: int, iterations: int) -> List[Step]:
+def solve(pl, n: int, b: int, levels0, n_levels: int, mode: int, how: int, seed: int, iterations: int,
+          factors: bool = False) -> List[Step]:
     """Run the iterative solver from levels0 for at most `iterations`
     iterations; one Step per iteration (the last one may be the local
     optimum where no move is kept)."""
     lv = np.ascontiguousarray(levels0, np.int8).copy()
     steps = []
     for it in range(iterations):
-        crit, m = critical_bases(pl, n, b, lv)
-        nbrs = neighbours(lv, n_levels, mode, crit)
+        crit, m = critical_bases(pl, n, b, lv, factors)
+        nbrs = neighbours(lv, n_levels, mode, crit, factors)
         ms = []
         for _, w in nbrs:
-            r = simulate(pl, n, b, w, schedule=False)
+            r = simulate_factors(pl, n, b, w, schedule=False) if factors else simulate(pl, n, b, w, schedule=False)
             if r["status"] != 0:
                 raise ValueError("simulation failed (%d)" % r["status"])
             ms.append(r["makespan"])

@@ -536,7 +536,7 @@ int hesp_sim_workspace_size_factors(const hesp_platform *p, int32_t max_tiles, i
 int hesp_simulate_factors(const hesp_platform *p, const hesp_cand *cands, const int8_t *factors, int64_t n_cand,
                           int32_t max_tiles, int32_t max_factor, int32_t b, int64_t task_cap, int64_t *makespan,
                           int32_t *status, int64_t *ntasks, const int64_t *sched_off, int16_t *sproc, int64_t *sstart,
-                          int64_t *sfinish, void *ws, size_t ws_bytes, void *stream) {
+                          int64_t *sfinish, int8_t *crit, void *ws, size_t ws_bytes, void *stream) {
     if (!p || n_cand < 0 || task_cap < 0) return HESP_ERR_ARG;
     if (n_cand == 0) return HESP_OK;
     if (!cands || !factors || !makespan || !status || !ws || b < 1) return HESP_ERR_ARG;
@@ -558,7 +558,7 @@ int hesp_simulate_factors(const hesp_platform *p, const hesp_cand *cands, const 
     if (slots > n_cand) slots = n_cand;
     const DevPlatform dp = dev_platform_factors(p, b, max_factor);
     return launch_sim(p, dp, ar, slots, cands, factors, n_cand, max_tiles, max_factor, makespan, status, ntasks,
-                      sched_off, sproc, sstart, sfinish, nullptr, 0, 0, 1, b, (char *)ws, (cudaStream_t)stream);
+                      sched_off, sproc, sstart, sfinish, crit, 0, 0, 1, b, (char *)ws, (cudaStream_t)stream);
 }
 
 int hesp_schedule_metrics(const hesp_cand *cands, const int8_t *levels, int64_t n_cand, const int64_t *sched_off,

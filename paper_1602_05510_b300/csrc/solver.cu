@@ -5,12 +5,13 @@
 // every moved partition (hesp_simulate_batch, one launch for the whole
 // neighbourhood), so each move is scored by its exact makespan gain.
 //
-// A partition is one split level per base task; move k = 2 t + d changes base
-// task t by +1 (d = 0, partition) or -1 (d = 1, merge back).  Candidate
-// moves, in increasing k: a partition move for each base task picked by the
-// selection policy (All: every one; CP: those flagged critical; Shallow:
-// those at the minimal level) that is not at the deepest level, and a merge
-// move for every split base task.
+// A partition is one value per base task in [lo, hi]: its split level
+// (dyadic partitions, lo = 0) or its partition factor k (p = 1/k, lo = 1);
+// move k = 2 t + d changes base task t by +1 (d = 0, partition finer) or -1
+// (d = 1, merge back / repartition coarser).  Candidate moves, in increasing
+// k: a finer move for each base task picked by the selection policy (All:
+// every one; CP: those flagged critical; Shallow: those at the minimal
+// value) that is below hi, and a coarser move for every base task above lo.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -50,7 +51,7 @@ __device__ int block_excl_scan(int v, int *excl, int *s_warp) {
     return total;
 }
 
-__global__ void __launch_bounds__(kThreads) moves_kernel(const int8_t *lv, int nb, int n_levels, int mode,
+__global__ void __launch_bounds__(kThreads) moves_kernel(const int8_t *lv, int nb, int lo, int hi, int mode,
                                                          const int8_t *crit, int32_t *moves, int64_t *count) {
     __shared__ int s_warp[32];
     __shared__ int s_min;
@@ -72,11 +73,11 @@ __global__ void __launch_bounds__(kThreads) moves_kernel(const int8_t *lv, int n
             const int t = k >> 1;
             const int l = lv[t];
             if (k & 1) {
-                ok = l > 0;
+                ok = l > lo;
             } else {
                 const bool sel = mode == HESP_SOLVER_ALL || (mode == HESP_SOLVER_CP && crit[t] != 0) ||
                                  (mode == HESP_SOLVER_SHALLOW && l == lmin);
-                ok = sel && l < n_levels - 1;
+                ok = sel && l < hi;
             }
         }
         int excl;
@@ -211,21 +212,30 @@ __global__ void __launch_bounds__(kThreads) pick_kernel(const int64_t *ms, const
 }  // namespace
 }  // namespace hesp
 
-extern "C" int hesp_solver_moves(const int8_t *levels_dev, int32_t n_base, int32_t n_levels, int32_t mode,
-                                 const int8_t *crit_dev, int32_t *moves_dev, int64_t *count_dev, int8_t *rows_dev,
-                                 void *stream) {
-    if (!levels_dev || !moves_dev || !count_dev || n_base < 1 || n_levels < 1 || n_levels > HESP_MAX_LEVEL + 1 ||
+extern "C" int hesp_solver_moves_range(const int8_t *values_dev, int32_t n_base, int32_t lo, int32_t hi,
+                                       int32_t mode, const int8_t *crit_dev, int32_t *moves_dev, int64_t *count_dev,
+                                       int8_t *rows_dev, void *stream) {
+    const int8_t *levels_dev = values_dev;
+    if (!levels_dev || !moves_dev || !count_dev || n_base < 1 || lo < 0 || hi < lo || hi > 127 ||
         mode < HESP_SOLVER_ALL || mode > HESP_SOLVER_SHALLOW || (mode == HESP_SOLVER_CP && !crit_dev))
         return HESP_ERR_ARG;
     if (n_base > 32767) return HESP_ERR_UNSUPPORTED;  // one grid row per move
     const cudaStream_t st = (cudaStream_t)stream;
-    hesp::moves_kernel<<<1, hesp::kThreads, 0, st>>>(levels_dev, n_base, n_levels, mode, crit_dev, moves_dev,
+    hesp::moves_kernel<<<1, hesp::kThreads, 0, st>>>(levels_dev, n_base, lo, hi, mode, crit_dev, moves_dev,
                                                      count_dev);
     if (rows_dev) {
         const int bx = (n_base + 255) / 256;
         hesp::rows_kernel<<<dim3(bx, 2 * n_base), 256, 0, st>>>(levels_dev, n_base, moves_dev, count_dev, rows_dev);
     }
     return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
+}
+
+extern "C" int hesp_solver_moves(const int8_t *levels_dev, int32_t n_base, int32_t n_levels, int32_t mode,
+                                 const int8_t *crit_dev, int32_t *moves_dev, int64_t *count_dev, int8_t *rows_dev,
+                                 void *stream) {
+    if (n_levels < 1 || n_levels > HESP_MAX_LEVEL + 1) return HESP_ERR_ARG;
+    return hesp_solver_moves_range(levels_dev, n_base, 0, n_levels - 1, mode, crit_dev, moves_dev, count_dev,
+                                   rows_dev, stream);
 }
 
 extern "C" int hesp_solver_pick(const int64_t *makespan_dev, const int32_t *status_dev, const int32_t *moves_dev,

@@ -41,6 +41,7 @@ EXPORTS = (
     "hesp_sim_autotune", "hesp_sort_cands_workspace_size", "hesp_sort_cands_by_size", "hesp_platform_set_policy",
     "hesp_simulate_critical", "hesp_solver_moves", "hesp_solver_pick", "hesp_schedule_metrics",
     "hesp_sim_workspace_size_factors", "hesp_simulate_factors", "hesp_platform_set_capacity",
+    "hesp_solver_moves_range",
     "hesp_sim_workspace_size_kept", "hesp_simulate_batch_keep", "hesp_simulate_batch_reuse",
     "hesp_platform_set_cache", "hesp_surrogate_save", "hesp_surrogate_load", "hesp_platform_set_link",
     "hesp_dag_build_kept",
@@ -108,8 +109,9 @@ def lib():
         L.hesp_simulate_critical.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, sz, vp]
         L.hesp_platform_set_capacity.argtypes = [vp, i32, i64]
         L.hesp_sim_workspace_size_factors.argtypes = [vp, i32, i32, i64, i64, ctypes.POINTER(sz)]
-        L.hesp_simulate_factors.argtypes = [vp, vp, vp, i64, i32, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, sz,
-                                            vp]
+        L.hesp_simulate_factors.argtypes = [vp, vp, vp, i64, i32, i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                            sz, vp]
+        L.hesp_solver_moves_range.argtypes = [vp, i32, i32, i32, i32, vp, vp, vp, vp, vp]
         L.hesp_sim_workspace_size_kept.argtypes = [i32, i32, i64, i64, ctypes.POINTER(sz)]
         L.hesp_simulate_batch_keep.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, vp, vp, sz, vp]
         L.hesp_dag_build_kept.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp, vp, sz, vp]
@@ -323,10 +325,12 @@ def alloc_workspace_factors(platform: Platform, max_tiles, max_factor, n_cand, t
 
 
 def simulate_factors(platform: Platform, cands, factors, n_cand, max_tiles, max_factor, b, workspace,
-                     makespan=None, status=None, ntasks=None, schedule=None, stream=None, task_cap=0):
+                     makespan=None, status=None, ntasks=None, schedule=None, stream=None, task_cap=0, crit=None):
     """hesp_simulate_factors: one partition factor k (p = 1/k) per base task,
     every candidate of block size b.  Arguments and results as
-    simulate_batch, with `factors` (int8 device tensor) in place of levels."""
+    simulate_batch, with `factors` (int8 device tensor) in place of levels;
+    `crit` (int8 device tensor like factors, optional) receives the
+    critical-path flags per base task."""
     import torch
     dev = factors.device
     if makespan is None:
@@ -338,7 +342,8 @@ def simulate_factors(platform: Platform, cands, factors, n_cand, max_tiles, max_
         so, sp, ss, sf = schedule
     check(lib().hesp_simulate_factors(platform.h, _ptr(cands), _ptr(factors), n_cand, max_tiles, max_factor, b,
                                       task_cap, _ptr(makespan), _ptr(status), _ptr(ntasks), _ptr(so), _ptr(sp),
-                                      _ptr(ss), _ptr(sf), _ptr(workspace), workspace.numel(), _stream(stream)),
+                                      _ptr(ss), _ptr(sf), _ptr(crit), _ptr(workspace), workspace.numel(),
+                                      _stream(stream)),
           "hesp_simulate_factors")
     return makespan, status, ntasks
 
@@ -451,6 +456,13 @@ def solver_moves(levels, n_base, n_levels, mode, crit, moves, count, rows=None, 
     """hesp_solver_moves: candidate moves of the partition `levels`."""
     check(lib().hesp_solver_moves(_ptr(levels), n_base, n_levels, mode, _ptr(crit), _ptr(moves), _ptr(count),
                                   _ptr(rows), _stream(stream)), "hesp_solver_moves")
+
+
+def solver_moves_range(values, n_base, lo, hi, mode, crit, moves, count, rows=None, stream=None):
+    """hesp_solver_moves_range: candidate moves of a partition whose values
+    lie in [lo, hi] (partition factors: lo = 1, hi = max_factor)."""
+    check(lib().hesp_solver_moves_range(_ptr(values), n_base, lo, hi, mode, _ptr(crit), _ptr(moves), _ptr(count),
+                                        _ptr(rows), _stream(stream)), "hesp_solver_moves_range")
 
 
 def solver_pick(makespan, status, moves, count, pick, seed, iteration, cur_makespan, levels, chosen, stream=None):

@@ -222,16 +222,27 @@ class IterativeSolver:
     (selection All / CP / Shallow), simulates every moved partition in one
     batched launch, and applies the best (Hard) or a score-proportional draw
     (Soft).  Per iteration the host reads back two numbers (the move count
-    and the chosen move)."""
+    and the chosen move).
+
+    factors=True: the partition is one factor k in 1 .. n_levels per base
+    task (one-level k-way partitions, p = 1/k, hesp_simulate_factors); a move
+    makes a task's p finer (k + 1) or coarser (k - 1, merging it back at
+    k = 1)."""
 
     def __init__(self, spec, n_tiles, b, n_levels, mode, pick, task_cap=0, ws_bytes=None, order=0, select=0,
-                 rp_seed=0):
+                 rp_seed=0, factors=False):
         import torch
         self.plat = hesp.Platform(spec, order=order, select=select, rp_seed=rp_seed)
         self.n, self.b, self.NL, self.mode, self.pick, self.task_cap = n_tiles, b, n_levels, mode, pick, task_cap
+        self.factors = factors
+        self.lo, self.hi = (1, n_levels) if factors else (0, n_levels - 1)
         nb = self.nb = W.base_count(n_tiles)
         self.max_moves = 2 * nb
-        self.ws = hesp.alloc_workspace(self.plat, n_tiles, n_levels - 1, self.max_moves, task_cap, max_bytes=ws_bytes)
+        if factors:
+            self.ws = hesp.alloc_workspace_factors(self.plat, n_tiles, n_levels, self.max_moves, task_cap)
+        else:
+            self.ws = hesp.alloc_workspace(self.plat, n_tiles, n_levels - 1, self.max_moves, task_cap,
+                                           max_bytes=ws_bytes)
         dev = "cuda"
         self.cur = torch.zeros(nb, dtype=torch.int8, device=dev)
         self.rows = torch.empty(self.max_moves * nb, dtype=torch.int8, device=dev)
@@ -253,12 +264,26 @@ class IterativeSolver:
         import torch
         if levels is not None:
             self.cur.copy_(torch.from_numpy(np.ascontiguousarray(levels, np.int8)))
+        elif self.factors:
+            self.cur.copy_(torch.from_numpy(W.uniform_factors(seed, draw, 1, self.nb, self.NL)[0]))
         else:
             hesp.generate_candidates(hesp.GEN_UNIFORM, seed, draw, 1, self.n, self.b, self.NL, self.cur)
 
     def schedule_stage(self):
-        hesp.simulate_critical(self.plat, self.cand_cur, self.cur, 1, self.n, self.NL - 1, self.ws, self.crit,
-                               makespan=self.cur_ms, status=self.cur_st, task_cap=self.task_cap)
+        if self.factors:
+            hesp.simulate_factors(self.plat, self.cand_cur, self.cur, 1, self.n, self.NL, self.b, self.ws,
+                                  makespan=self.cur_ms, status=self.cur_st, task_cap=self.task_cap, crit=self.crit)
+        else:
+            hesp.simulate_critical(self.plat, self.cand_cur, self.cur, 1, self.n, self.NL - 1, self.ws, self.crit,
+                                   makespan=self.cur_ms, status=self.cur_st, task_cap=self.task_cap)
+
+    def simulate_rows(self, k):
+        if self.factors:
+            hesp.simulate_factors(self.plat, self.cands_rows, self.rows, k, self.n, self.NL, self.b, self.ws,
+                                  makespan=self.ms, status=self.st, ntasks=self.nt, task_cap=self.task_cap)
+        else:
+            hesp.simulate_batch(self.plat, self.cands_rows, self.rows, k, self.n, self.NL - 1, self.ws,
+                                makespan=self.ms, status=self.st, ntasks=self.nt, task_cap=self.task_cap)
 
     def iterate(self, seed, iteration, trace=False):
         """One iteration from the current partition.  Returns (chosen move or
@@ -267,7 +292,8 @@ class IterativeSolver:
         if trace:
             lv0 = self.cur.cpu().numpy().copy()
         self.schedule_stage()
-        hesp.solver_moves(self.cur, self.nb, self.NL, self.mode, self.crit, self.moves, self.count, self.rows)
+        hesp.solver_moves_range(self.cur, self.nb, self.lo, self.hi, self.mode, self.crit, self.moves, self.count,
+                                self.rows)
         k = int(self.count.item())
         step = None
         if trace:
@@ -276,8 +302,7 @@ class IterativeSolver:
             if trace:
                 step = SolverStep(lv0, m0, [], [], None)
             return None, 0, 0, step
-        hesp.simulate_batch(self.plat, self.cands_rows, self.rows, k, self.n, self.NL - 1, self.ws,
-                            makespan=self.ms, status=self.st, ntasks=self.nt, task_cap=self.task_cap)
+        self.simulate_rows(k)
         if trace:
             mv = self.moves[:k].cpu().numpy().tolist()
             mss = self.ms[:k].cpu().numpy().tolist()

@@ -97,3 +97,44 @@ def test_iterative_search_arm_small_budget():
     lv0 = W.uniform_levels(3, 0, 1, 120, 3)[0]
     m0 = O.simulate(O.make_platform(spec), 8, 2048, lv0, schedule=False)["makespan"]
     assert log.best[0] <= m0
+
+
+@pytest.mark.parametrize("mode", [hesp.SOLVER_ALL, hesp.SOLVER_CP, hesp.SOLVER_SHALLOW])
+@pytest.mark.parametrize("pick", [hesp.PICK_HARD, hesp.PICK_SOFT])
+@pytest.mark.parametrize("key,n", [("cfg1a", 3), ("cfg1b", 3), ("cfg2", 2)])
+def test_factor_solver_trajectory_parity(mode, pick, key, n):
+    """The solver over partition factors (p = 1/k, k in 1..4, non-dyadic
+    moves): GPU trajectories equal the oracle's, from the unsplit partition
+    and from a random factor vector."""
+    spec = W.PLATFORMS[key]
+    nb = W.base_count(n)
+    b = 3072
+    for start in (np.ones(nb, np.int8), W.uniform_factors(mode * 7 + pick, 0, 1, nb, 4)[0]):
+        seed = 2000 + mode
+        sv = S.IterativeSolver(spec, n, b, 4, mode, pick, factors=True)
+        g = sv.solve(start, seed, 6)
+        o = V.solve(O.make_platform(spec), n, b, start, 4, mode, pick, seed, 6, factors=True)
+        same_trajectory(g, o)
+
+
+def test_factor_critical_flags_parity():
+    """Critical-path flags of factor candidates (hesp_simulate_factors with
+    crit) against the oracle, on 8 x 8 tiles."""
+    import torch
+    spec = W.PLATFORMS["cfg1a"]
+    n, b, C = 8, 3072, 16
+    nb = W.base_count(n)
+    f = W.uniform_factors(31, 0, C, nb, 4)
+    plat = hesp.Platform(spec)
+    d_f = torch.from_numpy(f.reshape(-1).copy()).cuda()
+    cands = hesp.cands_tensor(n, b, np.arange(C, dtype=np.int64) * nb)
+    crit = torch.zeros(C * nb, dtype=torch.int8, device="cuda")
+    ms, st, _ = hesp.simulate_factors(plat, cands, d_f, C, n, 4, b, hesp.alloc_workspace_factors(plat, n, 4, C),
+                                      crit=crit)
+    torch.cuda.synchronize()
+    crit = crit.cpu().numpy().reshape(C, nb)
+    pl = O.make_platform(spec)
+    for c in range(C):
+        flags, m = V.critical_bases(pl, n, b, f[c], factors=True)
+        assert int(st[c]) == 0 and int(ms[c]) == m
+        assert np.array_equal(crit[c], flags), c

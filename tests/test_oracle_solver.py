@@ -192,3 +192,76 @@ def test_soft_draw_and_frequencies():
     assert V.pick(cur, moves, [1000] * 6, V.PICK_SOFT, 5, 0) is None
     assert V.pick(cur, moves, ms, V.PICK_HARD, 0, 0) == 2
     assert V.pick(cur, [0, 1], [900, 900], V.PICK_HARD, 0, 0) == 0
+
+
+# ------------------------------------------ the solver over partition factors
+
+
+@pytest.mark.parametrize("mode", [V.MODE_ALL, V.MODE_CP, V.MODE_SHALLOW])
+@pytest.mark.parametrize("how", [V.PICK_HARD, V.PICK_SOFT])
+def test_factor_solver_with_factors_one_two_is_the_level_solver(mode, how):
+    """Factors 1 / 2 are the dyadic levels 0 / 1: with the largest factor 2
+    the factor solver makes exactly the level solver's moves (same codes,
+    same makespans) from the same start."""
+    pl = O.make_platform(W.PLATFORMS["cfg1a"])
+    n, b = 3, 2048
+    lv0 = np.random.default_rng(mode * 2 + how).integers(0, 2, W.base_count(n)).astype(np.int8)
+    a = V.solve(pl, n, b, lv0, 2, mode, how, 99, 8)
+    f = V.solve(pl, n, b, lv0 + 1, 2, mode, how, 99, 8, factors=True)
+    assert len(a) == len(f)
+    for sa, sf in zip(a, f):
+        assert np.array_equal(sa.levels + 1, sf.levels)
+        assert sa.makespan == sf.makespan and sa.moves == sf.moves and sa.makespans == sf.makespans
+        assert sa.chosen == sf.chosen
+
+
+def test_factor_neighbours_bounds():
+    """Values 1 .. 4: a finer move below 4, a coarser move above 1."""
+    nb = V.neighbours([1, 2, 4, 3], 4, V.MODE_ALL, factors=True)
+    assert [k for k, _ in nb] == [0, 2, 3, 5, 6, 7]
+    assert [list(w) for _, w in nb][:2] == [[2, 2, 4, 3], [1, 3, 4, 3]]
+
+
+def test_factor_solver_improves_and_crit_flags_brute_force():
+    """Hard moves lower the makespan at every step on non-dyadic
+    partitions, and the factor critical flags equal a brute-force path
+    enumeration."""
+    pl = O.make_platform(W.PLATFORMS["cfg1a"])
+    n, b = 2, 3072
+    f0 = np.array([3, 1, 2, 1], np.int8)
+    steps = V.solve(pl, n, b, f0, 4, V.MODE_ALL, V.PICK_HARD, 1, 6, factors=True)
+    ms = [s.makespan for s in steps]
+    assert all(x > y for x, y in zip(ms, ms[1:]))
+    # brute force on the factor DAG
+    r = O.simulate_factors(pl, n, b, f0)
+    code = O.factors_to_code(n, f0)
+    d = O.expand(n, b, code)
+    po, pv, _ = O.deps_side(n, b, code, b // O.lcm_of(f0))
+    T = r["n_tasks"]
+    dur = (r["finish"] - r["start"]).astype(np.int64)
+    succ = [[] for _ in range(T)]
+    for j in range(T):
+        for e in range(po[j], po[j + 1]):
+            succ[int(pv[e])].append(j)
+    best, paths = 0, []
+
+    def walk(j, acc, path):
+        path.append(j)
+        acc += int(dur[j])
+        if not succ[j]:
+            paths.append((acc, list(path)))
+        for s_ in succ[j]:
+            walk(s_, acc, path)
+        path.pop()
+
+    for j in range(T):
+        if po[j + 1] == po[j]:
+            walk(j, 0, [])
+    best = max(w for w, _ in paths)
+    flags = np.zeros(len(f0), np.int8)
+    for w, p in paths:
+        if w == best:
+            for j in p:
+                flags[int(d["base"][j])] = 1
+    got, m = V.critical_bases(pl, n, b, f0, factors=True)
+    assert m == r["makespan"] and np.array_equal(got, flags)
