@@ -309,8 +309,8 @@ def run_gpu(args):
 # for the kernel source they were taken on: DRAM bytes per 4,096 candidates on the
 # CPU+GPU platform (scaled to a launch by candidates; traffic grows in proportion)
 # and the share of issue slots busy.
-SIM_NCU = {"source_sha1_12": "474a8c57dc3c", "dram_bytes_per_4096": 0.531109e9 + 0.327541e9,
-           "issue_active_pct": 62.76, "warps_per_sm": 25.4, "alu_pipe_pct": 56.1}
+SIM_NCU = {"source_sha1_12": "cbeb422b6770", "dram_bytes_per_4096": 0.530871e9 + 0.327955e9,
+           "issue_active_pct": 62.60, "warps_per_sm": 25.5, "alu_pipe_pct": 56.2}
 
 
 def sim_source_matches():
