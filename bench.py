@@ -142,8 +142,9 @@ def run_gpu(args):
 
     plats = [hesp.Platform(W.PLATFORMS[k]) for k in PLATS]
     if args.share_dag:
-        # one arena per candidate: the first platform's launch builds and keeps
-        # each DAG, the second simulates the kept DAGs
+        # one arena per candidate: each DAG is built once (in a launch of its
+        # own, or inside the first platform's launch with --keep-in-first) and
+        # every platform simulates the kept DAGs
         kept = hesp.alloc_workspace_kept(N_TILES, MAX_LEVEL, C)
         ws = [kept for _ in plats]
     else:
@@ -152,7 +153,7 @@ def run_gpu(args):
     bst = torch.empty(C, dtype=torch.int32, device=dev)
     build_apart = args.share_dag and not args.keep_in_first
 
-    def build(cands_, levels_):
+    def build_dags(cands_, levels_):
         # the DAGs alone, in a launch of their own (platform independent)
         hesp.dag_build_kept(cands_, levels_, C, N_TILES, MAX_LEVEL, ws[0], status=bst)
 
@@ -183,7 +184,7 @@ def run_gpu(args):
         if build_apart:
             if ev is not None:
                 ev[-1][0].record(stream)
-            build(sim_c, levels)
+            build_dags(sim_c, levels)
             if ev is not None:
                 ev[-1][1].record(stream)
         for i, p in enumerate(plats):
@@ -254,7 +255,7 @@ def run_gpu(args):
             cands.copy_(cand_host, non_blocking=True)
             sim_c = hesp.sort_cands_by_size(cands, levels, C, scands, perm, sort_ws)[0] if args.lpt else cands
             if build_apart:
-                build(sim_c, levels)
+                build_dags(sim_c, levels)
             for i, p in enumerate(plats):
                 simulate(i, p, sim_c, levels)
                 out_host[i].copy_(ms[i], non_blocking=True)
