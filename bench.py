@@ -310,8 +310,8 @@ def run_gpu(args):
 # for the kernel source they were taken on: DRAM bytes per 4,096 candidates on the
 # CPU+GPU platform (scaled to a launch by candidates; traffic grows in proportion)
 # and the share of issue slots busy.
-SIM_NCU = {"source_sha1_12": "cbeb422b6770", "dram_bytes_per_4096": 0.530871e9 + 0.327955e9,
-           "issue_active_pct": 62.60, "warps_per_sm": 25.5, "alu_pipe_pct": 56.2}
+SIM_NCU = {"source_sha1_12": "abb1db5e3780", "dram_bytes_per_4096": 0.531826e9 + 0.327195e9,
+           "issue_active_pct": 63.07, "warps_per_sm": 25.6, "alu_pipe_pct": 55.6}
 
 
 def sim_source_matches():

@@ -1400,9 +1400,9 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
             Link *const link = at<Link>(base, a.ar.off_link);
             int qh = 0, qt = 0;  // F-P / R-P wait queue: link[qh .. qt).rq
             int64_t t = 0;
-            int64_t iters = 0;
-            const int64_t iter_cap = 4 * T + 64;
-            int64_t scheduled = 0;
+            int iters = 0;
+            const int iter_cap = 4 * (int)T + 64;
+            int scheduled = 0;
             bool ok = true;
             // Released tasks wait either in the bitmap (several completions at
             // one time, or a long successor list) or, when a single task
