@@ -897,6 +897,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
     __shared__ int64_t s_wsum[4 * HESP_LB];
     __shared__ int8_t s_pmem[HESP_MAX_PROCS];
     __shared__ int8_t s_ptype[HESP_MAX_PROCS];
+    __shared__ int s_info[8][32];  // dependence phase: per-lane atom info of the warp's round
     extern __shared__ uint32_t s_bitmap[];
     for (int i = threadIdx.x; i < 4 * HESP_MAX_TYPES * HESP_LB; i += blockDim.x) s_exec[i] = pl.exec[i];
     for (int i = threadIdx.x; i < 4 * HESP_LB; i += blockDim.x) s_wsum[i] = pl.wsum[i];
@@ -1075,10 +1076,91 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
             }
             __syncwarp();
             const unsigned lt_mask = (1u << lane) - 1u;
-            uint64_t dn = T > 0 ? desc[0] : 0;
-            for (int j = 0; j < (int)T; ++j) {
-                const uint64_t d = dn;
-                if (j + 1 < (int)T) dn = desc[j + 1];  // prefetch
+            int *const info = s_info[threadIdx.x >> 5];  // per lane: (task in group << 1) | writes
+            // Tasks are taken in creation order, as many consecutive ones per
+            // round as have 32 atoms between them (one atom per lane).  The
+            // last writer of an atom a task touches is the latest earlier
+            // task of the round that writes it, else the last writer before
+            // the round; a task whose atoms need more than one round is
+            // taken alone (the per-task mark deduplicates across rounds).
+            int j0 = 0;
+            while (j0 < (int)T) {
+                const int jt = j0 + lane;
+                uint64_t dl = 0;
+                int totl = 0;
+                if (jt < (int)T) {
+                    dl = desc[jt];
+                    const int opl = (int)(dl & 3), lvll = (int)((dl >> 2) & 7);
+                    const int wfl = fm ? fL / lvll : 0;
+                    totl = nreg_of(opl) * (fm ? wfl * wfl : 1 << (2 * (Lc - lvll)));
+                }
+                const int incl = warp_incl_scan(totl, lane);
+                const int g = __popc(__ballot_sync(FULL, jt < (int)T && incl <= 32));  // tasks of the round
+                if (g > 0) {
+                    const int total = __shfl_sync(FULL, incl, g - 1);
+                    // owner task of atom slot `lane`: first task lane whose inclusive count exceeds it
+                    int pos = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int v = __shfl_sync(FULL, incl, pos + step - 1);
+                        if (v <= lane) pos += step;
+                    }
+                    const int ob = min(pos, 31);
+                    const bool act = lane < total;
+                    const uint64_t d = __shfl_sync(FULL, dl, ob);
+                    const int q = lane - (__shfl_sync(FULL, incl, ob) - __shfl_sync(FULL, totl, ob));
+                    const int op = (int)(d & 3), lvl = (int)((d >> 2) & 7);
+                    const int nr = nreg_of(op);
+                    const int wf = fm ? fL / lvl : 0;
+                    const int sh = fm ? 0 : 2 * (Lc - lvl);
+                    int rr = 0;
+                    const uint32_t x = act ? task_atom(d, q, sh, wf, fL, fm, rr) : 0u;
+                    const bool wr = act && rr == nr - 1;
+                    const int before = act ? lw[x] : -1;
+                    info[lane] = (ob << 1) | (wr ? 1 : 0);
+                    const unsigned peers = __match_any_sync(FULL, act ? (int)x : -1 - lane);
+                    __syncwarp();
+                    // latest writer of x among earlier tasks of the round, and the
+                    // round's last writer of x (which updates the last-writer table)
+                    int inw = -1, lastw = -1;
+                    for (unsigned pm = peers; pm; pm &= pm - 1) {
+                        const int v = info[__ffs(pm) - 1];
+                        if (v & 1) {
+                            const int pb = v >> 1;
+                            if (pb < ob) inw = max(inw, pb);
+                            lastw = max(lastw, pb);
+                        }
+                    }
+                    const int pred = !act ? -1 : (inw >= 0 ? j0 + inw : before);
+                    // one edge per distinct (task, predecessor)
+                    const unsigned long long key = pred >= 0 ? ((unsigned long long)ob << 32) | (unsigned)pred
+                                                             : ~0ull - (unsigned long long)lane;
+                    const unsigned kg = __match_any_sync(FULL, key);
+                    const bool emit = pred >= 0 && lane == __ffs(kg) - 1;
+                    const unsigned em = __ballot_sync(FULL, emit);
+                    if (emit) {
+                        const int64_t e = E + __popc(em & lt_mask);
+                        if (e < a.ar.Ecap) {
+                            epred[e] = pred;
+                            esucc[e] = j0 + ob;
+                        }
+                        atomicAdd(&scnt[pred], 1);
+                    }
+                    E += __popc(em);
+                    if (lane < g) {  // lane t: task j0 + t, its atom slots [incl - tot, incl)
+                        const int lo = incl - totl;
+                        const unsigned rm = (totl >= 32 ? ~0u : ((1u << totl) - 1u)) << lo;
+                        pending[jt] = (uint16_t)__popc(em & rm);
+                    }
+                    __syncwarp();
+                    if (wr && ob == lastw) lw[x] = j0 + ob;
+                    __syncwarp();
+                    j0 += g;
+                    continue;
+                }
+                // task j0 alone, over several rounds
+                const int j = j0;
+                const uint64_t d = __shfl_sync(FULL, dl, 0);
                 const int op = (int)(d & 3);
                 const int lvl = (int)((d >> 2) & 7);
                 const int nr = nreg_of(op);
@@ -1086,9 +1168,6 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                 const int sh = fm ? 0 : 2 * (Lc - lvl);
                 const int na = fm ? wf * wf : 1 << sh;
                 const int tot = nr * na;
-                // a task whose atoms fit one round is deduplicated inside the
-                // warp; larger ones also use the per-task mark across rounds
-                const bool multi = tot > 32;
                 int cnt = 0;
                 for (int i0 = 0; i0 < tot; i0 += 32) {
                     const int i = i0 + lane;
@@ -1097,7 +1176,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     if (i < tot) w = lw[task_atom(d, i, sh, wf, fL, fm, rr)];
                     const unsigned grp = __match_any_sync(FULL, w);
                     bool isnew = lane == __ffs(grp) - 1 && w >= 0;
-                    if (multi && isnew) {
+                    if (isnew) {
                         if (mark[w] == j) isnew = false;
                         else mark[w] = j;
                     }
@@ -1111,7 +1190,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                         atomicAdd(&scnt[w], 1);
                     }
                     cnt += __popc(nm);
-                    if (multi) __syncwarp();
+                    __syncwarp();
                 }
                 if (lane == 0) pending[j] = (uint16_t)cnt;
                 E += cnt;
@@ -1120,6 +1199,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     lw[task_atom(d, (nr - 1) * na + i, sh, wf, fL, fm, rr)] = j;
                 }
                 __syncwarp();
+                j0 += 1;
             }
             if (E > a.ar.Ecap) status = HESP_ERR_CAPACITY;
         }
