@@ -68,6 +68,24 @@ __constant__ int8_t c_child_sel[4][8][3] = {
     // gemm(A, B, C): C -= A^T B; for k, i, j: gemm(Aki, Bkj -> Cij)
     {{0, 4, 8}, {0, 5, 9}, {1, 4, 10}, {1, 5, 11}, {2, 6, 8}, {2, 7, 9}, {3, 6, 10}, {3, 7, 11}}};
 
+// The partition tables, copied to shared memory by every kernel that decodes
+// tasks: lanes index them with different ops and levels, which the constant
+// cache would serialise.
+struct DecodeTables {
+    int32_t cnt[4][kMaxL + 1];
+    int8_t nchild[4];
+    int8_t child_op[4][8];
+    int8_t child_sel[4][8][3];
+};
+
+__device__ __forceinline__ void load_tables(DecodeTables &tb) {
+    for (int i = threadIdx.x; i < 4 * (kMaxL + 1); i += blockDim.x)
+        tb.cnt[i / (kMaxL + 1)][i % (kMaxL + 1)] = c_cnt[i / (kMaxL + 1)][i % (kMaxL + 1)];
+    for (int i = threadIdx.x; i < 4; i += blockDim.x) tb.nchild[i] = c_nchild[i];
+    for (int i = threadIdx.x; i < 32; i += blockDim.x) tb.child_op[i / 8][i % 8] = c_child_op[i / 8][i % 8];
+    for (int i = threadIdx.x; i < 96; i += blockDim.x) tb.child_sel[i / 24][(i / 3) % 8][i % 3] = c_child_sel[i / 24][(i / 3) % 8][i % 3];
+}
+
 __device__ __forceinline__ int nreg_of(int op) { return op == kOpChol ? 1 : (op == kOpGemm ? 3 : 2); }
 
 __device__ __forceinline__ uint32_t spread4(uint32_t v) {
@@ -145,7 +163,8 @@ __device__ void decode_base(int n, int64_t t, int &op, int &K, int &I, int &J) {
 
 // Descriptor of sub-task q of base task (op, K, I, J) split lvl times:
 // op (2 bits) | lvl (3) | atom start of region 0, 1, 2 (19 bits each).
-__device__ uint64_t decode_sub(int op, int K, int I, int J, int lvl, int q, int Lc, int n) {
+__device__ uint64_t decode_sub(int op, int K, int I, int J, int lvl, int q, int Lc, int n,
+                               const DecodeTables &tb) {
     int R[3] = {0, 0, 0}, C[3] = {0, 0, 0};
     if (op == kOpChol) {
         R[0] = K; C[0] = K;
@@ -163,19 +182,19 @@ __device__ uint64_t decode_sub(int op, int K, int I, int J, int lvl, int q, int 
     }
     int side = 1 << Lc;
     for (int d = lvl; d > 0; --d) {
-        int nch = c_nchild[op];
+        int nch = tb.nchild[op];
         int ci = 0;
         for (; ci < nch - 1; ++ci) {
-            int cc = c_cnt[c_child_op[op][ci]][d - 1];
+            int cc = tb.cnt[tb.child_op[op][ci]][d - 1];
             if (q < cc) break;
             q -= cc;
         }
-        int cop = c_child_op[op][ci];
+        int cop = tb.child_op[op][ci];
         int half = side >> 1;
         int nR[3] = {0, 0, 0}, nC[3] = {0, 0, 0};
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            int sel = c_child_sel[op][ci][r];
+            int sel = tb.child_sel[op][ci][r];
             int pr = sel >> 2, qp = (sel >> 1) & 1, qq = sel & 1;
             int baseR = pr == 0 ? R[0] : (pr == 1 ? R[1] : R[2]);
             int baseC = pr == 0 ? C[0] : (pr == 1 ? C[1] : C[2]);
@@ -898,6 +917,8 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
     __shared__ int8_t s_pmem[HESP_MAX_PROCS];
     __shared__ int8_t s_ptype[HESP_MAX_PROCS];
     __shared__ int s_info[8][32];  // dependence phase: per-lane atom info of the warp's round
+    __shared__ DecodeTables s_tab;
+    load_tables(s_tab);
     extern __shared__ uint32_t s_bitmap[];
     for (int i = threadIdx.x; i < 4 * HESP_MAX_TYPES * HESP_LB; i += blockDim.x) s_exec[i] = pl.exec[i];
     for (int i = threadIdx.x; i < 4 * HESP_LB; i += blockDim.x) s_wsum[i] = pl.wsum[i];
@@ -1014,7 +1035,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     int op, K, I, J;
                     decode_base(n, t, op, K, I, J);
                     const int l = a.levels[loff + t];
-                    cnt = fm ? fcount(op, l) : c_cnt[op][l];
+                    cnt = fm ? fcount(op, l) : s_tab.cnt[op][l];
                 }
                 tcount += __reduce_add_sync(FULL, (unsigned)cnt);
             }
@@ -1030,7 +1051,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                 if (t < nb) {
                     decode_base(n, t, op, K, I, J);
                     l = a.levels[loff + t];
-                    cnt = fm ? fcount(op, l) : c_cnt[op][l];
+                    cnt = fm ? fcount(op, l) : s_tab.cnt[op][l];
                 }
                 const int incl = warp_incl_scan(cnt, lane);
                 const int excl = incl - cnt;
@@ -1053,7 +1074,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     const int ol = __shfl_sync(FULL, l, owner);
                     if (g < total)
                         desc[off + g] = fm ? decode_sub_f(oop, oK, oI, oJ, ol, q, fL, n)
-                                           : decode_sub(oop, oK, oI, oJ, ol, q, Lc, n);
+                                           : decode_sub(oop, oK, oI, oJ, ol, q, Lc, n, s_tab);
                 }
                 off += total;
             }
@@ -1676,7 +1697,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     int op, K, I, J;
                     decode_base(n, t, op, K, I, J);
                     const int l = a.levels[loff + t];
-                    cnt = fm ? fcount(op, l) : c_cnt[op][l];
+                    cnt = fm ? fcount(op, l) : s_tab.cnt[op][l];
                 }
                 const int incl = warp_incl_scan(cnt, lane);
                 if (t < nb) {
