@@ -1104,20 +1104,23 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
             // task of the round that writes it, else the last writer before
             // the round; a task whose atoms need more than one round is
             // taken alone (the per-task mark deduplicates across rounds).
+            // (k-way partitions whose smallest tasks already fill a round are
+            // taken one task at a time)
+            const bool rounds = !fm || 3 * (fL / lmax) * (fL / lmax) <= 16;
             int j0 = 0;
             while (j0 < (int)T) {
                 const int jt = j0 + lane;
                 uint64_t dl = 0;
                 int totl = 0;
-                if (jt < (int)T) {
+                if (rounds && jt < (int)T) {
                     dl = desc[jt];
                     const int opl = (int)(dl & 3), lvll = (int)((dl >> 2) & 7);
                     const int wfl = fm ? fL / lvll : 0;
                     totl = nreg_of(opl) * (fm ? wfl * wfl : 1 << (2 * (Lc - lvll)));
                 }
-                const int incl = warp_incl_scan(totl, lane);
-                const int g = __popc(__ballot_sync(FULL, jt < (int)T && incl <= 32));  // tasks of the round
-                if (g > 0) {
+                const int incl = rounds ? warp_incl_scan(totl, lane) : 0;
+                const int g = rounds ? __popc(__ballot_sync(FULL, jt < (int)T && incl <= 32)) : 0;  // tasks of the round
+                if (g > 1) {
                     const int total = __shfl_sync(FULL, incl, g - 1);
                     // owner task of atom slot `lane`: first task lane whose inclusive count exceeds it
                     int pos = 0;
@@ -1179,9 +1182,9 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     j0 += g;
                     continue;
                 }
-                // task j0 alone, over several rounds
+                // task j0 alone (over several rounds when it has more than 32 atoms)
                 const int j = j0;
-                const uint64_t d = __shfl_sync(FULL, dl, 0);
+                const uint64_t d = rounds ? __shfl_sync(FULL, dl, 0) : desc[j];
                 const int op = (int)(d & 3);
                 const int lvl = (int)((d >> 2) & 7);
                 const int nr = nreg_of(op);
@@ -1189,6 +1192,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                 const int sh = fm ? 0 : 2 * (Lc - lvl);
                 const int na = fm ? wf * wf : 1 << sh;
                 const int tot = nr * na;
+                const bool multi = tot > 32;  // one round: deduplicated inside the warp
                 int cnt = 0;
                 for (int i0 = 0; i0 < tot; i0 += 32) {
                     const int i = i0 + lane;
@@ -1197,7 +1201,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     if (i < tot) w = lw[task_atom(d, i, sh, wf, fL, fm, rr)];
                     const unsigned grp = __match_any_sync(FULL, w);
                     bool isnew = lane == __ffs(grp) - 1 && w >= 0;
-                    if (isnew) {
+                    if (multi && isnew) {
                         if (mark[w] == j) isnew = false;
                         else mark[w] = j;
                     }
@@ -1749,6 +1753,9 @@ void launch_one(bool gen, bool cap, unsigned blocks, int threads, size_t smem, c
 __global__ void metrics_kernel(const hesp_cand *cands, const int8_t *levels, int64_t n_cand, const int64_t *sched_off,
                                const int64_t *start, const int64_t *finish, int64_t *busy, int64_t *ntasks,
                                int64_t *sum_block, int32_t *depth) {
+    __shared__ DecodeTables s_tab;
+    load_tables(s_tab);
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (c >= n_cand) return;
@@ -1761,8 +1768,8 @@ __global__ void metrics_kernel(const hesp_cand *cands, const int8_t *levels, int
         int op, K, I, J;
         decode_base(n, t, op, K, I, J);
         const int l = levels[cd.level_offset + t];
-        cnt += c_cnt[op][l];
-        sb += (int64_t)c_cnt[op][l] * (b >> l);
+        cnt += s_tab.cnt[op][l];
+        sb += (int64_t)s_tab.cnt[op][l] * (b >> l);
         lmax = max(lmax, l);
     }
 #pragma unroll
