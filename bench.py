@@ -310,8 +310,8 @@ def run_gpu(args):
 # for the kernel source they were taken on: DRAM bytes per 4,096 candidates on the
 # CPU+GPU platform (scaled to a launch by candidates; traffic grows in proportion)
 # and the share of issue slots busy.
-SIM_NCU = {"source_sha1_12": "abb1db5e3780", "dram_bytes_per_4096": 0.531826e9 + 0.327195e9,
-           "issue_active_pct": 63.07, "warps_per_sm": 25.6, "alu_pipe_pct": 55.6}
+SIM_NCU = {"source_sha1_12": "e2ee6a664226", "dram_bytes_per_4096": 0.531371e9 + 0.327081e9,
+           "issue_active_pct": 62.92, "warps_per_sm": 25.6, "alu_pipe_pct": 55.6}
 
 
 def sim_source_matches():
@@ -325,7 +325,7 @@ def sim_source_matches():
 
 def roofline(plats, t_kern, K, task_events_rank, clk, peaks):
     """Dominant kernel: the simulation kernel on the CPU+GPU platform (the
-    event loop with coherence, from the DAGs the build launch kept; 54 % of a
+    event loop with coherence, from the DAGs the build launch kept; 59 % of a
     step).  It is bound by integer/control issue, not by HBM or tensor cores;
     `achieved`
     counts the algorithmic int64 operations of the simulation per task-event
