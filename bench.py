@@ -346,6 +346,7 @@ def roofline(plats, t_kern, K, task_events_rank, clk, peaks):
             "peak_source": "derived: 148 SMs x 128 INT32 lanes x %.0f MHz / 2 (sm_max_mhz of MEASURED_PEAKS)" % sm_max,
             "kernel_ms": 1e3 * t,
             "traffic": SIM_NCU["dram_bytes_per_4096"] * C / 4096 if fresh else None,
+            "dram_gbs": SIM_NCU["dram_bytes_per_4096"] * C / 4096 / t / 1e9 if fresh and t > 0 else None,
             "traffic_note": "DRAM bytes per launch from one ncu capture of 4,096 candidates, scaled by candidates; "
                             "all of it is per-candidate arena state (algorithmic I/O is 120 B in + 20 B out per "
                             "candidate)",
