@@ -855,10 +855,23 @@ def run_solver(args):
                 "first_local_optimum": first_opt,
                 "time_to_random_best_s": lg.time_to_reach(rlog.best[-1])}
             torch.cuda.synchronize()
+    # the solver over partition factors (p = 1/k, k in 1..4) on 8 x 8 tiles of 3072
+    fb = W.FACTOR_B
+    for mode, mname in ((hesp.SOLVER_ALL, "all"), (hesp.SOLVER_CP, "cp")):
+        sv = S.IterativeSolver(spec, n, fb, W.FACTOR_MAX, mode, hesp.PICK_HARD, factors=True)
+        lg = S.iterative_search(spec, n, fb, W.FACTOR_MAX, mode, hesp.PICK_HARD, seed=6, budget_s=B, solver=sv,
+                                first=np.ones(120, np.int8))
+        arms["factors_%s_hard" % mname] = {
+            "best": lg.best[-1], "candidates_simulated": lg.simulated[-1], "task_events": lg.events[-1],
+            "iterations": len(lg.best), "restarts": len(lg.metrics),
+            "first_local_optimum": lg.metrics[0] if lg.metrics else None,
+            "best_after_first_iteration": lg.best[0] if lg.best else None}
+        torch.cuda.synchronize()
     line = {"metric": "best makespan in %.0f s per arm, iterative solver policies vs plain search" % B,
             "unit": "ns", "higher_is_better": False, "n_gpus": 1,
             "workload": "8x8 tiles, b=2048, levels 0..2, 12 CPU + 1 GPU-type processors; solver arms start "
-                        "from the unsplit partition", "arms": arms}
+                        "from the unsplit partition; factors_* arms: the solver over partition factors "
+                        "k in 1..4 (p = 1/k) on 8x8 tiles of b=3072", "arms": arms}
     print(json.dumps(line))
 
 
