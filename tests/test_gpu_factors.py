@@ -168,3 +168,17 @@ def test_bad_candidates_get_status():
     hesp.simulate_factors(plat, cands, d_f, 0, n, 4, 3072, ws)
     with pytest.raises(hesp.HespError):
         hesp.simulate_factors(plat, cands, d_f, 1, n, 5, 3072, ws)
+
+
+@pytest.mark.parametrize("order,select,cache", [(0, 0, 0), (1, 0, 1)])
+def test_32x32_tiles_with_schedules(order, select, cache):
+    """The search workload's size: 32 x 32 tiles (5,984 base tasks, ~140,000
+    tasks per candidate) with factors 1..4 on 32 CPU + 2 GPU-type
+    processors (two accelerator memories, more than 32 processors), full
+    schedules against the oracle."""
+    spec = W.PLATFORMS["cfg4"]
+    n, b = 32, 3072
+    f = W.uniform_factors(13 + order, 0, 2, W.base_count(n), 4)
+    plat = hesp.Platform(spec, order=order, select=select, cache=cache)
+    pl = O.make_platform(spec, order, select, cache=cache)
+    check(pl, n, b, f, gpu_factors(plat, n, b, f))
