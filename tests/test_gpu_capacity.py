@@ -142,3 +142,25 @@ def test_refused_combinations():
         hesp.simulate_factors(plat, cands, torch.ones_like(lv), 1, n, 4, 3072, hesp.alloc_workspace_factors(plat, n, 4, 1))
     with pytest.raises(hesp.HespError):
         hesp.Platform(spec, capacity={0: 64 * MB})  # host memory is unbounded
+
+
+def test_capacity_workload_full_launch_sampled():
+    """The benchmark's finite-memory launch: 65,536 candidates of 8 x 8 tiles
+    on 12 CPU + 1 GPU-type with 256 MB of GPU memory; every 512th candidate
+    against the oracle."""
+    n, b, C = 8, 2048, 65536
+    nb = W.base_count(n)
+    plat = hesp.Platform(W.PLATFORMS["cfg1a"], capacity={1: 256 * MB})
+    cands = torch.empty(C * 16, dtype=torch.uint8, device="cuda")
+    levels = torch.empty(C * nb, dtype=torch.int8, device="cuda")
+    hesp.generate_candidates(hesp.GEN_UNIFORM, 1, 0, C, n, b, 3, levels, cands)
+    ms, st, nt = hesp.simulate_batch(plat, cands, levels, C, n, 2, hesp.alloc_workspace(plat, n, 2, C),
+                                     ntasks=torch.empty(C, dtype=torch.int64, device="cuda"))
+    torch.cuda.synchronize()
+    ms, st, nt = ms.cpu().numpy(), st.cpu().numpy(), nt.cpu().numpy()
+    assert (st == 0).all()
+    lv = W.uniform_levels(1, 0, C, nb, 3)
+    pl = O.make_platform(W.PLATFORMS["cfg1a"], capacity={1: 256 * MB})
+    for c in range(0, C, 512):
+        r = O.simulate(pl, n, b, lv[c], schedule=False)
+        assert ms[c] == r["makespan"] and nt[c] == r["n_tasks"], c

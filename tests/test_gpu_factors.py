@@ -73,17 +73,17 @@ def test_random_factors_parity(key, n):
 
 
 def test_full_size_workload_sampled():
-    """The benchmark's workload (8 x 8 tiles of 3072, factors uniform in
-    1..4) at 4,096 candidates on both platforms; every 64th against the
-    oracle, with its schedule."""
-    n, b, C = W.FACTOR_N, W.FACTOR_B, 4096
-    f = W.uniform_factors(7, 0, C, W.base_count(n), W.FACTOR_MAX)
+    """The benchmark's launch (65,536 candidates of 8 x 8 tiles of 3072,
+    factors uniform in 1..4, seed 9) on both platforms; every 1,024th
+    against the oracle."""
+    n, b, C = W.FACTOR_N, W.FACTOR_B, 65536
+    f = W.uniform_factors(9, 0, C, W.base_count(n), W.FACTOR_MAX)
     for key in ("cfg1a", "cfg1b"):
         spec = W.PLATFORMS[key]
         g = gpu_factors(hesp.Platform(spec), n, b, f, schedule=False)
         assert (g["status"] == 0).all()
         pl = O.make_platform(spec)
-        for c in range(0, C, 64):
+        for c in range(0, C, 1024):
             r = O.simulate_factors(pl, n, b, f[c], schedule=False)
             assert g["makespan"][c] == r["makespan"] and g["ntasks"][c] == r["n_tasks"], (key, c)
 
