@@ -26,9 +26,13 @@ int64_t regions_uniform(int64_t n, int level) {
 
 static int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
 
-Arena arena_offsets(Arena a, int32_t n_mem);
+Arena arena_offsets(Arena a, int32_t n_mem, unsigned room);
 
-Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem, int64_t task_cap) {
+unsigned arena_room_of(const hesp_platform *p) {
+    return (p->order == HESP_ORDER_PL ? kRoomPL : 0u) | (p->use_cap ? kRoomCap : 0u);
+}
+
+Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem, int64_t task_cap, unsigned room) {
     Arena a;
     memset(&a, 0, sizeof a);
     const int64_t tb = tasks_uniform(max_tiles, max_level), eb = regions_uniform(max_tiles, max_level);
@@ -38,19 +42,23 @@ Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem, int64_t ta
     a.Ecap = task_cap > 0 && 4 * a.Tcap < eb ? 4 * a.Tcap : eb;
     a.Acap = ((int64_t)max_tiles * (max_tiles + 1) / 2) << (2 * max_level);
     a.Kcap = (3LL << (2 * max_level)) + 1;
-    return arena_offsets(a, n_mem);
+    return arena_offsets(a, n_mem, room);
 }
 
-// Offsets of the arena areas for the capacities in a.
-Arena arena_offsets(Arena a, int32_t n_mem) {
+// Offsets of the arena areas for the capacities in a.  The link area holds,
+// one after the other in time, the edge list of the dependence build (4
+// bytes per edge), the FIFO records of the event loop (16 bytes per task),
+// or the four per-task words of the priority-list order (32 bytes per task,
+// only with kRoomPL) and the two of the critical-path pass (16).
+Arena arena_offsets(Arena a, int32_t n_mem, unsigned room) {
     const int64_t mp = n_mem <= 1 ? 0 : (n_mem == 2 ? 2 : 4);  // int64 words of coherence state per atom
-    const int64_t link_bytes = 32 * a.Tcap > 8 * a.Ecap ? 32 * a.Tcap : 8 * a.Ecap;
+    const int64_t per_task = (room & kRoomPL) ? 32 : 16;
+    const int64_t link_bytes = per_task * a.Tcap > 4 * a.Ecap ? per_task * a.Tcap : 4 * a.Ecap;
     int64_t o = 0;
     a.off_desc = o; o = align256(o + 8 * a.Tcap);
     a.off_pending = o; o = align256(o + 2 * a.Tcap);
     a.off_link = o; o = align256(o + link_bytes);
     a.off_epred = a.off_link;
-    a.off_esucc = a.off_link + 4 * a.Ecap;
     a.off_next = o; o = align256(o + 4 * a.Tcap);
     a.off_succoff = o; o = align256(o + 4 * (a.Tcap + 1));
     a.off_succ = o; o = align256(o + 4 * a.Ecap);
@@ -59,9 +67,11 @@ Arena arena_offsets(Arena a, int32_t n_mem) {
     a.off_bitmap = o; o = align256(o + 4 * ((a.Tcap + 31) / 32));
     a.off_xt = o; o = align256(o + 8 * a.Kcap * (n_mem > 1 ? HESP_MAX_MEMS * HESP_MAX_MEMS : 1));  // per link
     a.off_hist = o; o = align256(o + 4 * 256);  // radix histogram of the priority-list sort
-    a.off_pend0 = o; o = align256(o + 2 * a.Tcap);  // keep / reuse: the DAG's initial pending counts
-    a.off_hdr = o; o = align256(o + 64);            // keep / reuse: the candidate's header
-    a.off_use = o; o = align256(o + 8 * a.Acap * mp);  // finite memories: last use per atom and memory
+    // keep / reuse: the DAG's initial pending counts and the candidate's header
+    a.off_pend0 = o; o = align256(o + ((room & kRoomKept) ? 2 * a.Tcap : 0));
+    a.off_hdr = o; o = align256(o + ((room & kRoomKept) ? 64 : 0));
+    // finite memories: last use per atom and memory
+    a.off_use = o; o = align256(o + ((room & kRoomCap) ? 8 * a.Acap * mp : 0));
     a.slot_bytes = o;
     return a;
 }
@@ -85,7 +95,7 @@ int32_t factor_lcm(int32_t max_factor) {
 // tasks of every base task cut max_factor ways, atoms of side b / lcm(1 ..
 // max_factor), edges up to 16 per task (a larger DAG reports
 // HESP_ERR_CAPACITY).
-Arena make_arena_factors(int32_t max_tiles, int32_t max_factor, int32_t n_mem, int64_t task_cap) {
+Arena make_arena_factors(int32_t max_tiles, int32_t max_factor, int32_t n_mem, int64_t task_cap, unsigned room) {
     Arena a;
     memset(&a, 0, sizeof a);
     const int64_t n = max_tiles, k = max_factor;
@@ -96,7 +106,7 @@ Arena make_arena_factors(int32_t max_tiles, int32_t max_factor, int32_t n_mem, i
     const int64_t L = factor_lcm(max_factor);
     a.Acap = n * (n + 1) / 2 * L * L;
     a.Kcap = 3 * L * L + 1;
-    return arena_offsets(a, n_mem);
+    return arena_offsets(a, n_mem, room);
 }
 
 static DevPlatform dev_platform(const hesp_platform *p) {
@@ -432,7 +442,7 @@ int hesp_sim_workspace_size(const hesp_platform *p, int32_t max_tiles, int32_t m
     if (!p || !bytes_out || n_cand < 0 || task_cap < 0) return HESP_ERR_ARG;
     if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_level < 0 || max_level > HESP_MAX_LEVEL)
         return HESP_ERR_UNSUPPORTED;
-    const Arena ar = make_arena(max_tiles, max_level, p->n_mem, task_cap);
+    const Arena ar = make_arena(max_tiles, max_level, p->n_mem, task_cap, arena_room_of(p));
     int64_t resident = 0;
     const int rc = sim_slots_for(p, ar, &resident);
     if (rc) return rc;
@@ -458,7 +468,7 @@ int simulate_common(const hesp_platform *p, const hesp_cand *cands, const int8_t
     if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_level < 0 || max_level > HESP_MAX_LEVEL)
         return HESP_ERR_UNSUPPORTED;
     if (p->use_cap && p->select >= HESP_SELECT_FP) return HESP_ERR_ARG;  // finite memories: EFT-P / EIT-P
-    const Arena ar = make_arena(max_tiles, max_level, p->n_mem, task_cap);
+    const Arena ar = make_arena(max_tiles, max_level, p->n_mem, task_cap, arena_room_of(p));
     if ((int64_t)ws_bytes < kWsHeaderBytes + ar.slot_bytes) return HESP_ERR_ARG;
     int64_t resident = 0;
     int rc = sim_slots_for(p, ar, &resident);
@@ -494,7 +504,7 @@ int simulate_kept(const hesp_platform *p, const hesp_cand *cands, const int8_t *
     if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_level < 0 || max_level > HESP_MAX_LEVEL)
         return HESP_ERR_UNSUPPORTED;
     if (p->use_cap && p->select >= HESP_SELECT_FP) return HESP_ERR_ARG;  // finite memories: EFT-P / EIT-P
-    const Arena ar = make_arena(max_tiles, max_level, HESP_MAX_MEMS, task_cap);
+    const Arena ar = make_arena(max_tiles, max_level, HESP_MAX_MEMS, task_cap, kRoomAll);
     if ((int64_t)ws_bytes < kWsHeaderBytes || ((int64_t)ws_bytes - kWsHeaderBytes) / ar.slot_bytes < n_cand)
         return HESP_ERR_ARG;
     int64_t resident = 0;
@@ -523,7 +533,7 @@ int hesp_sim_workspace_size_factors(const hesp_platform *p, int32_t max_tiles, i
     if (!p || !bytes_out || n_cand < 0 || task_cap < 0) return HESP_ERR_ARG;
     if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_factor < 1 || max_factor > HESP_MAX_FACTOR)
         return HESP_ERR_UNSUPPORTED;
-    const Arena ar = make_arena_factors(max_tiles, max_factor, p->n_mem, task_cap);
+    const Arena ar = make_arena_factors(max_tiles, max_factor, p->n_mem, task_cap, arena_room_of(p));
     int64_t resident = 0;
     const int rc = sim_slots_for(p, ar, &resident);
     if (rc) return rc;
@@ -548,7 +558,7 @@ int hesp_simulate_factors(const hesp_platform *p, const hesp_cand *cands, const 
     if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_factor < 1 || max_factor > HESP_MAX_FACTOR ||
         b > (1 << HESP_MAX_LOG2_BLOCK))
         return HESP_ERR_UNSUPPORTED;
-    const Arena ar = make_arena_factors(max_tiles, max_factor, p->n_mem, task_cap);
+    const Arena ar = make_arena_factors(max_tiles, max_factor, p->n_mem, task_cap, arena_room_of(p));
     if ((int64_t)ws_bytes < kWsHeaderBytes + ar.slot_bytes) return HESP_ERR_ARG;
     int64_t resident = 0;
     int rc = sim_slots_for(p, ar, &resident);
@@ -578,7 +588,7 @@ int hesp_sim_workspace_size_kept(int32_t max_tiles, int32_t max_level, int64_t t
     if (!bytes_out || n_cand < 0 || task_cap < 0) return HESP_ERR_ARG;
     if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_level < 0 || max_level > HESP_MAX_LEVEL)
         return HESP_ERR_UNSUPPORTED;
-    const Arena ar = make_arena(max_tiles, max_level, HESP_MAX_MEMS, task_cap);
+    const Arena ar = make_arena(max_tiles, max_level, HESP_MAX_MEMS, task_cap, kRoomAll);
     *bytes_out = (size_t)(kWsHeaderBytes + n_cand * ar.slot_bytes);
     return HESP_OK;
 }
@@ -591,7 +601,7 @@ int hesp_dag_build_kept(const hesp_cand *cands, const int8_t *levels, int64_t n_
     if (!cands || !levels || !status || !ws || ((uintptr_t)ws & 255) != 0) return HESP_ERR_ARG;
     if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_level < 0 || max_level > HESP_MAX_LEVEL)
         return HESP_ERR_UNSUPPORTED;
-    const Arena ar = make_arena(max_tiles, max_level, HESP_MAX_MEMS, task_cap);
+    const Arena ar = make_arena(max_tiles, max_level, HESP_MAX_MEMS, task_cap, kRoomAll);
     if ((int64_t)ws_bytes < kWsHeaderBytes || ((int64_t)ws_bytes - kWsHeaderBytes) / ar.slot_bytes < n_cand)
         return HESP_ERR_ARG;
     return launch_build(ar, cands, levels, n_cand, max_tiles, max_level, ntasks, status,

@@ -526,30 +526,41 @@ int make_level_map(CUtensorMap *tm, const int8_t *ptr, int64_t rows, int64_t n_b
     return r == CUDA_SUCCESS ? HESP_OK : HESP_ERR_ARG;
 }
 
-int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
-                                                      cudaSuccess)
-            n = 148;
+// Per-device launch state: the SM count and, per one-hot variant NL, whether
+// the kernel's dynamic shared-memory limit has been raised on that device
+// (a function attribute is per device).  Guarded by one mutex.
+constexpr int kMaxDevices = 64;
+std::mutex g_dev_mu;
+int g_sms[kMaxDevices] = {0};
+bool g_attr_set[kMaxDevices][6] = {{false}};
+
+template <int NL>
+int prepare_device(int *sms) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HESP_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (g_sms[dev] == 0 &&
+        cudaDeviceGetAttribute(&g_sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return HESP_ERR_CUDA;
+    if (!g_attr_set[dev][NL]) {
+        if (cudaFuncSetAttribute(gemm_bf16_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_bytes_of(NL)) != cudaSuccess)
+            return HESP_ERR_CUDA;
+        g_attr_set[dev][NL] = true;
     }
-    return n;
+    *sms = g_sms[dev];
+    return HESP_OK;
 }
 
 template <int NL>
 int launch_persistent(const CUtensorMap &ta, const CUtensorMap &tb, const CUtensorMap &tl, const GemmArgs &g,
                       cudaStream_t st) {
     constexpr int SMEM = smem_bytes_of(NL);
-    static bool attr_set = false;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(gemm_bf16_kernel<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) !=
-            cudaSuccess)
-            return HESP_ERR_CUDA;
-        attr_set = true;
-    }
+    int sms = 0;
+    const int rc = prepare_device<NL>(&sms);
+    if (rc) return rc;
     const int64_t tiles = (int64_t)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
-    const int64_t grid = tiles < sm_count() ? tiles : sm_count();
+    const int64_t grid = tiles < sms ? tiles : sms;
     gemm_bf16_kernel<NL><<<(unsigned)grid, NL > 0 ? 320 + 128 * N_PROD_GROUPS : 320, SMEM, st>>>(ta, tb, tl, g);
     return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
 }

@@ -86,12 +86,21 @@ struct Arena {
     int64_t Ecap;  // dependence edges
     int64_t Acap;  // atoms
     int64_t Kcap;  // transfer-table entries (atoms per task + 1)
-    // The edge lists of the dependence build (epred, esucc) live in the FIFO
-    // link area and the per-task marks in the successor offsets: neither is
-    // in use at the same time as what it shares memory with.
-    int64_t off_desc, off_pending, off_link, off_next, off_succoff, off_succ, off_epred, off_esucc, off_lw,
-        off_vfrom, off_bitmap, off_xt, off_hist, off_pend0, off_hdr, off_use;
+    // The edge list of the dependence build (epred: the predecessor of each
+    // edge, grouped by successor) lives in the FIFO link area and the
+    // per-task marks in the successor offsets: neither is in use at the same
+    // time as what it shares memory with.
+    int64_t off_desc, off_pending, off_link, off_next, off_succoff, off_succ, off_epred, off_lw, off_vfrom,
+        off_bitmap, off_xt, off_hist, off_pend0, off_hdr, off_use;
 };
+
+// Optional areas of an arena (the `room` flags of make_arena): a launch
+// only touches the areas its platform and mode need, so a workspace sized
+// without them holds more concurrent candidates.
+constexpr unsigned kRoomPL = 1;    // priority-list order: 32 bytes per task in the link area (else 16)
+constexpr unsigned kRoomKept = 2;  // keep / reuse: the initial pending counts and the candidate header
+constexpr unsigned kRoomCap = 4;   // finite memories: the last use of every atom per memory
+constexpr unsigned kRoomAll = kRoomPL | kRoomKept | kRoomCap;
 
 // Header at the start of the workspace.
 struct WsHeader {
@@ -103,8 +112,9 @@ constexpr int64_t kWsHeaderBytes = 256;
 // Closed forms used to size arenas (host side).
 int64_t tasks_uniform(int64_t n, int level);  // tasks when every base task is split `level` times
 int64_t regions_uniform(int64_t n, int level); // sum over those tasks of their region count
-Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem, int64_t task_cap);
-Arena make_arena_factors(int32_t max_tiles, int32_t max_factor, int32_t n_mem, int64_t task_cap);
+Arena make_arena(int32_t max_tiles, int32_t max_level, int32_t n_mem, int64_t task_cap, unsigned room);
+Arena make_arena_factors(int32_t max_tiles, int32_t max_factor, int32_t n_mem, int64_t task_cap, unsigned room);
+unsigned arena_room_of(const hesp_platform *p);  // the optional areas a platform's launches use
 
 int sim_slots_for(const hesp_platform *p, const Arena &ar, int64_t *resident_warps);  // device resident warps
 int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, int64_t n_slots,

@@ -53,7 +53,7 @@ extern "C" int hesp_simulate_batch_noalloc(const hesp_platform *p, const hesp_ca
     if (max_tiles < 1 || max_tiles > HESP_MAX_TILES || max_level < 0 || max_level > HESP_MAX_LEVEL)
         return HESP_ERR_UNSUPPORTED;
     // One candidate arena (plus the work-counter header) must fit the array.
-    const hesp::Arena ar = hesp::make_arena(max_tiles, max_level, p->n_mem, 0);
+    const hesp::Arena ar = hesp::make_arena(max_tiles, max_level, p->n_mem, 0, hesp::arena_room_of(p));
     if (hesp::kWsHeaderBytes + ar.slot_bytes > (int64_t)HESP_NOALLOC_SCRATCH_BYTES) return HESP_ERR_CAPACITY;
     if (n_cand == 0) return HESP_OK;
     void *scratch = nullptr;

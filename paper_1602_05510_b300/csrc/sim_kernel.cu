@@ -1087,8 +1087,10 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
             int32_t *const lw = at<int32_t>(base, a.ar.off_lw);
             int32_t *const mark = at<int32_t>(base, a.ar.off_succoff);  // offsets are built after this phase
             int32_t *const scnt = at<int32_t>(base, a.ar.off_next);
+            // edges are appended grouped by successor, in creation order; only
+            // the predecessor is stored (the successor is recovered from the
+            // per-task counts when the successor lists are built)
             int32_t *const epred = at<int32_t>(base, a.ar.off_epred);
-            int32_t *const esucc = at<int32_t>(base, a.ar.off_esucc);
             uint16_t *const pending = at<uint16_t>(base, a.ar.off_pending);
             for (int64_t x = lane; x < A; x += 32) lw[x] = -1;
             for (int64_t j = lane; j < T; j += 32) {
@@ -1164,10 +1166,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     const unsigned em = __ballot_sync(FULL, emit);
                     if (emit) {
                         const int64_t e = E + __popc(em & lt_mask);
-                        if (e < a.ar.Ecap) {
-                            epred[e] = pred;
-                            esucc[e] = j0 + ob;
-                        }
+                        if (e < a.ar.Ecap) epred[e] = pred;
                         atomicAdd(&scnt[pred], 1);
                     }
                     E += __popc(em);
@@ -1208,10 +1207,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     const unsigned nm = __ballot_sync(FULL, isnew);
                     if (isnew) {
                         const int64_t e = E + cnt + __popc(nm & lt_mask);
-                        if (e < a.ar.Ecap) {
-                            epred[e] = w;
-                            esucc[e] = j;
-                        }
+                        if (e < a.ar.Ecap) epred[e] = w;
                         atomicAdd(&scnt[w], 1);
                     }
                     cnt += __popc(nm);
@@ -1229,13 +1225,15 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
             if (E > a.ar.Ecap) status = HESP_ERR_CAPACITY;
         }
 
-        // ---- 3. successor lists (CSR)
+        // ---- 3. successor lists (CSR).  The sweep appended pending[j] edges
+        // for task j, in creation order, so edge e belongs to the successor
+        // whose prefix range of those counts holds e.
         if (!reuse && status == HESP_OK) {
             int32_t *const scnt = at<int32_t>(base, a.ar.off_next);
             int32_t *const succoff = at<int32_t>(base, a.ar.off_succoff);
             int32_t *const succ = at<int32_t>(base, a.ar.off_succ);
             const int32_t *const epred = at<int32_t>(base, a.ar.off_epred);
-            const int32_t *const esucc = at<int32_t>(base, a.ar.off_esucc);
+            const uint16_t *const npred = at<uint16_t>(base, a.ar.off_pending);
             int run = 0;
             for (int64_t j0 = 0; j0 < T; j0 += 32) {
                 const int64_t j = j0 + lane;
@@ -1249,9 +1247,27 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
             }
             if (lane == 0) succoff[T] = run;
             __syncwarp();
-            for (int64_t e = lane; e < E; e += 32) {
-                const int pos = atomicAdd(&scnt[epred[e]], 1);
-                succ[pos] = esucc[e];
+            int erun = 0;
+            for (int64_t j0 = 0; j0 < T; j0 += 32) {
+                const int64_t j = j0 + lane;
+                const int k = j < T ? (int)npred[j] : 0;
+                const int incl = warp_incl_scan(k, lane);
+                const int total = __shfl_sync(FULL, incl, 31);
+                for (int g0 = 0; g0 < total; g0 += 32) {
+                    const int g = g0 + lane;
+                    // successor lane = first lane whose inclusive count exceeds g
+                    int pos = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int v = __shfl_sync(FULL, incl, pos + step - 1);
+                        if (v <= g) pos += step;
+                    }
+                    if (g < total) {
+                        const int q = atomicAdd(&scnt[epred[erun + g]], 1);
+                        succ[q] = (int)j0 + pos;
+                    }
+                }
+                erun += total;
             }
             __syncwarp();
         }
@@ -1548,6 +1564,8 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                             nz &= nz - 1;
                             uint32_t wb = __shfl_sync(FULL, bits, src);
                             const int jb = (w0 + src) * 32;
+                            // the descriptors of the word's released tasks, one per lane, in one round trip
+                            const uint64_t dw = ((wb >> lane) & 1u) ? desc[jb + lane] : 0ull;
                             while (wb) {
                                 const int bit = __ffs(wb) - 1;
                                 wb &= wb - 1;
@@ -1556,7 +1574,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                                     ++qt;
                                     continue;
                                 }
-                                schedule_task<M, NS, true, GEN, CAP>(jb + bit, desc[jb + bit], t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype,
+                                schedule_task<M, NS, true, GEN, CAP>(jb + bit, __shfl_sync(FULL, dw, bit), t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype,
                                                            pm, pt, pv, avail, head, tail, hfin, mk, ok, sched_base,
                                                            sel, rp_seed, cache, links, cs, capfail);
                                 ++scheduled;
@@ -1618,11 +1636,14 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                             const int e = e0 + lane;
                             if (e < e1) {
                                 const int sj = succ[e];
+                                // the descriptor is read beside the count (one
+                                // round trip instead of two for a released task)
+                                const uint64_t dsj = desc[sj];
                                 const int pvv = (int)pending[sj] - 1;
                                 pending[sj] = (uint16_t)pvv;
                                 if (pvv == 0) {
                                     dj = sj;
-                                    djd = desc[sj];
+                                    djd = dsj;
                                 }
                             }
                             direct = true;

@@ -83,3 +83,76 @@ def test_gemm_rejects_bad_shapes():
     C = torch.zeros((128, 128), dtype=torch.float32, device="cuda")
     with pytest.raises(hesp.HespError):
         hesp.gemm_bf16(a, a, hesp.GEMM_F32, C=C)   # K = 100 not a multiple of 64
+
+
+# The persistent kernel runs min(tiles, SMs) CTAs, each walking output tiles
+# of 128 x 256; these shapes give every CTA several tiles (both TMEM
+# accumulators, the epilogue of one tile under the next tile's main loop, and
+# the mbarrier phases carried across tiles): 65,536 x 512 is 1,024 tiles (the
+# surrogate's inference chunk, K = 2,496 for the 816-task one-hot layer and
+# K = 512 for layer 2); 512 x 23,936 with K = 512 is 376 tiles (the
+# weight-gradient GEMM dW1 = dZ1^T X of the 5,984-task, 4-level first layer);
+# 40,000 x 640 is ragged in both M and N.
+MULTI = [(65536, 512, 2496), (65536, 512, 512), (512, 23936, 512), (40000, 640, 256)]
+
+
+def _ref64(A, B):
+    return torch.from_numpy(A).double() @ torch.from_numpy(B).double().T
+
+
+def _absbound(A, B):
+    return torch.from_numpy(np.abs(A)).double() @ torch.from_numpy(np.abs(B)).double().T
+
+
+@pytest.mark.parametrize("M,N,K", MULTI)
+def test_gemm_f32_multi_tile(M, N, K):
+    rng = np.random.default_rng(M + 3 * N + K)
+    A, B = rand_bf16((M, K), rng).astype(np.float32), rand_bf16((N, K), rng).astype(np.float32)
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    hesp.gemm_bf16(dev(A), dev(B), hesp.GEMM_F32, C=C, err=err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    ref = _ref64(A, B)
+    bound = _absbound(A, B)
+    got = C.cpu().double()
+    # every element: fp32 accumulation over K of exact bf16 products
+    assert bool(torch.all((got - ref).abs() <= 1e-5 * np.sqrt(K) * (bound + 1e-3)))
+
+
+@pytest.mark.parametrize("M,N,K", MULTI[:2] + MULTI[3:])
+def test_gemm_bias_relu_multi_tile(M, N, K):
+    rng = np.random.default_rng(11 + M + N)
+    A, B = rand_bf16((M, K), rng).astype(np.float32), rand_bf16((N, K), rng).astype(np.float32)
+    bias = rng.standard_normal(N).astype(np.float32)
+    out = torch.zeros((M, N), dtype=torch.bfloat16, device="cuda")
+    out_t = torch.zeros((N, M), dtype=torch.bfloat16, device="cuda")
+    hesp.gemm_bf16(dev(A), dev(B), hesp.GEMM_BIAS_RELU, bias=torch.from_numpy(bias).cuda(), out=out, out_t=out_t)
+    torch.cuda.synchronize()
+    ref = torch.clamp(_ref64(A, B) + torch.from_numpy(bias).double(), min=0)
+    got = out.cpu().double()
+    assert torch.equal(out.cpu(), out_t.cpu().T)
+    # got = bf16(relu(s)) with s the fp32 sum, |s - exact| <= e (the bound of
+    # the fp32 test); relu is 1-Lipschitz and the bf16 rounding moves a value
+    # by at most 2^-8 of it, so |got - ref| <= 2^-8 (|ref| + e) + e
+    e = 1e-5 * np.sqrt(K) * (_absbound(A, B) + torch.from_numpy(np.abs(bias).astype(np.float64))[None, :] + 1e-3)
+    assert bool(torch.all((got - ref).abs() <= 2 ** -7 * ref.abs() + 2 * e))
+    assert float((got == torch.from_numpy(bf16_round(ref.numpy()))).double().mean()) > 0.98
+
+
+def test_gemm_mask_multi_tile():
+    rng = np.random.default_rng(5)
+    M, N, K = 65536, 512, 512
+    A, B = rand_bf16((M, K), rng).astype(np.float32), rand_bf16((N, K), rng).astype(np.float32)
+    mask = bf16_round(rng.standard_normal((M, N))).astype(np.float32)
+    out = torch.zeros((M, N), dtype=torch.bfloat16, device="cuda")
+    out_t = torch.zeros((N, M), dtype=torch.bfloat16, device="cuda")
+    hesp.gemm_bf16(dev(A), dev(B), hesp.GEMM_MASK, mask=dev(mask), out=out, out_t=out_t)
+    torch.cuda.synchronize()
+    keep = torch.from_numpy(mask > 0)
+    ref = _ref64(A, B) * keep
+    got = out.cpu().double()
+    assert torch.equal(out.cpu(), out_t.cpu().T)
+    e = 1e-5 * np.sqrt(K) * (_absbound(A, B) + 1e-3)
+    assert bool(torch.all((got - ref).abs() <= 2 ** -7 * ref.abs() + 2 * e))
+    assert bool(torch.all(got[~keep] == 0))

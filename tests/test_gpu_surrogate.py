@@ -216,3 +216,93 @@ def test_checkpoint_roundtrip_and_resume(tmp_path):
         open(p2, "wb").write(bad)
         with pytest.raises(hesp.HespError):
             hesp.Surrogate.load(p2)
+
+
+def _ref_forward_rows(ref, lv, NL, Fp, chunk=2048):
+    """The FP64 reference forward over many rows, in row chunks (the dense
+    one-hot matrix of every row at once would not fit): y, and per row the
+    bound sum_h |w3_h| |A2_bh| used by the element-wise tolerance."""
+    ys, bs = [], []
+    for i in range(0, lv.shape[0], chunk):
+        f = ref.forward(R.one_hot(lv[i:i + chunk], NL, Fp))
+        ys.append(f["y"])
+        bs.append(np.abs(f["A2"]) @ np.abs(ref.w3))
+    return np.concatenate(ys), np.concatenate(bs)
+
+
+# Inference chunks large enough that the persistent layer-1 and layer-2 GEMMs
+# run several 128 x 256 tiles per CTA: 65,536 rows of the 816-task, 3-level
+# input (1,024 tiles per layer) and 40,960 rows of the 5,984-task, 4-level
+# input (23,936 features, 640 tiles).
+@pytest.mark.parametrize("T,NL,M", [(816, 3, 65536), (5984, 4, 40960)])
+def test_infer_elementwise_multi_tile(T, NL, M):
+    rng = np.random.default_rng(T + M)
+    H = 512
+    s = hesp.Surrogate(T, NL, H, max_batch=M, seed=13)
+    p = W.surrogate_init(13, T * NL, s.Fp, H)
+    p["b1"] = (rng.standard_normal(H) * 0.1).astype(np.float32)
+    p["b2"] = (rng.standard_normal(H) * 0.1).astype(np.float32)
+    p["b3"] = np.array([0.05], np.float32)
+    s.set(p)
+    lv = rng.integers(0, NL, (M, T)).astype(np.int8)
+    pred = torch.full((M,), float("nan"), dtype=torch.float32, device="cuda")
+    s.infer(torch.from_numpy(lv.reshape(-1).copy()).cuda(), M, pred)
+    torch.cuda.synchronize()
+    assert s.error_flag() == 0
+    ref = R.MLPRef(p["W1"], p["b1"], p["W2"], p["b2"], p["w3"], float(p["b3"][0]))
+    y, bound = _ref_forward_rows(ref, lv, NL, s.Fp)
+    got = pred.cpu().numpy().astype(np.float64)
+    # per row: FP32 sums may move a bf16 rounding of A1 or A2 by one step
+    # (2^-7 relative at most), so |dy| <= 2^-7 sum_h |w3_h| |A2_h|, plus the
+    # FP32 error of the last dot product
+    tol = 2.0 ** -7 * bound + 1e-5 * np.maximum(1.0, np.abs(y))
+    assert np.all(np.abs(got - y) <= tol), float(np.max(np.abs(got - y) / tol))
+
+
+def test_grad_elementwise_multi_tile_5984_tasks():
+    """Forward and backward of the 5,984-task, 4-level surrogate on a batch
+    of 512: the weight gradient dW1 = dZ1^T X is a 512 x 23,936 GEMM of 376
+    output tiles.  Biases keep every ReLU clearly active (checked below), so
+    the masks agree with the reference and each bf16-rounded backward
+    activation dZ1 is within one bf16 step (2^-7 relative) of the
+    reference's; every element of dW1 must then lie within
+    2^-6 sum_b |dZ1_bh| X_bf of the FP64 value."""
+    rng = np.random.default_rng(4)
+    T, NL, H, B = 5984, 4, 512, 512
+    s = hesp.Surrogate(T, NL, H, max_batch=B, seed=21)
+    p = W.surrogate_init(21, T * NL, s.Fp, H)
+    p["b1"] = np.full(H, 6.0, np.float32)
+    p["b2"] = np.full(H, 60.0, np.float32)
+    p["b3"] = np.array([0.1], np.float32)
+    s.set(p)
+    s.set_stats(20.4, 0.25)
+    lv, ms = batch(rng, B, T, NL)
+    pred = torch.empty(B, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    s.grad(torch.from_numpy(lv.reshape(-1).copy()).cuda(), torch.from_numpy(ms).cuda(), B, pred, loss)
+    torch.cuda.synchronize()
+    assert s.error_flag() == 0
+    g = s.get(1)
+    ref = R.MLPRef(p["W1"], p["b1"], p["W2"], p["b2"], p["w3"], float(p["b3"][0]))
+    X = R.one_hot(lv, NL, s.Fp)
+    f = ref.forward(X)
+    # precondition of the element-wise bound: no pre-activation near the ReLU cut
+    pre1 = X @ f["W1r"].T + ref.b1
+    pre2 = f["A1"] @ f["W2r"].T + ref.b2
+    assert pre1.min() > 1.0 and pre2.min() > 1.0
+    t = (np.log(ms.astype(np.float64)) - 20.4) / 0.25
+    out = ref.backward(X, t)
+    y_gpu = pred.cpu().numpy().astype(np.float64)
+    close(y_gpu, out["y"], rel=2e-3)
+    assert abs(loss.item() - out["loss"]) <= 1e-2 * out["loss"]
+    for k in s.PARTS:
+        close(g[k], out["grads"][k])
+    # The backward pass starts from dy = 2 (y - t) / B; a bf16 step of A2
+    # moves the GPU's y slightly, which would move roundings of dZ2.  Shifting
+    # the targets by y_ref - y_gpu gives the reference the GPU's dy, so dZ2
+    # and dZ1 differ from the GPU's by FP32-vs-FP64 rounding alone.
+    out = ref.backward(X, t + out["y"] - y_gpu)
+    bound = np.abs(out["dZ1"]).T @ X
+    got = np.asarray(g["W1"], np.float64)
+    want = out["grads"]["W1"]
+    assert np.all(np.abs(got - want) <= 2.0 ** -6 * bound + 1e-12), float(np.max(np.abs(got - want) - 2.0 ** -6 * bound))
