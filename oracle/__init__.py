@@ -95,8 +95,43 @@ def _p(a, ct):
 def lib():
     global _lib
     if _lib is None:
-        path = build()
-        L = ctypes.CDLL(path)
+        _lib = _load(build())
+    return _lib
+
+
+def build_variant(source_text: str, out_path: str) -> str:
+    """Compile a variant of the oracle's C source (the tests plant a mistake
+    in a copy of it and check that a pin fails) into out_path."""
+    src = out_path + ".c"
+    with open(src, "w") as f:
+        f.write(source_text)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-w", "-shared", "-fPIC", "-o", out_path, src])
+    return out_path
+
+
+class using_library:
+    """Context in which every oracle call of this module goes to the library
+    at `path` (a variant built by build_variant) instead of liboracle.so."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = lib()
+        _lib = _load(self.path)
+        return _lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def _load(path):
+    """The oracle library at `path` with its argument types declared."""
+    L = ctypes.CDLL(path)
+    if True:  # (one block of declarations)
         i32, i64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
         L.or_exec_ns.restype = i64
         L.or_exec_ns.argtypes = [ctypes.POINTER(Platform), i32, i32, i64]
@@ -127,8 +162,7 @@ def lib():
                                           vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
         L.or_simulate_many.restype = i32
         L.or_simulate_many.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i64, vp, vp, vp]
-        _lib = L
-    return _lib
+    return L
 
 
 ORDER_FCFS, ORDER_PL = 0, 1

@@ -461,3 +461,29 @@ def test_build_apart_then_reuse():
         assert torch.equal(st, st2) and torch.equal(ms, ms2), key
     bst = bst.cpu().numpy()
     assert bst[5] == -1 and (np.delete(bst, 5) == 0).all()
+
+
+def test_pl_hand_derived_schedule_on_gpu():
+    """The hand-derived PL and FCFS schedules of the golden file (3
+    processors of two types in one memory, the syrk of a 2 x 2-tile Cholesky
+    split once; PL and FCFS differ): the GPU reproduces every processor,
+    start and finish of both, from the worked-out values, not from the oracle."""
+    import dataclasses
+    e = GOLD["n2_b1024_syrk_split_pl_vs_fcfs_p3"]
+    spec = dataclasses.replace(W.big_little_platform(), procs=tuple(tuple(p) for p in e["procs"]),
+                               exec_overrides=tuple(tuple(x) for x in e["overrides"]))
+    lv = np.array([e["levels"]], np.int8)
+    for order, want in ((1, e["pl"]), (0, e["fcfs"])):
+        plat = hesp.Platform(spec, order=order, select=0)
+        d_lv = torch.from_numpy(lv.reshape(-1).copy()).cuda()
+        cands = hesp.cands_tensor(e["n"], e["b"], np.zeros(1, np.int64))
+        ws = hesp.alloc_workspace(plat, e["n"], 1, 1)
+        T = len(want["proc"])
+        sched = (torch.zeros(1, dtype=torch.int64, device="cuda"), torch.empty(T, dtype=torch.int16, device="cuda"),
+                 torch.empty(T, dtype=torch.int64, device="cuda"), torch.empty(T, dtype=torch.int64, device="cuda"))
+        ms, st, _ = hesp.simulate_batch(plat, cands, d_lv, 1, e["n"], 1, ws, schedule=sched)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0 and int(ms.item()) == want["makespan"], order
+        assert sched[1].cpu().tolist() == want["proc"], order
+        assert sched[2].cpu().tolist() == want["start"], order
+        assert sched[3].cpu().tolist() == want["finish"], order

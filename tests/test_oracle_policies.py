@@ -404,3 +404,64 @@ def test_link_replay(cache, key, n, b):
         s_, f_ = replay(spec, n, b, lv, o, [int(r["proc"][j]) for j in o], cache=cache, links=links)
         assert [s_[j] for j in range(r["n_tasks"])] == r["start"].tolist()
         assert [f_[j] for j in range(r["n_tasks"])] == r["finish"].tolist()
+
+
+# ---- PL pinned by a schedule worked out by hand (golden file), where PL
+# and FCFS differ, and two mistakes planted in a copy of the oracle's C source
+# (own time counted once per processor type; ties to the higher id), each of
+# which the pin catches.
+
+PLX = GOLD["n2_b1024_syrk_split_pl_vs_fcfs_p3"]
+
+
+def plx_spec():
+    return dataclasses.replace(W.big_little_platform(), procs=tuple(tuple(p) for p in PLX["procs"]),
+                               exec_overrides=tuple(tuple(x) for x in PLX["overrides"]))
+
+
+def plx_run(order):
+    return O.simulate(plat(plx_spec(), order, O.SELECT_EFT), PLX["n"], PLX["b"], PLX["levels"])
+
+
+def plx_matches(r, want):
+    return (r["status"] == 0 and r["makespan"] == want["makespan"] and r["proc"].tolist() == want["proc"]
+            and r["start"].tolist() == want["start"] and r["finish"].tolist() == want["finish"])
+
+
+def test_pl_hand_derived_schedule():
+    r = plx_run(O.ORDER_PL)
+    assert plx_matches(r, PLX["pl"]), (r["proc"], r["start"], r["finish"])
+    assert r["order"].tolist() == PLX["pl_order"]
+    f = plx_run(O.ORDER_FCFS)
+    assert plx_matches(f, PLX["fcfs"]), (f["proc"], f["start"], f["finish"])
+    assert r["proc"].tolist() != f["proc"].tolist()  # the two orders give different schedules
+    # the DAG of the example: predecessors as listed in the golden file
+    code = O.levels_to_code(PLX["n"], PLX["levels"])
+    po, pv, _ = O.deps(PLX["n"], PLX["b"], code, 1, 1)
+    assert [sorted(pv[po[j]:po[j + 1]].tolist()) for j in range(len(po) - 1)] == PLX["predecessors"]
+
+
+def _plant(tmp_path, name, old, new):
+    src = open(os.path.join(os.path.dirname(O.__file__), "hesp_oracle.c")).read()
+    assert src.count(old) == 1, name
+    return O.build_variant(src.replace(old, new), str(tmp_path / ("lib_%s.so" % name)))
+
+
+PL_PLANTS = {
+    # own time summed over processor types instead of processors
+    "per_type": ("for (int p = 0; p < P; p++) w += or_exec_ns(pl, d.t[j].op, pl->proc_type[p], d.t[j].bs);",
+                 "for (int p = 0; p < pl->n_types; p++) w += or_exec_ns(pl, d.t[j].op, p, d.t[j].bs);"),
+    # equal critical times ordered by decreasing id
+    "tie_high": ("    return i < j ? -1 : (i > j);\n}", "    return i > j ? -1 : (i < j);\n}"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PL_PLANTS))
+def test_pl_pin_catches_planted_mistake(tmp_path, name):
+    path = _plant(tmp_path, name, *PL_PLANTS[name])
+    with O.using_library(path):
+        r = plx_run(O.ORDER_PL)
+        f = plx_run(O.ORDER_FCFS)
+    assert not plx_matches(r, PLX["pl"])
+    assert plx_matches(f, PLX["fcfs"])  # the planted mistakes touch PL only
+    assert plx_matches(plx_run(O.ORDER_PL), PLX["pl"])  # the real oracle again

@@ -67,3 +67,70 @@ def test_two_gloo_ranks():
     for r in range(world):
         ok, t, c = res[r]
         assert ok and t == 0.5 and c == 201
+
+
+# ---- the exchange step of a sharded search, with the oracle simulating each
+# rank's shard of the exhaustive 3 x 3-tile search (1,024 partitions, 4 CPU +
+# 1 GPU-type processors)
+
+
+def test_best_pair_ties_and_empty():
+    from paper_1602_05510_b300.sharding import NONE, best_pair
+    assert best_pair([(5, 9), (5, 3), (7, 0)]) == (5, 3)
+    assert best_pair([(NONE, -1), (8, 100)]) == (8, 100)
+    assert best_pair([(NONE, -1), (NONE, -1)]) == (NONE, -1)
+
+
+def _shard_worker(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+
+    import oracle as O
+    from paper_1602_05510_b300 import workloads as W
+    from paper_1602_05510_b300.sharding import NONE, gather_makespans, global_best
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        per = 1024 // world
+        first = rank_first(rank, world, per, 0)
+        lv = W.exhaustive_levels(10)[first:first + per]
+        pl = O.make_platform(W.PLATFORMS["cfg0"])
+        ms, st, _ = O.simulate_many(pl, 3, 1024, lv, threads=1)
+        ok = st == 0
+        if ok.any():
+            m = int(ms[ok].min())
+            i = first + int(np.flatnonzero(ok & (ms == m))[0])
+        else:
+            m, i = NONE, -1
+        best = global_best(m, i, world)
+        allms = gather_makespans(torch.from_numpy(ms.astype(np.int64)), world).numpy()
+        out[rank] = (best, allms.tolist())
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 4])
+def test_sharded_search_equals_single_rank(world):
+    """Each gloo rank runs the oracle on its own shard; the gathered
+    makespans equal the single-rank run element by element, and the
+    all-ranks best (makespan, lowest index) equals its argmin."""
+    import torch.multiprocessing as mp
+
+    import oracle as O
+    from paper_1602_05510_b300 import workloads as W
+
+    lv = W.exhaustive_levels(10)
+    ms, st, _ = O.simulate_many(O.make_platform(W.PLATFORMS["cfg0"]), 3, 1024, lv, threads=1)
+    assert (st == 0).all()
+    want = (int(ms.min()), int(np.argmin(ms)))
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_shard_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    assert set(res) == set(range(world))
+    for r in range(world):
+        best, allms = res[r]
+        assert tuple(best) == want
+        assert np.array_equal(np.asarray(allms, np.int64), ms)
