@@ -2,16 +2,27 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hesp|reference]
 
-One step = the hot path over one batch: 65,536 candidate partition vectors of
-the 8 x 8-tile Cholesky (b = 2048, split levels uniform in {0, 1, 2}) drawn on
-the device from SplitMix64, then simulated on both platforms of that workload
-(12 CPU + 1 GPU-type processor with transfers, and 4 big + 4 LITTLE cores in
-shared memory).  The metric counts one task-event per task scheduled and
-completed in one candidate's simulation.
+One step = the hot path over one batch: 4,096 candidate partition vectors of
+the 32 x 32-tile Cholesky (N = 65536, b = 2048, 5,984 base tasks, split
+levels uniform in {0, 1, 2, 3}: DAGs of ~810,000 tasks) drawn on the device
+from SplitMix64, then expanded, dependence-analysed and simulated on 32 CPU
++ 2 GPU-type processors (FCFS + EFT-P, write-back caching of the two GPU
+memories) in one launch that holds every candidate resident, and reduced on
+the device to the batch's best candidate (least makespan, lowest index).
+The metric counts one task-event per task scheduled and completed in one
+candidate's simulation.
 
-N > 1 (torchrun): weak scaling -- rank r simulates its own 65,536 candidates
-(indices r * 65,536 ...); no collective touches the data path, only a barrier
-and a max over ranks of the timed region.
+Extra keys of the same run (one GPU): the 8 x 8-tile random-search step on
+its two platforms ("random_8x8_two_platforms": 65,536 candidates, 12 CPU +
+1 GPU-type and 4 big + 4 LITTLE), and the best makespan reached in 60 s of
+GPU time on the 32 x 32-tile problem by plain batched random search, by
+surrogate-guided search and by the paper's iterative solver ("search").
+
+N > 1 (torchrun): weak scaling -- rank r simulates its own 4,096 candidates
+per step (global indices (step * N + r) * 4096 ...); after the timed loop
+the ranks exchange their per-step best (makespan, index) pairs in one
+all-gather (16 bytes per rank and step), and rank 0 reports the best over
+all ranks; the timed region ends with a barrier and a max over ranks.
 
 --impl reference times the CPU oracle (the plain C implementation the GPU
 results are checked against) on the host cores, on a bounded sample of the
@@ -20,6 +31,7 @@ same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -34,17 +46,23 @@ sys.path.insert(0, ROOT)
 
 from paper_1602_05510_b300 import workloads as W  # noqa: E402
 
-WORKLOAD = W.WORKLOADS["cfg1"]
-N_TILES, B, N_LEVELS, N_CAND = WORKLOAD.n_tiles, WORKLOAD.b, WORKLOAD.n_levels, WORKLOAD.n_cand
+# the 32 x 32-tile random-search launch
+N_TILES, B, N_LEVELS, N_CAND, SEED = 32, 2048, 4, 4096, 4
 MAX_LEVEL = N_LEVELS - 1
-PLATS = ("cfg1a", "cfg1b")
+PLAT = "cfg4"  # 32 CPU + 2 GPU-type processors
+TASK_CAP = 1 << 20  # arena task capacity (the largest DAG of this distribution has ~0.87 M tasks)
 METRIC = "sim task-events/s (bit-exact)"
 UNIT = "task-events/s"
-CONFIG = {"workload": "random search, N=16384 Cholesky, b=2048 (8x8 tiles, 120 base tasks), split levels "
-                      "uniform {0,1,2}, 65,536 candidates per launch, simulated on 12 CPU + 1 GPU-type "
-                      "(transfers, write-back caching) and on 4 big + 4 LITTLE cores (shared memory)",
+CONFIG = {"workload": "random search, N=65536 Cholesky, b=2048 (32x32 tiles, 5,984 base tasks), split levels "
+                      "uniform {0,1,2,3} (finest b=256; DAGs of ~810,000 tasks), 4,096 candidates per launch, all "
+                      "resident, simulated on 32 CPU + 2 GPU-type processors (FCFS + EFT-P, transfers, write-back "
+                      "caching)",
           "n_tiles": N_TILES, "b": B, "levels": N_LEVELS, "candidates_per_step": N_CAND,
-          "platforms": ["cpu12_gpu1", "big4_little4"], "seed": WORKLOAD.seed}
+          "platform": "cpu32_gpu2", "seed": SEED, "task_cap": TASK_CAP}
+
+# the 8 x 8-tile random-search step on two platforms (extra key)
+C1 = W.WORKLOADS["cfg1"]
+C1_PLATS = ("cfg1a", "cfg1b")
 
 
 def env_int(k, d):
@@ -118,6 +136,15 @@ def measured_peaks():
         return None
 
 
+def free_cuda():
+    import gc
+
+    import torch
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
 # ---------------------------------------------------------------- GPU arm
 
 
@@ -126,7 +153,7 @@ def run_gpu(args):
     import torch.distributed as dist
 
     from paper_1602_05510_b300 import build, hesp
-    from paper_1602_05510_b300.sharding import rank_first, reduce_timing
+    from paper_1602_05510_b300.sharding import global_best, rank_first, reduce_timing
 
     world = env_int("WORLD_SIZE", 1)
     rank = env_int("RANK", 0)
@@ -139,75 +166,38 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     nb = W.base_count(N_TILES)
     C = args.candidates
-
-    plats = [hesp.Platform(W.PLATFORMS[k]) for k in PLATS]
-    if args.share_dag:
-        # one arena per candidate: each DAG is built once (in a launch of its
-        # own, or inside the first platform's launch with --keep-in-first) and
-        # every platform simulates the kept DAGs
-        kept = hesp.alloc_workspace_kept(N_TILES, MAX_LEVEL, C)
-        ws = [kept for _ in plats]
-    else:
-        ws = [hesp.alloc_workspace(p, N_TILES, MAX_LEVEL, C) for p in plats]
-
-    bst = torch.empty(C, dtype=torch.int32, device=dev)
-    build_apart = args.share_dag and not args.keep_in_first
-
-    def build_dags(cands_, levels_):
-        # the DAGs alone, in a launch of their own (platform independent)
-        hesp.dag_build_kept(cands_, levels_, C, N_TILES, MAX_LEVEL, ws[0], status=bst)
-
-    def simulate(i, p, cands_, levels_):
-        if not args.share_dag:
-            f = hesp.simulate_batch
-        elif build_apart:
-            f = hesp.simulate_batch_reuse
-        else:
-            f = hesp.simulate_batch_keep if i == 0 else hesp.simulate_batch_reuse
-        f(p, cands_, levels_, C, N_TILES, MAX_LEVEL, ws[i], makespan=ms[i], status=stt[i], ntasks=nts[i])
+    plat = hesp.Platform(W.PLATFORMS[PLAT])
+    ws = hesp.alloc_workspace(plat, N_TILES, MAX_LEVEL, C, TASK_CAP)  # every candidate resident
     levels = torch.empty(C * nb, dtype=torch.int8, device=dev)
     cands = torch.empty(C * 16, dtype=torch.uint8, device=dev)
-    ms = [torch.empty(C, dtype=torch.int64, device=dev) for _ in plats]
-    stt = [torch.empty(C, dtype=torch.int32, device=dev) for _ in plats]
-    nts = [torch.empty(C, dtype=torch.int64, device=dev) for _ in plats]
+    ms = torch.empty(C, dtype=torch.int64, device=dev)
+    st = torch.empty(C, dtype=torch.int32, device=dev)
+    nt = torch.empty(C, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
-    # largest DAG first (LPT): the persistent kernel's tail is then the smallest candidates
-    scands = torch.empty(C * 16, dtype=torch.uint8, device=dev)
-    perm = torch.empty(C, dtype=torch.int32, device=dev)
-    sort_ws = hesp.sort_workspace(C, dev)
+    K = args.steps
+    best = torch.empty((max(K, 1), 2), dtype=torch.int64, device=dev)  # per step: (makespan, global index)
+    evs = torch.empty((max(K, 1), 2), dtype=torch.int64, device=dev)   # per step: (best, task-events)
 
-    def step(first, ev=None):
-        hesp.generate_candidates(hesp.GEN_UNIFORM, WORKLOAD.seed, first, C, N_TILES, B, N_LEVELS, levels, cands)
-        sim_c = cands
-        if args.lpt:
-            sim_c, _ = hesp.sort_cands_by_size(cands, levels, C, scands, perm, sort_ws)
-        if build_apart:
-            if ev is not None:
-                ev[-1][0].record(stream)
-            build_dags(sim_c, levels)
-            if ev is not None:
-                ev[-1][1].record(stream)
-        for i, p in enumerate(plats):
-            if ev is not None:
-                ev[i][0].record(stream)
-            simulate(i, p, sim_c, levels)
-            if ev is not None:
-                ev[i][1].record(stream)
+    def step(first, k, kev=None):
+        # generation, simulation, the batch's best candidate and its task-event count (4 launches)
+        hesp.generate_candidates(hesp.GEN_UNIFORM, SEED, first, C, N_TILES, B, N_LEVELS, levels, cands)
+        if kev is not None:
+            kev[0].record(stream)
+        hesp.simulate_batch(plat, cands, levels, C, N_TILES, MAX_LEVEL, ws, makespan=ms, status=st, ntasks=nt,
+                            task_cap=TASK_CAP)
+        if kev is not None:
+            kev[1].record(stream)
+        hesp.best_candidate(ms, st, first, out=best[k])
+        hesp.best_makespan(ms, st, nt, out=evs[k])
 
     for w in range(args.warmup):
-        step(rank_first(rank, world, C, w))
+        step(rank_first(rank, world, C, w), 0)
     torch.cuda.synchronize()
-    for i in range(len(plats)):
-        bad = int((stt[i] != 0).sum().item())
-        if bad:
-            raise RuntimeError("%d candidates failed on %s" % (bad, PLATS[i]))
+    if args.warmup and int((st != 0).sum().item()):
+        raise RuntimeError("%d candidates failed" % int((st != 0).sum().item()))
 
-    K = args.steps
     step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    # per step: one event pair per platform's simulation launch, and one for the DAG build
-    kern_ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(len(plats) + 1)]
-               for _ in range(K)]
-    task_events = 0
+    kern_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     clocks = ClockSampler(local)
     if world > 1:
         dist.barrier()
@@ -218,32 +208,32 @@ def run_gpu(args):
     for k in range(K):
         flush.fill_(k & 0xFF)  # evict L2 between timed steps (outside the step's events)
         step_ev[k][0].record(stream)
-        step(rank_first(rank, world, C, args.warmup + k), kern_ev[k])
+        step(rank_first(rank, world, C, args.warmup + k), k, kern_ev[k])
         step_ev[k][1].record(stream)
-        for i in range(len(plats)):
-            task_events += nts[i].sum()  # device-side accumulation, read after the loop
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
-    task_events = int(task_events.item()) if K else 0
-    for i in range(len(plats)):
-        if int((stt[i] != 0).sum().item()):
-            raise RuntimeError("candidates failed on %s" % PLATS[i])
-    t_steps = sum(step_ev[k][0].elapsed_time(step_ev[k][1]) for k in range(K)) / 1e3
-    t_kern = [sum(kern_ev[k][i][0].elapsed_time(kern_ev[k][i][1]) for k in range(K)) / 1e3 for i in range(len(plats))]
-    t_build = (sum(kern_ev[k][-1][0].elapsed_time(kern_ev[k][-1][1]) for k in range(K)) / 1e3) if build_apart else None
+    if int((st != 0).sum().item()):
+        raise RuntimeError("%d candidates failed" % int((st != 0).sum().item()))
+    ev_h = evs[:K].cpu().numpy()
+    task_events = int(ev_h[:, 1].sum()) if K else 0
+    t_steps = sum(a.elapsed_time(b_) for a, b_ in step_ev) / 1e3
+    t_kern = sum(a.elapsed_time(b_) for a, b_ in kern_ev) / 1e3
     t_max, tot_events = reduce_timing(t_steps, task_events, world, dev)
+    # the exchange step: every rank's per-step best, combined over ranks
+    bests = [global_best(best[k], None, world, dev) for k in range(K)]
+    overall = min(bests) if bests else None
 
     # ---- end to end through the public API with host buffers
     e2e = None
     if args.e2e_steps > 0:
-        lv_host = [torch.from_numpy(W.uniform_levels(WORKLOAD.seed, rank_first(rank, world, C, 1000 + s), C, nb,
+        lv_host = [torch.from_numpy(W.uniform_levels(SEED, rank_first(rank, world, C, 1000 + s), C, nb,
                                                      N_LEVELS).reshape(-1)).pin_memory()
                    for s in range(min(args.e2e_steps, 2))]
         cand_host = hesp.cands_tensor(N_TILES, B, np.arange(C, dtype=np.int64) * nb, device="cpu").pin_memory()
-        out_host = [torch.empty(C, dtype=torch.int64).pin_memory() for _ in plats]
-        e2e_ev = []
-        e2e_tasks = 0
+        ms_host = torch.empty(C, dtype=torch.int64).pin_memory()
+        best_host = torch.empty(2, dtype=torch.int64).pin_memory()
+        e2e_ev, e2e_tasks = [], 0
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -253,69 +243,191 @@ def run_gpu(args):
             a.record(stream)
             levels.copy_(lv_host[s % len(lv_host)], non_blocking=True)
             cands.copy_(cand_host, non_blocking=True)
-            sim_c = hesp.sort_cands_by_size(cands, levels, C, scands, perm, sort_ws)[0] if args.lpt else cands
-            if build_apart:
-                build_dags(sim_c, levels)
-            for i, p in enumerate(plats):
-                simulate(i, p, sim_c, levels)
-                out_host[i].copy_(ms[i], non_blocking=True)
+            hesp.simulate_batch(plat, cands, levels, C, N_TILES, MAX_LEVEL, ws, makespan=ms, status=st, ntasks=nt,
+                                task_cap=TASK_CAP)
+            hesp.best_candidate(ms, st, 0, out=best[0])
+            hesp.best_makespan(ms, st, nt, out=evs[0])
+            ms_host.copy_(ms, non_blocking=True)
+            best_host.copy_(best[0], non_blocking=True)
             b_.record(stream)
             e2e_ev.append((a, b_))
-            for i in range(len(plats)):
-                e2e_tasks += nts[i].sum()
-        torch.cuda.synchronize()
+            torch.cuda.synchronize()
+            e2e_tasks += int(evs[0, 1].item())
         t_e2e = sum(a.elapsed_time(b_) for a, b_ in e2e_ev) / 1e3
-        e2e_tasks = int(e2e_tasks.item())
         t_e2e, e2e_tasks = reduce_timing(t_e2e, e2e_tasks, world, dev)
         e2e = {"value": e2e_tasks / t_e2e, "unit": UNIT, "h2d_bytes_per_step": C * nb + C * 16,
-               "d2h_bytes_per_step": 8 * C * len(plats), "steps": args.e2e_steps,
-               "path": "pinned host partition vectors -> largest-first order -> DAG build -> simulation on both "
-                       "platforms -> host makespans"}
+               "d2h_bytes_per_step": 8 * C + 16, "steps": args.e2e_steps,
+               "path": "pinned host partition vectors -> simulation -> best candidate -> host makespans and best"}
+    del ws
+    free_cuda()
 
-    if rank == 0:
-        peaks = measured_peaks()
-        line = {
-            "metric": METRIC, "value": tot_events / t_max if t_max > 0 else None, "unit": UNIT,
-            "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / max(K, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic (seeded SplitMix64 partition vectors generated on the device)",
-            "config": dict(CONFIG, candidates_per_step=C,
-                           parallelism="candidates sharded across ranks (dp%d)" % world,
-                           dag=("built once per candidate in a launch of its own, then simulated on both "
-                                "platforms" if build_apart else
-                                "built once per candidate (the first platform's launch keeps it, the second "
-                                "simulates it)") if args.share_dag else "built in each platform's launch",
-                           order="largest DAG first" if args.lpt else "generation order",
-                           l2="256 MB buffer written between timed steps; per-step working set ~GBs > L2"),
-            "candidates_per_s": 2 * C * world * K / t_max if t_max > 0 else None,
-            "task_events": tot_events,
-            "wall_s": wall,
-            # generation, [3 sort kernels,] [the DAG build,] 2 simulations
-            "gpu_launches": (3 + (3 if args.lpt else 0) + (1 if build_apart else 0)) * K,
-            "kernel_ms_per_step": {"dag_build": 1e3 * t_build / K if build_apart else None,
-                                   PLATS[0]: 1e3 * t_kern[0] / K, PLATS[1]: 1e3 * t_kern[1] / K},
-            "clocks": clk,
-            "e2e": e2e,
-        }
-        line["roofline"] = roofline(plats, t_kern, K, tot_events // world, clk, peaks)
-        if args.cpu_baseline and world == 1:
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    line = {
+        "metric": METRIC, "value": tot_events / t_max if t_max > 0 else None, "unit": UNIT,
+        "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / max(K, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic (seeded SplitMix64 partition vectors generated on the device)",
+        "config": dict(CONFIG, candidates_per_step=C, parallelism="candidates sharded across ranks (dp%d)" % world,
+                       l2="256 MB buffer written between timed steps; per-step working set ~220 GB > L2"),
+        "candidates_per_s": C * world * K / t_max if t_max > 0 else None,
+        "task_events": tot_events,
+        "wall_s": wall,
+        "gpu_launches": 4 * K,  # generation, simulation, best candidate, task-event count
+        "kernel_ms_per_step": 1e3 * t_kern / max(K, 1),
+        "best_makespan_ns": overall[0] if overall else None,
+        "best_candidate": overall[1] if overall else None,
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    line["roofline"] = roofline(t_kern / max(K, 1), task_events / max(K, 1), props, peaks)
+    if world == 1:
+        extra_clk = ClockSampler(local)
+        extra_clk.start()
+        if args.extra_cfg1:
+            line["random_8x8_two_platforms"] = run_cfg1(args, dev)
+            free_cuda()
+        if args.search_budget > 0:
+            line["search"] = search_comparison(args)
+            free_cuda()
+        line["extra_clocks"] = extra_clk.stop()
+        if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_sample)
-        print(json.dumps(line))
+            line["cpu_baseline_1core"] = cpu_baseline(args.cpu_sample_1core, threads=1)
+    print(json.dumps(line))
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
 
 
-# ncu figures of the simulation kernel (profiles/sim_kernel_cfg1_small.md), valid only
-# for the kernel source they were taken on: DRAM bytes per 4,096 candidates on the
-# CPU+GPU platform (scaled to a launch by candidates; traffic grows in proportion)
-# and the share of issue slots busy.
-SIM_NCU = {"source_sha1_12": "e2ee6a664226", "dram_bytes_per_4096": 0.531371e9 + 0.327081e9,
-           "issue_active_pct": 62.92, "warps_per_sm": 25.6, "alu_pipe_pct": 55.6}
+def run_cfg1(args, dev):
+    """The 8 x 8-tile random-search step (65,536 candidates, levels uniform
+    {0, 1, 2}): generation, largest DAG first, one DAG build launch, then the
+    kept DAGs simulated on 12 CPU + 1 GPU-type and on 4 big + 4 LITTLE."""
+    import torch
+
+    from paper_1602_05510_b300 import hesp
+
+    n, b, NL, C = C1.n_tiles, C1.b, C1.n_levels, C1.n_cand
+    nb = W.base_count(n)
+    stream = torch.cuda.current_stream()
+    plats = [hesp.Platform(W.PLATFORMS[k]) for k in C1_PLATS]
+    kept = hesp.alloc_workspace_kept(n, NL - 1, C)
+    levels = torch.empty(C * nb, dtype=torch.int8, device=dev)
+    cands = torch.empty(C * 16, dtype=torch.uint8, device=dev)
+    scands = torch.empty(C * 16, dtype=torch.uint8, device=dev)
+    perm = torch.empty(C, dtype=torch.int32, device=dev)
+    sort_ws = hesp.sort_workspace(C, dev)
+    bst = torch.empty(C, dtype=torch.int32, device=dev)
+    ms = [torch.empty(C, dtype=torch.int64, device=dev) for _ in plats]
+    st = [torch.empty(C, dtype=torch.int32, device=dev) for _ in plats]
+    nt = [torch.empty(C, dtype=torch.int64, device=dev) for _ in plats]
+    tot = torch.empty((len(plats), 2), dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(first):
+        hesp.generate_candidates(hesp.GEN_UNIFORM, C1.seed, first, C, n, b, NL, levels, cands)
+        sc, _ = hesp.sort_cands_by_size(cands, levels, C, scands, perm, sort_ws)
+        hesp.dag_build_kept(sc, levels, C, n, NL - 1, kept, status=bst)
+        for i, p in enumerate(plats):
+            hesp.simulate_batch_reuse(p, sc, levels, C, n, NL - 1, kept, makespan=ms[i], status=st[i], ntasks=nt[i])
+
+    for w in range(args.cfg1_warmup):
+        step(w * C)
+    torch.cuda.synchronize()
+    K = args.cfg1_steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    events = 0
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        step((args.cfg1_warmup + k) * C)
+        ev[k][1].record(stream)
+        for i in range(len(plats)):
+            hesp.best_makespan(ms[i], st[i], nt[i], out=tot[i])
+        torch.cuda.synchronize()
+        if any(int((s != 0).sum().item()) for s in st):
+            raise RuntimeError("8x8-tile candidates failed")
+        events += int(tot[:, 1].sum().item())
+    t = sum(a.elapsed_time(b_) for a, b_ in ev) / 1e3
+    return {"metric": METRIC, "value": events / t, "unit": UNIT, "steps": K, "ms_per_step": 1e3 * t / max(K, 1),
+            "candidates_per_s": len(plats) * C * K / t,
+            "workload": "random search, N=16384 Cholesky, b=2048 (8x8 tiles, 120 base tasks), split levels uniform "
+                        "{0,1,2}, 65,536 candidates per step, largest DAG first, one DAG build launch, simulated on "
+                        "12 CPU + 1 GPU-type (transfers, write-back) and on 4 big + 4 LITTLE (shared memory)"}
+
+
+def search_comparison(args):
+    """Best makespan reached on the 32 x 32-tile problem within the same
+    wall-time budget by plain batched random search, by surrogate-guided
+    search and by the paper's iterative solver (CP selection, Hard sampling,
+    from the unsplit partition), one arm after the other on this GPU."""
+    from paper_1602_05510_b300 import search as S
+
+    spec = W.PLATFORMS[PLAT]
+    ws = int(args.ws_gb * (1 << 30))
+    out = {"budget_s": args.search_budget}
+    sim = S.Simulator(spec, N_TILES, B, MAX_LEVEL, N_CAND, task_cap=TASK_CAP)
+    rlog = S.random_search(spec, N_TILES, B, N_LEVELS, seed=SEED, budget_s=args.search_budget, per_launch=N_CAND,
+                           sim=sim)
+    del sim
+    free_cuda()
+    # the surrogate arm starts as the solver does (from the unsplit partition,
+    # its descent labelling the model), then ranks mutants of its elites
+    scfg = dict(surrogate_cfg(args), start="solver", heldout=1024, p_mut=args.seeded_p_mut)
+    slog = S.surrogate_search(spec, N_TILES, B, N_LEVELS, seed=5, budget_s=args.search_budget,
+                              per_launch=args.round_sims, cfg=S.SurrogateConfig(**scfg), task_cap=TASK_CAP,
+                              ws_bytes=ws)
+    free_cuda()
+    ilog = S.iterative_search(spec, N_TILES, B, N_LEVELS, S.hesp.SOLVER_CP, S.hesp.PICK_HARD, seed=6,
+                              budget_s=args.search_budget, task_cap=TASK_CAP, ws_bytes=ws,
+                              first=np.zeros(W.base_count(N_TILES), np.int8))
+    target = rlog.best[-1]
+    t_reach = slog.time_to_reach(target)
+    t_solver = slog.time_to_reach(ilog.best[-1])
+    out.update({
+        "random": {"best": rlog.best[-1], "candidates": rlog.simulated[-1],
+                   "task_events_per_s": rlog.events[-1] / rlog.times[-1]},
+        "surrogate": {"best": slog.best[-1], "candidates_simulated": slog.simulated[-1],
+                      "start": "the iterative solver's descent from the unsplit partition (CP + Hard), then "
+                               "surrogate-ranked mutants of the elites",
+                      "time_to_random_best_s": t_reach,
+                      "time_ratio": (t_reach / rlog.times[-1]) if t_reach is not None else None,
+                      "time_to_solver_best_s": t_solver,
+                      "rounds": len(slog.metrics), "last_round": slog.metrics[-1] if slog.metrics else None,
+                      "spearman_selected_median": _median([m.get("spearman") for m in slog.metrics]),
+                      "spearman_heldout_median": _median([m.get("heldout_spearman") for m in slog.metrics])},
+        "iterative_cp_hard": {"best": ilog.best[-1], "candidates_simulated": ilog.simulated[-1],
+                              "iterations": len(ilog.best), "time_to_random_best_s": ilog.time_to_reach(target),
+                              "first_local_optimum": ilog.metrics[0] if ilog.metrics else None},
+    })
+    return out
+
+
+def _median(xs):
+    xs = [x for x in xs if x is not None and np.isfinite(x)]
+    return float(np.median(xs)) if xs else None
+
+
+def surrogate_cfg(args):
+    return dict(hidden=512, batch=2048, warmup_launches=1, warmup_steps=args.warmup_steps,
+                steps_per_round=args.round_steps, proposals=args.round_proposals, elites=32, p_mut=args.p_mut,
+                label_cap=1 << 17)
+
+
+# ncu figures of the simulation kernel taken on the kernel source whose sha1
+# prefix is given (null once the source changes): DRAM bytes and issued
+# warp-instructions per task-event and the share of issue slots busy.
+SIM_NCU = {"source_sha1_12": None, "dram_bytes_per_task_event": None, "warp_inst_per_task_event": None,
+           "issue_active_pct": None, "warps_per_sm": None, "case": None}
 
 
 def sim_source_matches():
-    import hashlib
     p = os.path.join(ROOT, "paper_1602_05510_b300", "csrc", "sim_kernel.cu")
     try:
         return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12] == SIM_NCU["source_sha1_12"]
@@ -323,40 +435,48 @@ def sim_source_matches():
         return False
 
 
-def roofline(plats, t_kern, K, task_events_rank, clk, peaks):
-    """Dominant kernel: the simulation kernel on the CPU+GPU platform (the
-    event loop with coherence, from the DAGs the build launch kept; 59 % of a
-    step).  It is bound by integer/control issue, not by HBM or tensor cores;
-    `achieved`
-    counts the algorithmic int64 operations of the simulation per task-event
-    (EFT evaluation 4 P, data-ready times M A_j, coherence commit A_j) and the
-    peak is the SM integer issue rate at the maximum SM clock (148 SMs x 128
-    lanes, one int64 operation = 2 lane-operations)."""
-    alg = alg_ops_per_event(W.workload_levels("cfg1", 0, 4096), len(W.PLATFORMS["cfg1a"].procs),
-                            W.PLATFORMS["cfg1a"].n_mem)
-    t = t_kern[0] / max(K, 1)
+def roofline(t, events, props, peaks):
+    """Dominant kernel: the simulation launch (expansion, dependences and the
+    event loop of every candidate).  It is bound by integer and control
+    issue, not by HBM or tensor cores.  `achieved` counts the algorithmic
+    int64 operations per task-event (EFT evaluation 4 P, data-ready times
+    M A_j, coherence commit A_j) over one launch's task-events, divided by the
+    launch's CUDA-event time; the peak is the SM integer issue rate at the
+    maximum SM clock (SMs x 128 INT32 lanes, one int64 operation = 2
+    lane-operations).  Beside it: the issue-slot view (warp-instructions per
+    task-event from ncu, times the live task-event rate, against SMs x 4
+    schedulers x clock)."""
+    spec = W.PLATFORMS[PLAT]
+    alg = alg_ops_per_event(W.uniform_levels(SEED, 0, 256, W.base_count(N_TILES), N_LEVELS), N_TILES, B,
+                            len(spec.procs), spec.n_mem)
     sm_max = (peaks or {}).get("sm_max_mhz", 2032.0)
-    peak = 148 * 128 * sm_max * 1e6 / 2 / 1e12  # T int64-op/s
-    ev_a = task_events_rank / 2  # both platforms run the same candidates
-    achieved = alg * ev_a / t / 1e12 if t > 0 and alg else None
+    sms = props.multi_processor_count
+    peak = sms * 128 * sm_max * 1e6 / 2 / 1e12  # T int64-op/s
+    achieved = alg * events / t / 1e12 if t > 0 and alg else None
     fresh = sim_source_matches()
-    C = N_CAND
-    return {"bound": "alu", "kernel": "sim_kernel<M=2> reuse (cpu12_gpu1)", "achieved": achieved, "peak": peak,
-            "unit": "T int64-op/s", "frac": achieved / peak if achieved else None,
-            "peak_source": "derived: 148 SMs x 128 INT32 lanes x %.0f MHz / 2 (sm_max_mhz of MEASURED_PEAKS)" % sm_max,
-            "kernel_ms": 1e3 * t,
-            "traffic": SIM_NCU["dram_bytes_per_4096"] * C / 4096 if fresh else None,
-            "dram_gbs": SIM_NCU["dram_bytes_per_4096"] * C / 4096 / t / 1e9 if fresh and t > 0 else None,
-            "traffic_note": "DRAM bytes per launch from one ncu capture of 4,096 candidates, scaled by candidates; "
-                            "all of it is per-candidate arena state (algorithmic I/O is 120 B in + 20 B out per "
-                            "candidate)",
-            "issue_slots": {"busy_pct": SIM_NCU["issue_active_pct"] if fresh else None,
-                            "warps_per_sm": SIM_NCU["warps_per_sm"], "alu_pipe_pct": SIM_NCU["alu_pipe_pct"],
-                            "source": "ncu smsp__issue_active.avg.pct_of_peak_sustained_active"},
-            "alg_ops_per_task_event": alg}
+    issue_peak = sms * 4 * sm_max * 1e6
+    ipe = SIM_NCU["warp_inst_per_task_event"] if fresh else None
+    out = {"bound": "alu", "kernel": "sim_kernel<M=3,NS=2> (cpu32_gpu2)", "achieved": achieved, "peak": peak,
+           "unit": "T int64-op/s", "frac": achieved / peak if achieved else None,
+           "peak_source": "derived: %d SMs x 128 INT32 lanes x %.0f MHz / 2 (sm_max_mhz of MEASURED_PEAKS)"
+                          % (sms, sm_max),
+           "kernel_ms": 1e3 * t, "task_events_per_launch": events, "alg_ops_per_task_event": alg,
+           "traffic": SIM_NCU["dram_bytes_per_task_event"] * events if fresh else None,
+           "dram_gbs": SIM_NCU["dram_bytes_per_task_event"] * events / t / 1e9 if fresh and t > 0 else None,
+           "traffic_note": "DRAM bytes per task-event from one ncu capture of a smaller launch of the same kernel "
+                           "(%s), times this launch's task-events; algorithmic I/O is 5,984 B in + 24 B out per "
+                           "candidate" % SIM_NCU["case"],
+           "issue_slots": {"warp_inst_per_task_event": ipe,
+                           "achieved_frac_of_issue_peak": ipe * events / t / issue_peak if ipe and t > 0 else None,
+                           "issue_peak_warp_inst_per_s": issue_peak,
+                           "ncu_issue_active_pct": SIM_NCU["issue_active_pct"] if fresh else None,
+                           "ncu_warps_per_sm": SIM_NCU["warps_per_sm"] if fresh else None,
+                           "source": "ncu smsp__inst_executed.sum / task-events, "
+                                     "smsp__issue_active.avg.pct_of_peak_sustained_active"}}
+    return out
 
 
-def alg_ops_per_event(levels, P, M):
+def alg_ops_per_event(levels, n, b, P, M):
     """Algorithmic int64 operations per task-event of one launch: 4 P for the
     EFT evaluation (two max, one add, one compare per processor) plus
     (M + 1) per atom of the task's data (data-ready time per memory, then the
@@ -370,8 +490,8 @@ def alg_ops_per_event(levels, P, M):
     for l in range(1, 5):
         for op in range(4):
             tab[op, l] = sum(kids[op][c] * tab[c, l - 1] for c in range(4))
-    ops = hesp.Dag(N_TILES, B, MAX_LEVEL).base_tasks()[0]
     lv = np.asarray(levels, np.int64)
+    ops = hesp.Dag(n, b, int(lv.max())).base_tasks()[0]
     Lc = lv.max(axis=1, keepdims=True)
     tasks = tab[ops[None, :], lv].sum(-1)                  # [C, n_base]
     regs = (tab[ops[None, :], lv] * nreg).sum(-1)
@@ -379,21 +499,23 @@ def alg_ops_per_event(levels, P, M):
     return 4 * P + (M + 1) * atoms.sum() / tasks.sum()
 
 
-def cpu_baseline(sample):
+def cpu_baseline(sample, threads=None):
+    """The oracle on `sample` candidates of the same workload, one candidate
+    per thread chunk over the host cores (or `threads`)."""
     import oracle as O
 
-    cores = os.cpu_count() or 1
-    lv = W.workload_levels("cfg1", 0, sample)
+    cores = threads or os.cpu_count() or 1
+    lv = W.uniform_levels(SEED, 0, sample, W.base_count(N_TILES), N_LEVELS)
+    pl = O.make_platform(W.PLATFORMS[PLAT])
     t0 = time.perf_counter()
-    ev = 0
-    for k in PLATS:
-        pl = O.make_platform(W.PLATFORMS[k])
-        ms, st, tasks = O.simulate_many(pl, N_TILES, B, lv, threads=cores)
-        ev += int(tasks.sum())
+    ms, st, tasks = O.simulate_many(pl, N_TILES, B, lv, threads=cores)
     dt = time.perf_counter() - t0
+    assert (st == 0).all()
+    ev = int(tasks.sum())
     return {"value": ev / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d candidates of the same workload x 2 platforms (%d task-events), one candidate per "
-                      "thread-chunk over %d host threads, %.1f s" % (sample, ev, cores, dt)}
+            "candidates_per_s": sample / dt,
+            "sample": "%d candidates of the same workload (%d task-events) on %d host thread(s), %.1f s; per "
+                      "task-event rate, so it extrapolates to a 4,096-candidate launch" % (sample, ev, cores, dt)}
 
 
 def cpu_baseline_each(sim_one, count, label):
@@ -424,16 +546,15 @@ def run_reference(args):
 
     O.build()
     cores = os.cpu_count() or 1
-    per_step = args.ref_sample
-    pls = [O.make_platform(W.PLATFORMS[k]) for k in PLATS]
+    per_step = args.ref_sample or cores  # one candidate per host thread per step
+    pl = O.make_platform(W.PLATFORMS[PLAT])
+    nb = W.base_count(N_TILES)
 
     def one(k):
-        lv = W.workload_levels("cfg1", (k * 7919) % (N_CAND - per_step), per_step)
-        ev = 0
-        for pl in pls:
-            _, st, tasks = O.simulate_many(pl, N_TILES, B, lv, threads=cores)
-            ev += int(tasks.sum())
-        return ev
+        lv = W.uniform_levels(SEED, k * per_step, per_step, nb, N_LEVELS)
+        _, st, tasks = O.simulate_many(pl, N_TILES, B, lv, threads=cores)
+        assert (st == 0).all()
+        return int(tasks.sum())
 
     for w in range(args.warmup):
         one(w)
@@ -448,7 +569,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "impl": "reference",
             "config": dict(CONFIG, parallelism="host threads"),
             "cpu_baseline": {"kind": "oracle", "cores": cores, "value": v, "unit": UNIT,
-                             "sample": "%d candidates per step x 2 platforms on %d host threads" % (per_step, cores)},
+                             "sample": "%d candidates of the same workload per step on %d host threads"
+                                       % (per_step, cores)},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -601,11 +723,11 @@ def run_factors(args):
 
     build.build()
     n, b, K = W.FACTOR_N, W.FACTOR_B, W.FACTOR_MAX
-    C = args.candidates
+    C = args.general_candidates
     nb = W.base_count(n)
     f = torch.from_numpy(W.uniform_factors(9, 0, C, nb, K).reshape(-1).copy()).cuda()
     cands = hesp.cands_tensor(n, b, np.arange(C, dtype=np.int64) * nb)
-    plats = [hesp.Platform(W.PLATFORMS[k]) for k in PLATS]
+    plats = [hesp.Platform(W.PLATFORMS[k]) for k in C1_PLATS]
     wss = [hesp.alloc_workspace_factors(p, n, K, C) for p in plats]
     ms = [torch.empty(C, dtype=torch.int64, device="cuda") for _ in plats]
     st = [torch.empty(C, dtype=torch.int32, device="cuda") for _ in plats]
@@ -640,13 +762,13 @@ def run_factors(args):
                         "b / lcm(factors), simulated on 12 CPU + 1 GPU-type and on 4 big + 4 LITTLE" % C,
             "ms_per_step": 1e3 * t / args.steps, "all_ok": ok, "task_events_per_step": events,
             "candidates_per_s": C * len(plats) * args.steps / t,
-            "kernel_ms_per_step": {k: 1e3 * x / args.steps for k, x in zip(PLATS, t_k)},
+            "kernel_ms_per_step": {k: 1e3 * x / args.steps for k, x in zip(C1_PLATS, t_k)},
             "l2": "256 MB buffer written between timed steps"}
     if args.cpu_baseline:
         import oracle as O
 
         fh = W.uniform_factors(9, 0, 8192, nb, K)
-        pls = [O.make_platform(W.PLATFORMS[k]) for k in PLATS]
+        pls = [O.make_platform(W.PLATFORMS[k]) for k in C1_PLATS]
 
         def one(c):
             return sum(O.simulate_factors(pl, n, b, fh[c], schedule=False)["n_tasks"] for pl in pls)
@@ -665,26 +787,27 @@ def run_capacity(args):
     from paper_1602_05510_b300 import build, hesp
 
     build.build()
-    C = args.candidates
-    nb = W.base_count(N_TILES)
+    C = args.general_candidates
+    n1, b1, nl1, ml1 = C1.n_tiles, C1.b, C1.n_levels, C1.n_levels - 1
+    nb = W.base_count(n1)
     plat = hesp.Platform(W.PLATFORMS["cfg1a"], capacity={1: 256 << 20})
     cands = torch.empty(C * 16, dtype=torch.uint8, device="cuda")
     levels = torch.empty(C * nb, dtype=torch.int8, device="cuda")
-    hesp.generate_candidates(hesp.GEN_UNIFORM, WORKLOAD.seed, 0, C, N_TILES, B, N_LEVELS, levels, cands)
-    ws = hesp.alloc_workspace(plat, N_TILES, MAX_LEVEL, C)
+    hesp.generate_candidates(hesp.GEN_UNIFORM, C1.seed, 0, C, n1, b1, nl1, levels, cands)
+    ws = hesp.alloc_workspace(plat, n1, ml1, C)
     ms = torch.empty(C, dtype=torch.int64, device="cuda")
     st = torch.empty(C, dtype=torch.int32, device="cuda")
     nt = torch.empty(C, dtype=torch.int64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
-        hesp.simulate_batch(plat, cands, levels, C, N_TILES, MAX_LEVEL, ws, makespan=ms, status=st, ntasks=nt)
+        hesp.simulate_batch(plat, cands, levels, C, n1, ml1, ws, makespan=ms, status=st, ntasks=nt)
     torch.cuda.synchronize()
     t = 0.0
     for it in range(args.steps):
         flush.fill_(it & 255)
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        hesp.simulate_batch(plat, cands, levels, C, N_TILES, MAX_LEVEL, ws, makespan=ms, status=st, ntasks=nt)
+        hesp.simulate_batch(plat, cands, levels, C, n1, ml1, ws, makespan=ms, status=st, ntasks=nt)
         e.record()
         torch.cuda.synchronize()
         t += a.elapsed_time(e) / 1e3
@@ -704,7 +827,7 @@ def run_capacity(args):
         pl = O.make_platform(W.PLATFORMS["cfg1a"], capacity={1: 256 << 20})
 
         def one(c):
-            return O.simulate(pl, N_TILES, B, lh[c], schedule=False)["n_tasks"]
+            return O.simulate(pl, n1, b1, lh[c], schedule=False)["n_tasks"]
 
         line["cpu_baseline"] = cpu_baseline_each(one, 8192, "12 CPU + 1 GPU-type, 256 MB GPU memory")
     print(json.dumps(line))
@@ -806,6 +929,7 @@ def run_search(args):
                               task_cap=cap, ws_bytes=ws, first=np.zeros(W.base_count(n), np.int8))
     target = rlog.best[-1]
     t_reach = slog.time_to_reach(target)
+    t_solver = slog.time_to_reach(ilog.best[-1])
     line = {"metric": "best makespan in %.0f s, surrogate vs plain search" % args.budget, "unit": "ns",
             "higher_is_better": False, "n_gpus": 1,
             "workload": "32x32 tiles, b=2048, levels 0..3, 32 CPU + 2 GPU-type processors",
@@ -915,23 +1039,25 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hesp", choices=["hesp", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--keep-in-first", action="store_true",
-                    help="build the DAGs inside the first platform's simulation launch instead of a launch of "
-                         "their own")
-    ap.add_argument("--no-share-dag", dest="share_dag", action="store_false",
-                    help="build each candidate's DAG in both platform launches instead of once")
-    ap.add_argument("--no-lpt", dest="lpt", action="store_false",
-                    help="simulate candidates in generation order instead of largest DAG first")
-    ap.add_argument("--cpu-sample", type=int, default=65536)
-    ap.add_argument("--ref-sample", type=int, default=256)
+    ap.add_argument("--cpu-sample", type=int, default=64, help="oracle candidates timed on all host cores")
+    ap.add_argument("--cpu-sample-1core", type=int, default=12, help="oracle candidates timed on one host core")
+    ap.add_argument("--ref-sample", type=int, default=0, help="reference arm: candidates per step (0: one per core)")
     ap.add_argument("--candidates", type=int, default=N_CAND,
-                    help="candidates per step (default: the workload's 65,536; smaller only for profiling)")
-    ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search", "uneven", "solver", "table1", "exhaustive",
-                             "factors", "capacity"],
+                    help="candidates per step (default: the workload's 4,096; smaller only for profiling)")
+    ap.add_argument("--no-extra-cfg1", dest="extra_cfg1", action="store_false",
+                    help="skip the 8x8-tile two-platform line of the default run")
+    ap.add_argument("--cfg1-steps", type=int, default=5)
+    ap.add_argument("--cfg1-warmup", type=int, default=3)
+    ap.add_argument("--search-budget", type=float, default=60.0,
+                    help="seconds per arm of the search comparison of the default run (0: skip)")
+    ap.add_argument("--general-candidates", type=int, default=65536,
+                    help="candidates per launch of the factors / capacity workloads")
+    ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search", "uneven", "solver",
+                                                            "table1", "exhaustive", "factors", "capacity"],
                     help="random: the default benchmark line; surrogate: label/train/rank/re-score "
-                         "pipeline; search: surrogate-guided vs random search")
+                         "pipeline; search: surrogate-guided vs random search with the ablation arm")
     ap.add_argument("--labels", type=int, default=1 << 20)
     ap.add_argument("--proposals", type=int, default=1 << 22)
     ap.add_argument("--train-steps", type=int, default=2000)
@@ -944,6 +1070,8 @@ def main():
     ap.add_argument("--round-steps", type=int, default=40)
     ap.add_argument("--warmup-steps", type=int, default=200)
     ap.add_argument("--p-mut", type=float, default=0.004)
+    ap.add_argument("--seeded-p-mut", type=float, default=0.001,
+                    help="mutation rate of the solver-seeded surrogate arm of the default run")
     ap.add_argument("--ws-gb", type=float, default=100.0)
     args = ap.parse_args()
     if args.workload == "surrogate":

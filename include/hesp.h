@@ -620,6 +620,16 @@ int hesp_gather_f32(const float *src_dev, const int64_t *idx_dev, int64_t k, flo
  * nullable: 0). */
 int hesp_best_makespan(const int64_t *makespan_dev, const int32_t *status_dev, const int64_t *ntasks_dev, int64_t n,
                        int64_t *out_dev, void *stream);
+/* The best candidate of a batch, the result of one schedule stage over a
+ * batch of partitions (Sec. 2.1 "Iterative solver": the partition with the
+ * least simulated makespan is kept): out_dev[0] = the least makespan among
+ * candidates with status HESP_OK (INT64_MAX if none), out_dev[1] =
+ * first_index + the lowest index holding it (-1 if none).  first_index is
+ * the global index of the batch's first candidate, so that the pairs of
+ * several batches or ranks combine by taking the least (makespan, index).
+ * out_dev: two int64 in device memory, written on `stream`. */
+int hesp_best_candidate(const int64_t *makespan_dev, const int32_t *status_dev, int64_t n, int64_t first_index,
+                        int64_t *out_dev, void *stream);
 /* dst_dev[i, :] = src_dev[idx_dev[i], :] for int8 rows of `width` bytes. */
 int hesp_gather_rows(const int8_t *src_dev, const int64_t *idx_dev, int64_t k, int64_t width, int8_t *dst_dev,
                      void *stream);

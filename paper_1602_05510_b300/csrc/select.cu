@@ -254,6 +254,41 @@ __global__ void best_kernel(const int64_t *ms, const int32_t *status, const int6
     }
 }
 
+// out[0] = min makespan over candidates with status 0 (INT64_MAX if none),
+// out[1] = first + the lowest index holding it (-1 if none); one block,
+// two block reductions (the minimum, then the lowest index at it).
+__global__ void best_index_kernel(const int64_t *ms, const int32_t *status, int64_t n, int64_t first, int64_t *out) {
+    __shared__ int64_t sm[1024];
+    __shared__ int64_t s_best;
+    int64_t m = INT64_MAX;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+        if (status[i] == 0) m = min(m, ms[i]);
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sm[threadIdx.x] = min(sm[threadIdx.x], sm[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) s_best = sm[0];
+    __syncthreads();
+    const int64_t best = s_best;
+    int64_t idx = INT64_MAX;
+    if (best != INT64_MAX)
+        for (int64_t i = threadIdx.x; i < n && idx == INT64_MAX; i += blockDim.x)
+            if (status[i] == 0 && ms[i] == best) idx = i;
+    __syncthreads();
+    sm[threadIdx.x] = idx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sm[threadIdx.x] = min(sm[threadIdx.x], sm[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = best;
+        out[1] = best == INT64_MAX ? -1 : first + sm[0];
+    }
+}
+
 constexpr int64_t kChunk = 4096;
 
 }  // namespace
@@ -330,6 +365,13 @@ int hesp_best_makespan(const int64_t *makespan_dev, const int32_t *status_dev, c
                        int64_t *out_dev, void *stream) {
     if (!makespan_dev || !status_dev || !out_dev || n < 0) return HESP_ERR_ARG;
     best_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(makespan_dev, status_dev, ntasks_dev, n, out_dev);
+    return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
+}
+
+int hesp_best_candidate(const int64_t *makespan_dev, const int32_t *status_dev, int64_t n, int64_t first_index,
+                        int64_t *out_dev, void *stream) {
+    if (!makespan_dev || !status_dev || !out_dev || n < 0 || first_index < 0) return HESP_ERR_ARG;
+    best_index_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(makespan_dev, status_dev, n, first_index, out_dev);
     return cudaGetLastError() == cudaSuccess ? HESP_OK : HESP_ERR_CUDA;
 }
 

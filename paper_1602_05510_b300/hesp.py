@@ -36,7 +36,8 @@ EXPORTS = (
     "hesp_surrogate_set", "hesp_surrogate_grad", "hesp_surrogate_adam", "hesp_surrogate_train",
     "hesp_surrogate_infer", "hesp_surrogate_error", "hesp_select_workspace_size", "hesp_select_topk",
     "hesp_make_cands", "hesp_gather_f32", "hesp_rank_metrics_workspace_size", "hesp_rank_metrics",
-    "hesp_generate_mutants", "hesp_gather_rows", "hesp_best_makespan", "hesp_graph_begin", "hesp_graph_end",
+    "hesp_generate_mutants", "hesp_gather_rows", "hesp_best_makespan", "hesp_best_candidate", "hesp_graph_begin",
+    "hesp_graph_end",
     "hesp_graph_launch", "hesp_graph_destroy", "hesp_platform_set_tuning", "hesp_platform_get_tuning",
     "hesp_sim_autotune", "hesp_sort_cands_workspace_size", "hesp_sort_cands_by_size", "hesp_platform_set_policy",
     "hesp_simulate_critical", "hesp_solver_moves", "hesp_solver_pick", "hesp_schedule_metrics",
@@ -159,6 +160,7 @@ def lib():
         L.hesp_platform_set_cache.argtypes = [vp, i32]
         L.hesp_platform_set_link.argtypes = [vp, i32, i32, i64, i64]
         L.hesp_best_makespan.argtypes = [vp, vp, vp, i64, vp, vp]
+        L.hesp_best_candidate.argtypes = [vp, vp, i64, i64, vp, vp]
         L.hesp_gather_rows.argtypes = [vp, vp, i64, i64, vp, vp]
         L.hesp_generate_mutants.argtypes = [vp, i32, i32, i32, ctypes.c_double, u64, i64, i64, vp, vp]
         L.hesp_generate_candidates.argtypes = [i32, u64, i64, i64, i32, i32, i32, vp, vp, vp]
@@ -664,6 +666,17 @@ def best_makespan(makespan, status, ntasks=None, out=None, stream=None):
         out = torch.empty(2, dtype=torch.int64, device=makespan.device)
     check(lib().hesp_best_makespan(_ptr(makespan), _ptr(status), _ptr(ntasks), makespan.numel(), _ptr(out),
                                    _stream(stream)), "hesp_best_makespan")
+    return out
+
+
+def best_candidate(makespan, status, first_index=0, out=None, stream=None):
+    """Device int64 [2]: the least makespan among successful candidates and
+    first_index + the lowest index holding it (INT64_MAX, -1 if none)."""
+    import torch
+    if out is None:
+        out = torch.empty(2, dtype=torch.int64, device=makespan.device)
+    check(lib().hesp_best_candidate(_ptr(makespan), _ptr(status), makespan.numel(), first_index, _ptr(out),
+                                    _stream(stream)), "hesp_best_candidate")
     return out
 
 

@@ -110,6 +110,14 @@ class SurrogateConfig:
     label_cap: int = 1 << 20
     infer_chunk: int = 16384       # rows per inference launch (activation buffers)
     use_surrogate: bool = True     # False: simulate random mutants (the same search without the model)
+    # "random": the first labels come from warmup_launches uniform launches;
+    # "solver": from the paper's iterative solver (CP selection, Hard
+    # sampling) run from the unsplit partition to its first local optimum --
+    # every partition it simulates is a label, and its elites seed the rounds
+    start: str = "random"
+    solver_iters: int = 1000       # cap on the solver's iterations in "solver" mode
+    heldout: int = 0               # uniform partitions simulated once, never trained on: each round's
+                                   # relative error and Spearman rank correlation on them
 
 
 def surrogate_search(spec, n_tiles, b, n_levels, seed, budget_s, per_launch=4096, cfg: SurrogateConfig = None,
@@ -119,8 +127,7 @@ def surrogate_search(spec, n_tiles, b, n_levels, seed, budget_s, per_launch=4096
     exactly, add them to the labels, retrain briefly."""
     import torch
     cfg = cfg or SurrogateConfig()
-    sim = sim or Simulator(spec, n_tiles, b, n_levels - 1, per_launch, task_cap, ws_bytes)
-    nb = sim.nb
+    nb = W.base_count(n_tiles)
     P = cfg.proposals
     n_rand = int(P * cfg.random_fraction) // 64 * 64
     lab_lv = torch.empty(cfg.label_cap * nb, dtype=torch.int8, device="cuda")
@@ -147,7 +154,8 @@ def surrogate_search(spec, n_tiles, b, n_levels, seed, budget_s, per_launch=4096
         m, ev = (int(v) for v in hesp.best_makespan(ms, st, nt).cpu().numpy())
         events += ev
         done += count
-        best = m if best is None else min(best, m)
+        if m != big:
+            best = m if best is None else min(best, m)
 
     def record(t0, extra=None):
         log.times.append(time.perf_counter() - t0)
@@ -159,12 +167,48 @@ def surrogate_search(spec, n_tiles, b, n_levels, seed, budget_s, per_launch=4096
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    # warm-up labels from uniform random partitions
-    for w in range(cfg.warmup_launches):
-        hesp.generate_candidates(hesp.GEN_UNIFORM, seed, w * per_launch, per_launch, n_tiles, b, n_levels, prop)
-        ms, st, nt = sim.run(prop)
-        add(prop, ms, st, nt, per_launch)
-        record(t0)
+    if cfg.start == "solver":
+        # the solver's descent from the unsplit partition: each iteration's
+        # current partition and every moved partition it simulated are labels
+        sv = IterativeSolver(spec, n_tiles, b, n_levels, hesp.SOLVER_CP, hesp.PICK_HARD, task_cap, ws_bytes)
+        sv.start(levels=np.zeros(nb, np.int8))
+        for it in range(cfg.solver_iters):
+            if time.perf_counter() - t0 >= budget_s:
+                break
+            chosen, k, _, _ = sv.iterate(seed, it)
+            add(sv.cur_before, sv.cur_ms, sv.cur_st, None, 1)
+            if k:
+                add(sv.rows, sv.ms[:k], sv.st[:k], sv.nt[:k], k)
+            record(t0)
+            if chosen is None:
+                break
+        del sv
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    sim = sim or Simulator(spec, n_tiles, b, n_levels - 1, per_launch, task_cap, ws_bytes)
+    if cfg.start != "solver":
+        # warm-up labels from uniform random partitions
+        for w in range(cfg.warmup_launches):
+            hesp.generate_candidates(hesp.GEN_UNIFORM, seed, w * per_launch, per_launch, n_tiles, b, n_levels,
+                                     prop)
+            ms, st, nt = sim.run(prop)
+            add(prop, ms, st, nt, per_launch)
+            record(t0)
+    ho = None
+    if cfg.heldout > 0:
+        # a held-out uniform sample (its own SplitMix64 stream), simulated once
+        H_ = cfg.heldout
+        ho_lv = torch.empty(H_ * nb, dtype=torch.int8, device="cuda")
+        ho_ms = torch.empty(H_, dtype=torch.int64, device="cuda")
+        ho_st = torch.empty(H_, dtype=torch.int32, device="cuda")
+        hesp.generate_candidates(hesp.GEN_UNIFORM, seed + 11, 0, H_, n_tiles, b, n_levels, ho_lv)
+        for i in range(0, H_, per_launch):
+            c = min(per_launch, H_ - i)
+            ms, st, _ = sim.run(ho_lv[i * nb:], c)
+            ho_ms[i:i + c].copy_(ms)
+            ho_st[i:i + c].copy_(st)
+        ho_ok = ho_st == 0
+        ho = (ho_lv, ho_ms, ho_ok, torch.empty(H_, dtype=torch.float32, device="cuda"))
     sur.fit_stats(lab_ms[:n_lab])
     mu, sigma, _ = sur.stats()
     if cfg.use_surrogate:
@@ -199,7 +243,12 @@ def surrogate_search(spec, n_tiles, b, n_levels, seed, budget_s, per_launch=4096
                 rel, rho = hesp.rank_metrics(sel_pred[okm], ms[okm], mu, sigma)
         rows = hesp.gather_rows(prop, idx, nb)
         add(rows, ms, st, nt, per_launch)
-        record(t0, {"round": rnd, "rel_err": rel, "spearman": rho, "labels": n_lab})
+        m = {"round": rnd, "rel_err": rel, "spearman": rho, "labels": n_lab}
+        if cfg.use_surrogate and ho is not None:
+            ho_lv, ho_ms, ho_ok, ho_pred = ho
+            sur.infer(ho_lv, cfg.heldout, ho_pred)
+            m["heldout_rel_err"], m["heldout_spearman"] = hesp.rank_metrics(ho_pred[ho_ok], ho_ms[ho_ok], mu, sigma)
+        record(t0, m)
         if cfg.use_surrogate:
             sur.train(lab_lv, lab_ms, n_lab, cfg.batch, cfg.steps_per_round, cfg.lr, seed=seed + 100 + rnd)
         rnd += 1
@@ -255,6 +304,7 @@ class IterativeSolver:
         self.st = torch.empty(self.max_moves, dtype=torch.int32, device=dev)
         self.nt = torch.empty(self.max_moves, dtype=torch.int64, device=dev)
         self.chosen = torch.empty(1, dtype=torch.int64, device=dev)
+        self.cur_before = torch.empty(nb, dtype=torch.int8, device=dev)  # the last iteration's start
         self.cands_rows = hesp.cands_tensor(n_tiles, b, np.arange(self.max_moves, dtype=np.int64) * nb)
         self.cand_cur = hesp.cands_tensor(n_tiles, b, np.zeros(1, np.int64))
 
@@ -291,6 +341,7 @@ class IterativeSolver:
         import torch
         if trace:
             lv0 = self.cur.cpu().numpy().copy()
+        self.cur_before.copy_(self.cur)
         self.schedule_stage()
         hesp.solver_moves_range(self.cur, self.nb, self.lo, self.hi, self.mode, self.crit, self.moves, self.count,
                                 self.rows)

@@ -8,6 +8,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle as O  # noqa: E402
+from paper_1602_05510_b300 import hesp  # noqa: E402
 from paper_1602_05510_b300 import search as S  # noqa: E402
 from paper_1602_05510_b300 import workloads as W  # noqa: E402
 
@@ -75,3 +76,39 @@ def test_trained_surrogate_gains_over_unranked_proposals():
     assert top.min() <= plain.min()
     rel, rho = hesp.rank_metrics(pred, ms_all, mu, sigma)
     assert rho > 0.5 and rel < 0.05
+
+
+def test_best_candidate_matches_definition():
+    """hesp_best_candidate: the least makespan among successful candidates
+    and the lowest index holding it (offset by the batch's first global
+    index), with ties, failed candidates and an all-failed batch."""
+    rng = np.random.default_rng(8)
+    for n, first in ((1, 0), (1000, 7), (70000, 123456789)):
+        ms = rng.integers(10 ** 9, 10 ** 9 + 50, n).astype(np.int64)  # many ties
+        st = np.where(rng.random(n) < 0.2, -1, 0).astype(np.int32)
+        st[0] = 0
+        out = hesp.best_candidate(torch.from_numpy(ms).cuda(), torch.from_numpy(st).cuda(), first).cpu().numpy()
+        ok = st == 0
+        m = int(ms[ok].min())
+        assert out.tolist() == [m, first + int(np.flatnonzero(ok & (ms == m))[0])]
+    st = np.full(16, -1, np.int32)
+    out = hesp.best_candidate(torch.zeros(16, dtype=torch.int64, device="cuda"), torch.from_numpy(st).cuda(), 5)
+    assert out.cpu().tolist() == [np.iinfo(np.int64).max, -1]
+
+
+def test_solver_seeded_surrogate_search_small():
+    """The surrogate arm started from the iterative solver's descent: its
+    first records follow the solver from the unsplit partition (so its best
+    is at most the unsplit makespan), later rounds report the error and
+    rank correlation on a held-out uniform sample, and the best is a real
+    simulation result (the oracle agrees on the unsplit partition)."""
+    spec = W.PLATFORMS["cfg1a"]
+    cfg = S.SurrogateConfig(hidden=128, batch=1024, warmup_steps=50, steps_per_round=10, proposals=8192,
+                            elites=16, label_cap=1 << 16, p_mut=0.01, start="solver", heldout=256)
+    s = S.surrogate_search(spec, 8, 2048, 3, seed=5, budget_s=4.0, per_launch=1024, cfg=cfg)
+    unsplit = O.simulate(O.make_platform(spec), 8, 2048, np.zeros(120, np.int8), schedule=False)["makespan"]
+    assert s.best[0] <= unsplit
+    assert all(a >= b for a, b in zip(s.best, s.best[1:]))
+    assert s.metrics
+    for m in s.metrics:
+        assert np.isfinite(m["heldout_rel_err"]) and -1 <= m["heldout_spearman"] <= 1
