@@ -1225,9 +1225,9 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
             if (E > a.ar.Ecap) status = HESP_ERR_CAPACITY;
         }
 
-        // ---- 3. successor lists (CSR).  The sweep appended pending[j] edges
-        // for task j, in creation order, so edge e belongs to the successor
-        // whose prefix range of those counts holds e.
+        // ---- 3. successor lists (CSR), each sorted by task id.  The sweep
+        // appended pending[j] edges for task j, in creation order, so edge e
+        // belongs to the successor whose prefix range of those counts holds e.
         if (!reuse && status == HESP_OK) {
             int32_t *const scnt = at<int32_t>(base, a.ar.off_next);
             int32_t *const succoff = at<int32_t>(base, a.ar.off_succoff);
@@ -1262,10 +1262,16 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                         const int v = __shfl_sync(FULL, incl, pos + step - 1);
                         if (v <= g) pos += step;
                     }
-                    if (g < total) {
-                        const int q = atomicAdd(&scnt[epred[erun + g]], 1);
-                        succ[q] = (int)j0 + pos;
-                    }
+                    // lanes of one predecessor take consecutive slots in lane
+                    // (= successor) order, so every successor list is sorted by id
+                    const int pr = g < total ? epred[erun + g] : -1 - lane;
+                    const unsigned grp = __match_any_sync(FULL, pr);
+                    const int lead = __ffs(grp) - 1;
+                    int q0 = 0;
+                    if (g < total && lane == lead) q0 = atomicAdd(&scnt[pr], __popc(grp));
+                    q0 = __shfl_sync(FULL, q0, lead);
+                    if (g < total) succ[q0 + __popc(grp & ((1u << lane) - 1u))] = (int)j0 + pos;
+                    __syncwarp();
                 }
                 erun += total;
             }
@@ -1525,32 +1531,12 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
             const int iter_cap = 4 * (int)T + 64;
             int scheduled = 0;
             bool ok = true;
-            // Released tasks wait either in the bitmap (several completions at
-            // one time, or a long successor list) or, when a single task
-            // completed and released at most 32 successors, in the lanes (dj).
-            int dj = INT_MAX;
-            uint64_t djd = 0;  // descriptor of task dj, loaded when it is released
-            bool direct = false;
+            // Tasks released when a single task completes are taken straight
+            // from its (sorted) successor list; those released by several
+            // completions at one time wait in the bitmap.
             for (;;) {
-                // schedule every released task in ascending id
-                if (direct) {
-                    for (;;) {
-                        const int j = __reduce_min_sync(FULL, dj);
-                        if (j == INT_MAX) break;
-                        const unsigned own = __ballot_sync(FULL, dj == j);
-                        const uint64_t dsc = __shfl_sync(FULL, djd, __ffs(own) - 1);
-                        if (dj == j) dj = INT_MAX;
-                        if (waits) {
-                            if (lane == 0) link[qt].rq = j;
-                            ++qt;
-                            continue;
-                        }
-                        schedule_task<M, NS, true, GEN, CAP>(j, dsc, t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem, s_ptype, pm, pt, pv,
-                                                   avail, head, tail, hfin, mk, ok, sched_base, sel, rp_seed, cache, links, cs, capfail);
-                        ++scheduled;
-                    }
-                    direct = false;
-                } else {
+                // schedule every task the bitmap holds, in ascending id
+                {
                     for (int w0 = wlo; w0 <= whi; w0 += 32) {
                         const int w = w0 + lane;
                         uint32_t bits = 0;
@@ -1617,6 +1603,68 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                     cms[s] = __ballot_sync(FULL, hfin[s] == t);
                     ncomp += __popc(cms[s]);
                 }
+                if (ncomp == 1) {
+                    // the only completion: its processor's FIFO advances, then
+                    // its successors, 32 at a time in ascending id, lose one
+                    // pending predecessor, and the released ones are scheduled
+                    // (F-P / R-P: queued) in lane order
+                    int src = 0, i = 0;
+#pragma unroll
+                    for (int s = 0; s < NS; ++s)
+                        if (cms[s]) {
+                            src = __ffs(cms[s]) - 1;
+                            i = __shfl_sync(FULL, head[s], src);
+                        }
+                    Link l0;
+                    l0.next = 0;
+                    l0.nfin = 0;
+                    if (lane == src) l0 = link[i];
+                    const int eq = lane < 2 ? succoff[i + lane] : 0;
+                    const int e0 = __shfl_sync(FULL, eq, 0), e1 = __shfl_sync(FULL, eq, 1);
+                    if (lane == src) {
+#pragma unroll
+                        for (int s = 0; s < NS; ++s)
+                            if (cms[s]) {
+                                head[s] = l0.next;
+                                hfin[s] = l0.next >= 0 ? l0.nfin : kInf;
+                                if (l0.next < 0) tail[s] = -1;
+                            }
+                    }
+                    __syncwarp();
+                    for (int c0 = e0; c0 < e1; c0 += 32) {
+                        const int e = c0 + lane;
+                        int sj = 0;
+                        uint64_t dsj = 0;
+                        bool relj = false;
+                        if (e < e1) {
+                            sj = succ[e];
+                            // the descriptor is read beside the count (one
+                            // round trip instead of two for a released task)
+                            dsj = desc[sj];
+                            const int pvv = (int)pending[sj] - 1;
+                            pending[sj] = (uint16_t)pvv;
+                            relj = pvv == 0;
+                        }
+                        unsigned rel = __ballot_sync(FULL, relj);
+                        while (rel) {
+                            const int bl = __ffs(rel) - 1;
+                            rel &= rel - 1;
+                            const int j = __shfl_sync(FULL, sj, bl);
+                            const uint64_t dj = __shfl_sync(FULL, dsj, bl);
+                            if (waits) {
+                                if (lane == 0) link[qt].rq = j;
+                                ++qt;
+                                continue;
+                            }
+                            schedule_task<M, NS, true, GEN, CAP>(j, dj, t, base, a, Lc, lb_b, fL, lane, s_exec, s_pmem,
+                                                               s_ptype, pm, pt, pv, avail, head, tail, hfin, mk, ok,
+                                                               sched_base, sel, rp_seed, cache, links, cs, capfail);
+                            ++scheduled;
+                        }
+                    }
+                    __syncwarp();
+                    continue;
+                }
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
                     unsigned cm = cms[s];
@@ -1631,23 +1679,7 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
                         if (lane == src) l0 = link[i];
                         const int eq = lane < 2 ? succoff[i + lane] : 0;
                         const int e0 = __shfl_sync(FULL, eq, 0), e1 = __shfl_sync(FULL, eq, 1);
-                        if (ncomp == 1 && e1 - e0 <= 32) {
-                            // the only completion: its released successors wait in the lanes
-                            const int e = e0 + lane;
-                            if (e < e1) {
-                                const int sj = succ[e];
-                                // the descriptor is read beside the count (one
-                                // round trip instead of two for a released task)
-                                const uint64_t dsj = desc[sj];
-                                const int pvv = (int)pending[sj] - 1;
-                                pending[sj] = (uint16_t)pvv;
-                                if (pvv == 0) {
-                                    dj = sj;
-                                    djd = dsj;
-                                }
-                            }
-                            direct = true;
-                        } else {
+                        {
                             int lo = INT_MAX, hi = -1;
                             for (int e = e0 + lane; e < e1; e += 32) {
                                 const int sj = succ[e];
