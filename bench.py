@@ -164,10 +164,12 @@ def run_gpu(args):
     build.build()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    nb = W.base_count(N_TILES)
+    n = args.tiles  # 32 (smaller only for profiling)
+    cap = args.task_cap
+    nb = W.base_count(n)
     C = args.candidates
     plat = hesp.Platform(W.PLATFORMS[PLAT])
-    ws = hesp.alloc_workspace(plat, N_TILES, MAX_LEVEL, C, TASK_CAP)  # every candidate resident
+    ws = hesp.alloc_workspace(plat, n, MAX_LEVEL, C, cap)  # every candidate resident
     levels = torch.empty(C * nb, dtype=torch.int8, device=dev)
     cands = torch.empty(C * 16, dtype=torch.uint8, device=dev)
     ms = torch.empty(C, dtype=torch.int64, device=dev)
@@ -180,11 +182,11 @@ def run_gpu(args):
 
     def step(first, k, kev=None):
         # generation, simulation, the batch's best candidate and its task-event count (4 launches)
-        hesp.generate_candidates(hesp.GEN_UNIFORM, SEED, first, C, N_TILES, B, N_LEVELS, levels, cands)
+        hesp.generate_candidates(hesp.GEN_UNIFORM, SEED, first, C, n, B, N_LEVELS, levels, cands)
         if kev is not None:
             kev[0].record(stream)
-        hesp.simulate_batch(plat, cands, levels, C, N_TILES, MAX_LEVEL, ws, makespan=ms, status=st, ntasks=nt,
-                            task_cap=TASK_CAP)
+        hesp.simulate_batch(plat, cands, levels, C, n, MAX_LEVEL, ws, makespan=ms, status=st, ntasks=nt,
+                            task_cap=cap)
         if kev is not None:
             kev[1].record(stream)
         hesp.best_candidate(ms, st, first, out=best[k])
@@ -230,7 +232,7 @@ def run_gpu(args):
         lv_host = [torch.from_numpy(W.uniform_levels(SEED, rank_first(rank, world, C, 1000 + s), C, nb,
                                                      N_LEVELS).reshape(-1)).pin_memory()
                    for s in range(min(args.e2e_steps, 2))]
-        cand_host = hesp.cands_tensor(N_TILES, B, np.arange(C, dtype=np.int64) * nb, device="cpu").pin_memory()
+        cand_host = hesp.cands_tensor(n, B, np.arange(C, dtype=np.int64) * nb, device="cpu").pin_memory()
         ms_host = torch.empty(C, dtype=torch.int64).pin_memory()
         best_host = torch.empty(2, dtype=torch.int64).pin_memory()
         e2e_ev, e2e_tasks = [], 0
@@ -243,8 +245,8 @@ def run_gpu(args):
             a.record(stream)
             levels.copy_(lv_host[s % len(lv_host)], non_blocking=True)
             cands.copy_(cand_host, non_blocking=True)
-            hesp.simulate_batch(plat, cands, levels, C, N_TILES, MAX_LEVEL, ws, makespan=ms, status=st, ntasks=nt,
-                                task_cap=TASK_CAP)
+            hesp.simulate_batch(plat, cands, levels, C, n, MAX_LEVEL, ws, makespan=ms, status=st, ntasks=nt,
+                                task_cap=cap)
             hesp.best_candidate(ms, st, 0, out=best[0])
             hesp.best_makespan(ms, st, nt, out=evs[0])
             ms_host.copy_(ms, non_blocking=True)
@@ -275,6 +277,7 @@ def run_gpu(args):
         "data": "synthetic (seeded SplitMix64 partition vectors generated on the device)",
         "config": dict(CONFIG, candidates_per_step=C, parallelism="candidates sharded across ranks (dp%d)" % world,
                        l2="256 MB buffer written between timed steps; per-step working set ~220 GB > L2"),
+        "profiling_case": None if (n, cap) == (N_TILES, TASK_CAP) else {"n_tiles": n, "task_cap": cap},
         "candidates_per_s": C * world * K / t_max if t_max > 0 else None,
         "task_events": tot_events,
         "wall_s": wall,
@@ -285,8 +288,8 @@ def run_gpu(args):
         "clocks": clk,
         "e2e": e2e,
     }
-    line["roofline"] = roofline(t_kern / max(K, 1), task_events / max(K, 1), props, peaks)
-    if world == 1:
+    line["roofline"] = roofline(t_kern / max(K, 1), task_events / max(K, 1), props, peaks, n)
+    if world == 1 and (n, cap) == (N_TILES, TASK_CAP):
         extra_clk = ClockSampler(local)
         extra_clk.start()
         if args.extra_cfg1:
@@ -313,7 +316,7 @@ def run_cfg1(args, dev):
 
     from paper_1602_05510_b300 import hesp
 
-    n, b, NL, C = C1.n_tiles, C1.b, C1.n_levels, C1.n_cand
+    n, b, NL, C = C1.n_tiles, C1.b, C1.n_levels, args.cfg1_candidates
     nb = W.base_count(n)
     stream = torch.cuda.current_stream()
     plats = [hesp.Platform(W.PLATFORMS[k]) for k in C1_PLATS]
@@ -360,6 +363,19 @@ def run_cfg1(args, dev):
             "workload": "random search, N=16384 Cholesky, b=2048 (8x8 tiles, 120 base tasks), split levels uniform "
                         "{0,1,2}, 65,536 candidates per step, largest DAG first, one DAG build launch, simulated on "
                         "12 CPU + 1 GPU-type (transfers, write-back) and on 4 big + 4 LITTLE (shared memory)"}
+
+
+def run_random8x8(args):
+    """The 8 x 8-tile two-platform step on its own line (profiling and
+    comparison with the default run's extra key)."""
+    import torch
+
+    from paper_1602_05510_b300 import build
+
+    build.build()
+    r = run_cfg1(args, torch.device("cuda", 0))
+    r.update({"n_gpus": 1, "higher_is_better": True, "candidates_per_step": args.cfg1_candidates})
+    print(json.dumps(r))
 
 
 def search_comparison(args):
@@ -423,8 +439,13 @@ def surrogate_cfg(args):
 # ncu figures of the simulation kernel taken on the kernel source whose sha1
 # prefix is given (null once the source changes): DRAM bytes and issued
 # warp-instructions per task-event and the share of issue slots busy.
-SIM_NCU = {"source_sha1_12": None, "dram_bytes_per_task_event": None, "warp_inst_per_task_event": None,
-           "issue_active_pct": None, "warps_per_sm": None, "case": None}
+SIM_NCU = {"source_sha1_12": "9bfa3bffdffc",
+           # one 1-pass capture of a full 4,096-candidate launch: 1.06 TB read + 0.578 TB written
+           "dram_bytes_per_task_event": (1.06e12 + 0.578e12) / 3316708562,
+           # --set full on a 10x10-tile launch of the same kernel (3,072 candidates)
+           "warp_inst_per_task_event": 55.287302e9 / 78173006, "issue_active_pct": 45.52, "warps_per_sm": 18.35,
+           "case": "DRAM bytes: the full 4,096-candidate launch (one pass); instructions and issue slots: a "
+                   "10x10-tile launch of 3,072 candidates (20.8 warps per SM)"}
 
 
 def sim_source_matches():
@@ -435,7 +456,7 @@ def sim_source_matches():
         return False
 
 
-def roofline(t, events, props, peaks):
+def roofline(t, events, props, peaks, n=N_TILES):
     """Dominant kernel: the simulation launch (expansion, dependences and the
     event loop of every candidate).  It is bound by integer and control
     issue, not by HBM or tensor cores.  `achieved` counts the algorithmic
@@ -447,7 +468,7 @@ def roofline(t, events, props, peaks):
     task-event from ncu, times the live task-event rate, against SMs x 4
     schedulers x clock)."""
     spec = W.PLATFORMS[PLAT]
-    alg = alg_ops_per_event(W.uniform_levels(SEED, 0, 256, W.base_count(N_TILES), N_LEVELS), N_TILES, B,
+    alg = alg_ops_per_event(W.uniform_levels(SEED, 0, 256, W.base_count(n), N_LEVELS), n, B,
                             len(spec.procs), spec.n_mem)
     sm_max = (peaks or {}).get("sm_max_mhz", 2032.0)
     sms = props.multi_processor_count
@@ -463,9 +484,8 @@ def roofline(t, events, props, peaks):
            "kernel_ms": 1e3 * t, "task_events_per_launch": events, "alg_ops_per_task_event": alg,
            "traffic": SIM_NCU["dram_bytes_per_task_event"] * events if fresh else None,
            "dram_gbs": SIM_NCU["dram_bytes_per_task_event"] * events / t / 1e9 if fresh and t > 0 else None,
-           "traffic_note": "DRAM bytes per task-event from one ncu capture of a smaller launch of the same kernel "
-                           "(%s), times this launch's task-events; algorithmic I/O is 5,984 B in + 24 B out per "
-                           "candidate" % SIM_NCU["case"],
+           "traffic_note": "DRAM bytes per task-event from ncu (%s), times this launch's task-events; "
+                           "algorithmic I/O is 5,984 B in + 24 B out per candidate" % SIM_NCU["case"],
            "issue_slots": {"warp_inst_per_task_event": ipe,
                            "achieved_frac_of_issue_peak": ipe * events / t / issue_peak if ipe and t > 0 else None,
                            "issue_peak_warp_inst_per_s": issue_peak,
@@ -900,53 +920,56 @@ def run_exhaustive(args):
 
 def run_search(args):
     """32 x 32 tiles (5984 base tasks, levels 0..3) on 32 CPU + 2 GPU-type
-    processors: plain batched random search against surrogate-guided search,
-    each for the same wall-time budget on one GPU."""
-    import torch
-
+    processors, each arm for the same wall-time budget on one GPU: plain
+    batched random search; surrogate-guided search started from the
+    iterative solver's descent; the same without the model (mutants of the
+    same elites simulated unranked: the ablation); surrogate-guided search
+    started from uniform random launches; the paper's iterative solver (CP
+    selection, Hard sampling) from the unsplit partition."""
     from paper_1602_05510_b300 import build, hesp
     from paper_1602_05510_b300 import search as S
 
     build.build()
-    n, b, NL = 32, 2048, 4
-    spec = W.PLATFORMS["cfg4"]
-    cap = 1 << 20
+    n, b, NL = N_TILES, B, N_LEVELS
+    spec = W.PLATFORMS[PLAT]
     ws = int(args.ws_gb * (1 << 30))
-    sim = S.Simulator(spec, n, b, NL - 1, args.per_launch, task_cap=cap, ws_bytes=ws)
-    rlog = S.random_search(spec, n, b, NL, seed=4, budget_s=args.budget, per_launch=args.per_launch, sim=sim)
-    cfg = S.SurrogateConfig(hidden=512, batch=2048, warmup_launches=1, warmup_steps=args.warmup_steps,
-                            steps_per_round=args.round_steps, proposals=args.round_proposals, elites=32,
-                            p_mut=args.p_mut, label_cap=1 << 17)
-    sim2 = S.Simulator(spec, n, b, NL - 1, args.round_sims, task_cap=cap, ws_bytes=ws)
-    slog = S.surrogate_search(spec, n, b, NL, seed=5, budget_s=args.budget, per_launch=args.round_sims, cfg=cfg,
-                              sim=sim2)
-    cfg_m = S.SurrogateConfig(**dict(cfg.__dict__, use_surrogate=False))
-    mlog = S.surrogate_search(spec, n, b, NL, seed=5, budget_s=args.budget, per_launch=args.round_sims, cfg=cfg_m,
-                              sim=sim2)
-    del sim, sim2
-    # the paper's own iterative solver (CP selection, Hard sampling) from the unsplit partition
+    sim = S.Simulator(spec, n, b, NL - 1, args.per_launch, task_cap=TASK_CAP)
+    rlog = S.random_search(spec, n, b, NL, seed=SEED, budget_s=args.budget, per_launch=args.per_launch, sim=sim)
+    del sim
+    free_cuda()
+    base = surrogate_cfg(args)
+    arms = {}
+    for name, extra in (("surrogate_solver_start", dict(start="solver", heldout=1024, p_mut=args.seeded_p_mut)),
+                        ("mutation_without_surrogate_solver_start",
+                         dict(start="solver", p_mut=args.seeded_p_mut, use_surrogate=False)),
+                        ("surrogate_random_start", dict(heldout=1024))):
+        lg = S.surrogate_search(spec, n, b, NL, seed=5, budget_s=args.budget, per_launch=args.round_sims,
+                                cfg=S.SurrogateConfig(**dict(base, **extra)), task_cap=TASK_CAP, ws_bytes=ws)
+        arms[name] = lg
+        free_cuda()
     ilog = S.iterative_search(spec, n, b, NL, hesp.SOLVER_CP, hesp.PICK_HARD, seed=6, budget_s=args.budget,
-                              task_cap=cap, ws_bytes=ws, first=np.zeros(W.base_count(n), np.int8))
+                              task_cap=TASK_CAP, ws_bytes=ws, first=np.zeros(W.base_count(n), np.int8))
     target = rlog.best[-1]
-    t_reach = slog.time_to_reach(target)
-    t_solver = slog.time_to_reach(ilog.best[-1])
     line = {"metric": "best makespan in %.0f s, surrogate vs plain search" % args.budget, "unit": "ns",
             "higher_is_better": False, "n_gpus": 1,
             "workload": "32x32 tiles, b=2048, levels 0..3, 32 CPU + 2 GPU-type processors",
             "random": {"best": rlog.best[-1], "candidates": rlog.simulated[-1], "task_events": rlog.events[-1],
-                       "task_events_per_s": rlog.events[-1] / rlog.times[-1], "trace": list(zip(rlog.times, rlog.best))},
-            "surrogate": {"best": slog.best[-1], "candidates_simulated": slog.simulated[-1],
-                          "task_events": slog.events[-1], "trace": list(zip(slog.times, slog.best)),
-                          "rounds": slog.metrics},
-            "mutation_without_surrogate": {"best": mlog.best[-1], "candidates_simulated": mlog.simulated[-1],
-                                           "trace": list(zip(mlog.times, mlog.best)),
-                                           "time_to_random_best_s": mlog.time_to_reach(target)},
+                       "task_events_per_s": rlog.events[-1] / rlog.times[-1],
+                       "trace": list(zip(rlog.times, rlog.best))},
             "iterative_cp_hard": {"best": ilog.best[-1], "candidates_simulated": ilog.simulated[-1],
                                   "iterations": len(ilog.best), "task_events": ilog.events[-1],
                                   "trace": list(zip(ilog.times, ilog.best)), "restarts": ilog.metrics,
-                                  "time_to_random_best_s": ilog.time_to_reach(target)},
-            "surrogate_time_to_random_best_s": t_reach,
-            "time_ratio": (t_reach / rlog.times[-1]) if t_reach is not None else None}
+                                  "time_to_random_best_s": ilog.time_to_reach(target)}}
+    for name, lg in arms.items():
+        t_reach = lg.time_to_reach(target)
+        line[name] = {"best": lg.best[-1], "candidates_simulated": lg.simulated[-1], "task_events": lg.events[-1],
+                      "time_to_random_best_s": t_reach,
+                      "time_ratio": (t_reach / rlog.times[-1]) if t_reach is not None else None,
+                      "time_to_solver_best_s": lg.time_to_reach(ilog.best[-1]),
+                      "spearman_selected_median": _median([m.get("spearman") for m in lg.metrics]),
+                      "spearman_heldout_median": _median([m.get("heldout_spearman") for m in lg.metrics]),
+                      "rel_err_heldout_median": _median([m.get("heldout_rel_err") for m in lg.metrics]),
+                      "rounds": len(lg.metrics), "trace": list(zip(lg.times, lg.best))}
     print(json.dumps(line))
 
 
@@ -1046,16 +1069,21 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=0, help="reference arm: candidates per step (0: one per core)")
     ap.add_argument("--candidates", type=int, default=N_CAND,
                     help="candidates per step (default: the workload's 4,096; smaller only for profiling)")
+    ap.add_argument("--tiles", type=int, default=N_TILES,
+                    help="tiles per matrix side (default 32; smaller only for profiling captures)")
+    ap.add_argument("--task-cap", type=int, default=TASK_CAP, help="arena task capacity (profiling captures)")
     ap.add_argument("--no-extra-cfg1", dest="extra_cfg1", action="store_false",
                     help="skip the 8x8-tile two-platform line of the default run")
     ap.add_argument("--cfg1-steps", type=int, default=5)
+    ap.add_argument("--cfg1-candidates", type=int, default=C1.n_cand,
+                    help="candidates of the 8x8-tile step (default 65,536; smaller only for profiling)")
     ap.add_argument("--cfg1-warmup", type=int, default=3)
     ap.add_argument("--search-budget", type=float, default=60.0,
                     help="seconds per arm of the search comparison of the default run (0: skip)")
     ap.add_argument("--general-candidates", type=int, default=65536,
                     help="candidates per launch of the factors / capacity workloads")
-    ap.add_argument("--workload", default="random", choices=["random", "surrogate", "search", "uneven", "solver",
-                                                            "table1", "exhaustive", "factors", "capacity"],
+    ap.add_argument("--workload", default="random", choices=["random", "random8x8", "surrogate", "search", "uneven",
+                                                            "solver", "table1", "exhaustive", "factors", "capacity"],
                     help="random: the default benchmark line; surrogate: label/train/rank/re-score "
                          "pipeline; search: surrogate-guided vs random search with the ablation arm")
     ap.add_argument("--labels", type=int, default=1 << 20)
@@ -1074,6 +1102,8 @@ def main():
                     help="mutation rate of the solver-seeded surrogate arm of the default run")
     ap.add_argument("--ws-gb", type=float, default=100.0)
     args = ap.parse_args()
+    if args.workload == "random8x8":
+        return run_random8x8(args)
     if args.workload == "surrogate":
         return run_surrogate_pipeline(args)
     if args.workload == "search":
