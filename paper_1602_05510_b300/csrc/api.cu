@@ -203,7 +203,9 @@ int sim_slots_for(const hesp_platform *p, const Arena &ar, int64_t *resident_war
     int rc = sim_kernel_occupancy(p->n_mem, p->n_procs, ar.Tcap, &blocks, &threads);
     if (rc) return rc;
     if (blocks < 1) blocks = 1;
-    if (p->tune_ctas_per_sm > 0 && p->tune_ctas_per_sm < blocks) blocks = p->tune_ctas_per_sm;
+    // the tuning value counts groups of 8 candidate warps per SM
+    const int per8 = threads >= 256 ? 1 : 256 / threads;
+    if (p->tune_ctas_per_sm > 0 && p->tune_ctas_per_sm * per8 < blocks) blocks = p->tune_ctas_per_sm * per8;
     *resident_warps = (int64_t)sms * blocks * (threads / 32);
     return HESP_OK;
 }

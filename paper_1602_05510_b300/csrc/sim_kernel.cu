@@ -473,11 +473,11 @@ struct AtomState {
 };
 
 // Packed per-(destination m, source s != m) atom counts: counter q =
-// m * (M - 1) + (s < m ? s : s - 1), 16 bits each, two per word.
+// m * (M - 1) + (s < m ? s : s - 1), 10 bits each, three per word.
 template <int M>
 struct Counts {
     static constexpr int NQ = M * (M - 1);
-    static constexpr int NW = (NQ + 1) / 2;
+    static constexpr int NW = (NQ + 2) / 3;  // three 10-bit counters per word (a task has <= 768 atoms)
     unsigned w[NW > 0 ? NW : 1];
     __device__ __forceinline__ static int q_of(int m, int s) { return m * (M - 1) + (s < m ? s : s - 1); }
     __device__ __forceinline__ void clear() {
@@ -489,12 +489,12 @@ struct Counts {
         for (int s = 0; s < M; ++s) {
             if (s == m) continue;
             const int q = q_of(m, s);
-            if (s == src) w[q >> 1] += 1u << (16 * (q & 1));
+            if (s == src) w[q / 3] += 1u << (10 * (q % 3));
         }
     }
     __device__ __forceinline__ unsigned get(int m, int s) const {
         const int q = q_of(m, s);
-        return (w[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+        return (w[q / 3] >> (10 * (q % 3))) & 1023u;
     }
 };
 
@@ -1777,9 +1777,15 @@ __global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl,
     }
 }
 
+// Simulation launches use CTAs of four candidate warps: a batch smaller than
+// the resident capacity (4,096 candidates of 32 x 32 tiles fill 27.7 of an
+// SM's 32 warp slots) then spreads over the SMs in steps of four warps, not
+// eight, so no SM carries many more candidates than the others.
+constexpr int kSimThreads = 128;
+
 template <int M, int NS>
 void occupancy_of(int *blocks, size_t smem) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, sim_kernel<M, NS, false>, 256, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, sim_kernel<M, NS, false>, kSimThreads, smem);
 }
 
 template <int M, int NS>
@@ -1901,8 +1907,8 @@ int sim_bitmap_smem_words(int64_t Tcap) {
 }
 
 int sim_kernel_occupancy(int n_mem, int n_procs, int64_t Tcap, int *blocks_per_sm, int *threads_per_block) {
-    *threads_per_block = 256;
-    const size_t smem = (size_t)sim_bitmap_smem_words(Tcap) * 4 * 8;
+    *threads_per_block = kSimThreads;
+    const size_t smem = (size_t)sim_bitmap_smem_words(Tcap) * 4 * (kSimThreads / 32);
     const bool two = n_procs > 32;
     switch (n_mem) {
     case 1: two ? set_smem_attr<1, 2>(smem) : set_smem_attr<1, 1>(smem); break;
@@ -1950,7 +1956,7 @@ int launch_sim(const hesp_platform *p, const DevPlatform &dp, const Arena &ar, i
     a.bm_smem_words = p->tune_bitmap == 1 ? 0 : sim_bitmap_smem_words(ar.Tcap);
     unsigned long long *ctr = &((WsHeader *)ws)->work_counter;
     if (cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), stream) != cudaSuccess) return HESP_ERR_CUDA;
-    const int threads = 256;
+    const int threads = kSimThreads;
     const size_t smem = (size_t)a.bm_smem_words * 4 * (threads / 32);
     const int64_t blocks = (n_slots * 32 + threads - 1) / threads;
     const bool two = p->n_procs > 32;
