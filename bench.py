@@ -439,11 +439,11 @@ def surrogate_cfg(args):
 # ncu figures of the simulation kernel taken on the kernel source whose sha1
 # prefix is given (null once the source changes): DRAM bytes and issued
 # warp-instructions per task-event and the share of issue slots busy.
-SIM_NCU = {"source_sha1_12": "9bfa3bffdffc",
-           # one 1-pass capture of a full 4,096-candidate launch: 1.06 TB read + 0.578 TB written
-           "dram_bytes_per_task_event": (1.06e12 + 0.578e12) / 3316708562,
+SIM_NCU = {"source_sha1_12": "625d145ba2bb",
+           # one 1-pass capture of a full 4,096-candidate launch: 1.05 TB read + 0.5756 TB written
+           "dram_bytes_per_task_event": (1.05e12 + 0.5756e12) / 3316708562,
            # --set full on a 10x10-tile launch of the same kernel (3,072 candidates)
-           "warp_inst_per_task_event": 55.287302e9 / 78173006, "issue_active_pct": 45.52, "warps_per_sm": 18.35,
+           "warp_inst_per_task_event": 54.446167e9 / 78173006, "issue_active_pct": 49.34, "warps_per_sm": 18.09,
            "case": "DRAM bytes: the full 4,096-candidate launch (one pass); instructions and issue slots: a "
                    "10x10-tile launch of 3,072 candidates (20.8 warps per SM)"}
 
@@ -477,7 +477,7 @@ def roofline(t, events, props, peaks, n=N_TILES):
     fresh = sim_source_matches()
     issue_peak = sms * 4 * sm_max * 1e6
     ipe = SIM_NCU["warp_inst_per_task_event"] if fresh else None
-    out = {"bound": "alu", "kernel": "sim_kernel<M=3,NS=2> (cpu32_gpu2)", "achieved": achieved, "peak": peak,
+    out = {"bound": "alu", "kernel": "sim_kernel<M=3,NS=2> (cpu32_gpu2; 72 registers, 4-warp CTAs)", "achieved": achieved, "peak": peak,
            "unit": "T int64-op/s", "frac": achieved / peak if achieved else None,
            "peak_source": "derived: %d SMs x 128 INT32 lanes x %.0f MHz / 2 (sm_max_mhz of MEASURED_PEAKS)"
                           % (sms, sm_max),

@@ -909,8 +909,12 @@ __device__ __forceinline__ int64_t schedule_task(int j, uint64_t d, int64_t t, c
 // without the simulation; platform independent, so one instantiation).
 // CAP: the general instantiation with finite memories (kept apart so that
 // the other general launches carry none of its registers).
+// Registers: 64 per thread (8 four-warp CTAs per SM); with two processor
+// slots per lane (more than 32 processors) 72, at 7 CTAs per SM (28 warps,
+// still 4,144 resident candidates on 148 SMs), which removes nearly all of
+// that instantiation's spills; the build launch 40 (six 8-warp CTAs).
 template <int M, int NS, bool GEN, bool BUILD = false, bool CAP = false>
-__global__ void __launch_bounds__(256, BUILD ? 6 : 4) sim_kernel(DevPlatform pl, KArgs a,
+__global__ void __launch_bounds__(BUILD ? 256 : 128, BUILD ? 6 : (NS > 1 ? 7 : 8)) sim_kernel(DevPlatform pl, KArgs a,
                                                                  unsigned long long *work_counter) {
     __shared__ int64_t s_exec[4 * HESP_MAX_TYPES * HESP_LB];
     __shared__ int64_t s_wsum[4 * HESP_LB];
