@@ -131,37 +131,36 @@ class using_library:
 def _load(path):
     """The oracle library at `path` with its argument types declared."""
     L = ctypes.CDLL(path)
-    if True:  # (one block of declarations)
-        i32, i64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
-        L.or_exec_ns.restype = i64
-        L.or_exec_ns.argtypes = [ctypes.POINTER(Platform), i32, i32, i64]
-        L.or_xfer_ns.restype = i64
-        L.or_xfer_ns.argtypes = [ctypes.POINTER(Platform), i64]
-        L.or_base_count.restype = i64
-        L.or_base_count.argtypes = [i32]
-        L.or_base_ops.restype = ctypes.c_int
-        L.or_base_ops.argtypes = [i32, vp]
-        L.or_levels_to_code.restype = i64
-        L.or_levels_to_code.argtypes = [i32, vp, vp, i64]
-        L.or_expand.restype = i64
-        L.or_expand.argtypes = [i32, i64, vp, i64, i64, vp, vp, vp, vp, vp, vp]
-        L.or_deps.restype = i64
-        L.or_deps.argtypes = [i32, i64, vp, i64, i64, i32, i32, i64, vp, vp, vp]
-        L.or_simulate.restype = i32
-        L.or_simulate.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i64, i64, i32, i32,
-                                  vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
-        L.or_simulate_levels.restype = i32
-        L.or_simulate_levels.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i32, i32,
-                                         vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
-        L.or_deps_side.restype = i64
-        L.or_deps_side.argtypes = [i32, i64, vp, i64, i64, i32, i64, i64, vp, vp, vp]
-        L.or_factors_to_code.restype = i64
-        L.or_factors_to_code.argtypes = [i32, vp, vp, i64]
-        L.or_simulate_factors.restype = i32
-        L.or_simulate_factors.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i32,
-                                          vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
-        L.or_simulate_many.restype = i32
-        L.or_simulate_many.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i64, vp, vp, vp]
+    i32, i64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    L.or_exec_ns.restype = i64
+    L.or_exec_ns.argtypes = [ctypes.POINTER(Platform), i32, i32, i64]
+    L.or_xfer_ns.restype = i64
+    L.or_xfer_ns.argtypes = [ctypes.POINTER(Platform), i64]
+    L.or_base_count.restype = i64
+    L.or_base_count.argtypes = [i32]
+    L.or_base_ops.restype = ctypes.c_int
+    L.or_base_ops.argtypes = [i32, vp]
+    L.or_levels_to_code.restype = i64
+    L.or_levels_to_code.argtypes = [i32, vp, vp, i64]
+    L.or_expand.restype = i64
+    L.or_expand.argtypes = [i32, i64, vp, i64, i64, vp, vp, vp, vp, vp, vp]
+    L.or_deps.restype = i64
+    L.or_deps.argtypes = [i32, i64, vp, i64, i64, i32, i32, i64, vp, vp, vp]
+    L.or_simulate.restype = i32
+    L.or_simulate.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i64, i64, i32, i32,
+                              vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
+    L.or_simulate_levels.restype = i32
+    L.or_simulate_levels.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i32, i32,
+                                     vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
+    L.or_deps_side.restype = i64
+    L.or_deps_side.argtypes = [i32, i64, vp, i64, i64, i32, i64, i64, vp, vp, vp]
+    L.or_factors_to_code.restype = i64
+    L.or_factors_to_code.argtypes = [i32, vp, vp, i64]
+    L.or_simulate_factors.restype = i32
+    L.or_simulate_factors.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i32,
+                                      vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
+    L.or_simulate_many.restype = i32
+    L.or_simulate_many.argtypes = [ctypes.POINTER(Platform), i32, i64, vp, i64, vp, vp, vp]
     return L
 
 
