@@ -46,3 +46,17 @@ def test_workload_constants():
     assert bench.N_LEVELS == 4 and bench.N_CAND == 4096
     spec = W.PLATFORMS[bench.PLAT]
     assert len(spec.procs) == 34 and spec.n_mem == 3
+
+
+def test_reference_arm_line(capsys):
+    """bench.py --impl reference: the oracle on one candidate of the default
+    workload prints one JSON line with the base contract's keys."""
+    import json
+
+    args = types.SimpleNamespace(steps=1, warmup=0, ref_sample=1)
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["e2e"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["config"]["n_tiles"] == 32 and line["higher_is_better"] is True
